@@ -1,0 +1,211 @@
+"""FP64 CPU oracle for the Shan-Chen bubble-merging LBM (arXiv 1708.01608).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow statement of what the GPU path
+computes.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it; the library package never does.  It shares
+no code with the CUDA path.
+
+The arithmetic lives in ``sc_oracle.c`` (plain C, double precision); this
+module only marshals numpy arrays.  Population arrays have shape
+``(Q, nz, ny, nx)`` in the post-streaming form ``f_i(x, t)``; velocity order
+as in ``velocities()``.
+
+Functions whose result is not pinned by a closed form, invariant or brute
+force are marked "parity unpinned" in their docstrings.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "sc_oracle.c")
+LIB = os.path.join(HERE, "_build", "libsc_oracle.so")
+
+D2Q9, D3Q19 = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile sc_oracle.c into _build/libsc_oracle.so (gcc, OpenMP)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        os.makedirs(os.path.dirname(LIB), exist_ok=True)
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+             "-ffp-contract=off", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        d, i64, i32, u64 = C.c_double, C.c_int64, C.c_int32, C.c_uint64
+        P = C.c_void_p
+        _lib.orc_q.argtypes = [C.c_int]
+        _lib.orc_velocities.argtypes = [C.c_int, P, P]
+        _lib.orc_splitmix64.argtypes = [u64, u64]
+        _lib.orc_splitmix64.restype = u64
+        _lib.orc_eos.argtypes = [i64, P, d, d, P, P]
+        _lib.orc_moments.argtypes = [C.c_int, i64, i64, i64, P, P, P, P, P]
+        _lib.orc_force.argtypes = [C.c_int, i64, i64, i64, P, d, P, P, P]
+        _lib.orc_step.argtypes = [C.c_int, i64, i64, i64, d, d, d, P, P, i32, P, P, P]
+        _lib.orc_run.argtypes = [C.c_int, i64, i64, i64, d, d, d, P, i64, i32, P, P, P]
+        _lib.orc_step_cells.argtypes = [C.c_int, i64, i64, i64, d, d, d, P, i64, P, P]
+        _lib.orc_init.argtypes = [C.c_int, i64, i64, i64, i32, P, d, d, d, d, u64, P, P]
+        _lib.orc_sample_sites.argtypes = [i64, i64, i64, i32, d, d, d, d, u64, i64, P]
+        _lib.orc_sample_sites.restype = i32
+        _lib.orc_laplacian.argtypes = [C.c_int, i64, i64, i64, P, P]
+        _lib.orc_line_d2.argtypes = [i64, i64, i64, P, i64, i64, i64, C.c_int, i64, P]
+        _lib.orc_label_gas.argtypes = [C.c_int, i64, i64, i64, P, d, P]
+        _lib.orc_label_gas.restype = i64
+        _lib.orc_totals.argtypes = [C.c_int, i64, i64, i64, P, P]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def q_of(lat: int) -> int:
+    return 9 if lat == D2Q9 else 19
+
+
+def velocities(lat: int):
+    """(c, w): c int array (Q, 3), w float64 (Q,) in the oracle's order."""
+    q = q_of(lat)
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q, dtype=np.float64)
+    _L().orc_velocities(lat, _p(c), _p(w))
+    return c, w
+
+
+def splitmix64(key: int, k: int) -> int:
+    """k-th output of a SplitMix64 generator seeded with key."""
+    return int(_L().orc_splitmix64(key & (2**64 - 1), k))
+
+
+def _shape(f):
+    q, nz, ny, nx = f.shape
+    return q, nx, ny, nz
+
+
+def eos(rho, G, rho0=1.0):
+    """(psi, p): psi = rho0 (1 - exp(-rho/rho0)), p = rho/3 + G/6 psi^2 (Sec. 3.1)."""
+    rho = _f64(rho)
+    psi = np.empty_like(rho)
+    p = np.empty_like(rho)
+    _L().orc_eos(rho.size, _p(rho), G, rho0, _p(psi), _p(p))
+    return psi, p
+
+
+def moments(lat, f):
+    """(rho, jx, jy, jz), each shaped (nz, ny, nx)."""
+    f = _f64(f)
+    q, nx, ny, nz = _shape(f)
+    out = [np.empty((nz, ny, nx)) for _ in range(4)]
+    _L().orc_moments(lat, nx, ny, nz, _p(f), *[_p(o) for o in out])
+    return tuple(out)
+
+
+def force(lat, psi, G):
+    """Shan-Chen force (Fx, Fy, Fz) for a psi field shaped (nz, ny, nx)."""
+    psi = _f64(psi)
+    nz, ny, nx = psi.shape
+    out = [np.empty_like(psi) for _ in range(3)]
+    _L().orc_force(lat, nx, ny, nz, _p(psi), G, *[_p(o) for o in out])
+    return tuple(out)
+
+
+def run(lat, f, nsteps, tau, G, rho0=1.0, sites=None, rate=None, budget=None):
+    """Advance f (copied) by nsteps.  sites: linear cell indices; budget is
+    updated in place when given.  Returns the new f."""
+    f = _f64(f).copy()
+    q, nx, ny, nz = _shape(f)
+    n = 0 if sites is None else len(sites)
+    sc = np.ascontiguousarray(sites, dtype=np.int64) if n else None
+    rt = _f64(rate) if n else None
+    if n:
+        assert budget is not None and budget.dtype == np.float64 and budget.flags.c_contiguous
+    _L().orc_run(lat, nx, ny, nz, tau, G, rho0, _p(f), int(nsteps), n, _p(sc), _p(rt),
+                 _p(budget) if n else None)
+    return f
+
+
+def step_cells(lat, f, cells, tau, G, rho0=1.0):
+    """f_i(x, t+1) at the listed linear cells computed one by one: (ncells, Q)."""
+    f = _f64(f)
+    q, nx, ny, nz = _shape(f)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.empty((len(cells), q))
+    _L().orc_step_cells(lat, nx, ny, nz, tau, G, rho0, _p(f), len(cells), _p(cells), _p(out))
+    return out
+
+
+def init(lat, nx, ny, nz, bubbles, rho_l, rho_g, width, noise_amp, seed):
+    """Initial populations f_eq(rho, 0) for tanh gas bubbles in liquid plus
+    SplitMix64 noise.  bubbles: (n, 4) array of x, y, z, r.  Returns (f, rho)."""
+    q = q_of(lat)
+    b = _f64(np.zeros((0, 4)) if bubbles is None else bubbles).reshape(-1, 4)
+    f = np.empty((q, nz, ny, nx))
+    rho = np.empty((nz, ny, nx))
+    _L().orc_init(lat, nx, ny, nz, len(b), _p(b), rho_l, rho_g, width, noise_amp,
+                  seed & (2**64 - 1), _p(f), _p(rho))
+    return f, rho
+
+
+def sample_sites(nx, ny, nz, n, r_min, r_max, min_spacing, min_gap, seed, max_tries=10**7):
+    """Random nucleation sites by rejection sampling (Sec. 3): (got, (n, 4))."""
+    out = np.zeros((max(n, 1), 4))
+    got = _L().orc_sample_sites(nx, ny, nz, n, r_min, r_max, min_spacing, min_gap,
+                                seed & (2**64 - 1), max_tries, _p(out))
+    return got, out[:n]
+
+
+def laplacian(lat, p):
+    """5-point (2-D) / 7-point (3-D) periodic Laplacian of a field (nz, ny, nx)."""
+    p = _f64(p)
+    nz, ny, nx = p.shape
+    out = np.empty_like(p)
+    _L().orc_laplacian(lat, nx, ny, nz, _p(p), _p(out))
+    return out
+
+
+def line_d2(p, start, axis, length):
+    """p(x+e) - 2p(x) + p(x-e) at `length` cells from start=(x, y, z) along axis."""
+    p = _f64(p)
+    nz, ny, nx = p.shape
+    out = np.empty(length)
+    _L().orc_line_d2(nx, ny, nz, _p(p), int(start[0]), int(start[1]), int(start[2]),
+                     int(axis), int(length), _p(out))
+    return out
+
+
+def label_gas(lat, rho, thr):
+    """Face-connected periodic components of rho < thr; labels = min linear
+    index of the component, -1 for liquid.  Returns (labels int32, ncomp)."""
+    rho = _f64(rho)
+    nz, ny, nx = rho.shape
+    lab = np.empty(rho.shape, dtype=np.int32)
+    n = _L().orc_label_gas(lat, nx, ny, nz, _p(rho), thr, _p(lab))
+    return lab, int(n)
+
+
+def totals(lat, f):
+    """FP64 (M, Jx, Jy, Jz) summed cell by cell in velocity order."""
+    f = _f64(f)
+    q, nx, ny, nz = _shape(f)
+    out = np.zeros(4)
+    _L().orc_totals(lat, nx, ny, nz, _p(f), _p(out))
+    return out

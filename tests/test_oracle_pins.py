@@ -1,0 +1,436 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a closed form,
+an invariant, a special case that reduces to textbook lattice Boltzmann, a
+published test vector, or a brute-force computation on a tiny input, chosen so
+that a dropped term, a wrong sign, index or weight in the oracle fails one of
+them.  CPU only.
+"""
+import math
+
+import networkx as nx
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+
+import oracle as O
+
+LATS = [O.D2Q9, O.D3Q19]
+
+
+def textbook_feq(lat, rho, u):
+    """Second-order Maxwell-Boltzmann equilibrium on a lattice with cs^2 = 1/3."""
+    c, w = O.velocities(lat)
+    cu = np.tensordot(c.astype(float), u, axes=([1], [0]))  # (Q, ...)
+    uu = (u * u).sum(0)
+    return w.reshape((-1,) + (1,) * rho.ndim) * rho * (1 + 3 * cu + 4.5 * cu**2 - 1.5 * uu)
+
+
+# ---------------------------------------------------------------- tables / RNG
+
+@pytest.mark.parametrize("lat", LATS)
+def test_velocity_set_isotropy(lat):
+    """Weights reproduce the lattice moments of a Maxwellian with cs^2 = 1/3 up
+    to fourth order (this fixes every weight and every velocity)."""
+    c, w = O.velocities(lat)
+    c = c.astype(float)
+    d = 2 if lat == O.D2Q9 else 3
+    assert len(w) == (9 if lat == O.D2Q9 else 19)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs((w[:, None] * c).sum(0)).max() < 1e-15
+    m2 = np.einsum("i,ia,ib->ab", w, c, c)
+    assert np.allclose(m2[:d, :d], np.eye(d) / 3, atol=1e-15)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)[:d, :d, :d, :d]
+    I = np.eye(d)
+    iso = (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+           + np.einsum("ad,bc->abcd", I, I)) / 9
+    assert np.allclose(m4, iso, atol=1e-15)
+    # odd moments vanish
+    assert np.abs(np.einsum("i,ia,ib,ic->abc", w, c, c, c)).max() < 1e-15
+    # every velocity appears with its opposite, all distinct
+    s = {tuple(v) for v in c.astype(int)}
+    assert len(s) == len(w) and all(tuple(-np.array(v)) in s for v in s)
+
+
+def test_splitmix64_published_vector():
+    """SplitMix64 seeded with 1234567: the published first outputs."""
+    assert [O.splitmix64(1234567, k) for k in range(3)] == [
+        6457827717110365317, 3203168211198807973, 9817491932198370423]
+
+
+# ---------------------------------------------------------------- EOS / psi
+
+def test_eos_critical_point_closed_form():
+    """p = rho/3 + G/6 psi^2 with psi = 1 - exp(-rho): dp/drho = d2p/drho2 = 0
+    at G = -4, rho = ln 2 (psi psi' has its maximum 1/4 there)."""
+    h = 1e-4
+    r = np.array([math.log(2) - h, math.log(2), math.log(2) + h])
+    _, p = O.eos(r, -4.0)
+    assert abs((p[2] - p[0]) / (2 * h)) < 1e-7
+    assert abs((p[2] - 2 * p[1] + p[0]) / h**2) < 1e-5
+    psi, _ = O.eos(np.array([0.0, 1.0, 50.0]), 0.0)
+    assert psi[0] == 0.0 and abs(psi[1] - (1 - math.exp(-1))) < 1e-16 and abs(psi[2] - 1) < 1e-15
+    psi2, _ = O.eos(np.array([2.0]), 0.0, rho0=2.0)
+    assert abs(psi2[0] - 2 * (1 - math.exp(-1))) < 1e-15
+
+
+# ---------------------------------------------------------------- force
+
+@pytest.mark.parametrize("lat", LATS)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_force_on_cosine_psi(lat, axis):
+    """For psi = a + b cos(k s) varying along one axis the weighted stencil
+    reduces to F_s = -G psi (1/6)(psi(s+1) - psi(s-1)) = (G/3) b sin k sin(ks) psi,
+    zero in the other axes."""
+    if lat == O.D2Q9 and axis == 2:
+        pytest.skip("no z axis in 2-D")
+    n = 16
+    shape = [1, n, n] if lat == O.D2Q9 else [n, n, n]  # (nz, ny, nx)
+    G, a, b = -5.0, 0.6, 0.1
+    k = 2 * math.pi * 3 / n
+    s = np.arange(n, dtype=float)
+    prof = a + b * np.cos(k * s)
+    psi = np.empty(shape)
+    idx = [slice(None)] * 3
+    target_dim = 2 - axis  # array dims are (z, y, x)
+    view = [1, 1, 1]
+    view[target_dim] = n
+    psi[...] = prof.reshape(view)
+    F = O.force(lat, psi, G)
+    expect = (G / 3) * b * math.sin(k) * np.sin(k * s).reshape(view) * psi
+    for ax in range(3):
+        if ax == axis:
+            assert np.abs(F[ax] - expect).max() < 1e-15
+        else:
+            assert np.abs(F[ax]).max() < 1e-16
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_uniform_psi_gives_zero_force(lat):
+    shape = (1, 8, 8) if lat == O.D2Q9 else (6, 5, 4)
+    F = O.force(lat, np.full(shape, 0.7), -5.0)
+    assert all(np.abs(f).max() == 0.0 for f in F)
+
+
+# ---------------------------------------------------------------- collision / streaming
+
+@pytest.mark.parametrize("lat", LATS)
+@pytest.mark.parametrize("G", [0.0, -5.0])
+def test_uniform_moving_equilibrium_is_fixed_point(lat, G):
+    """A uniform f_eq(rho, u) is invariant: streaming moves identical values and
+    the (zero) force leaves the equilibrium unchanged."""
+    shape = (1, 6, 7) if lat == O.D2Q9 else (4, 5, 6)
+    rho = np.full(shape, 1.3)
+    u = np.zeros((3,) + shape)
+    u[0], u[1] = 0.05, -0.03
+    if lat == O.D3Q19:
+        u[2] = 0.02
+    f0 = textbook_feq(lat, rho, u)
+    f1 = O.run(lat, f0, 3, 0.7, G)
+    assert np.abs(f1 - f0).max() < 1e-15
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_streaming_direction(lat):
+    """With tau huge the collision barely changes f: a marker added to
+    population i at cell x0 shows up at x0 + c_i after one step."""
+    c, w = O.velocities(lat)
+    shape = (1, 5, 6) if lat == O.D2Q9 else (5, 6, 7)
+    nz, ny, nx_ = shape
+    x0 = (2, 3, 1 if lat == O.D3Q19 else 0)
+    for i in range(len(w)):
+        f = textbook_feq(lat, np.ones(shape), np.zeros((3,) + shape))
+        f[i, x0[2], x0[1], x0[0]] += 1e-3
+        g = O.run(lat, f, 1, 1e12, 0.0)
+        d = g - textbook_feq(lat, np.ones(shape), np.zeros((3,) + shape))
+        j = ((x0[0] + c[i, 0]) % nx_, (x0[1] + c[i, 1]) % ny, (x0[2] + c[i, 2]) % nz)
+        assert abs(d[i, j[2], j[1], j[0]] - 1e-3) < 1e-12
+        d[i, j[2], j[1], j[0]] = 0
+        assert np.abs(d).max() < 1e-12
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_collision_adds_exactly_F_momentum(lat):
+    """Velocity-shift forcing: post-collision momentum at x is j(x) + F(x) and
+    post-collision mass is rho(x), for any tau (gathered from f(t+1) at x + c_i)."""
+    c, w = O.velocities(lat)
+    shape = (1, 12, 10) if lat == O.D2Q9 else (6, 7, 8)
+    nz, ny, nx_ = shape
+    bub = np.array([[4.0, 5.0, 2.0 if lat == O.D3Q19 else 0.0, 3.0]])
+    f0, _ = O.init(lat, nx_, ny, nz, bub, 2.0, 0.15, 2.0, 1e-2, 7)
+    f0 = O.run(lat, f0, 5, 0.8, -5.0)  # develop non-equilibrium parts and velocity
+    tau, G = 0.73, -5.0
+    rho, jx, jy, jz = O.moments(lat, f0)
+    psi, _ = O.eos(rho, G)
+    F = O.force(lat, psi, G)
+    f1 = O.run(lat, f0, 1, tau, G)
+    fs = np.empty_like(f1)
+    for i in range(len(w)):
+        fs[i] = np.roll(f1[i], shift=(-c[i, 2], -c[i, 1], -c[i, 0]), axis=(0, 1, 2))
+    assert np.abs(fs.sum(0) - rho).max() < 1e-13
+    for a, (j, Fa) in enumerate(zip((jx, jy, jz), F)):
+        mom = np.tensordot(c[:, a].astype(float), fs, axes=(0, 0))
+        assert np.abs(mom - (j + Fa)).max() < 1e-13
+
+
+def test_shear_wave_viscosity():
+    """G = 0: a shear wave u_y = A sin(kx) decays as exp(-nu k^2 t) with
+    nu = cs^2 (tau - 1/2) (BGK lattice viscosity)."""
+    for lat in LATS:
+        n, tau, A = 64, 0.8, 1e-4
+        shape = (1, 2, n) if lat == O.D2Q9 else (2, 2, n)
+        k = 2 * math.pi / n
+        x = np.arange(n)
+        u = np.zeros((3,) + shape)
+        u[1] = A * np.sin(k * x)
+        f = textbook_feq(lat, np.ones(shape), u)
+        T = 400
+        g = O.run(lat, f, T, tau, 0.0)
+        rho, jx, jy, jz = O.moments(lat, g)
+        amp = 2.0 / n * ((jy / rho)[0, 0] * np.sin(k * x)).sum()
+        rate = -math.log(amp / A) / T
+        nu = (tau - 0.5) / 3
+        assert abs(rate / (nu * k * k) - 1) < 5e-3, (lat, rate, nu * k * k)
+
+
+# ---------------------------------------------------------------- conservation
+
+@pytest.mark.parametrize("lat", LATS)
+def test_mass_and_momentum_conserved_without_injection(lat):
+    shape = (1, 24, 24) if lat == O.D2Q9 else (10, 12, 14)
+    nz, ny, nx_ = shape
+    bub = np.array([[6.0, 7.0, 4.0 if lat == O.D3Q19 else 0.0, 4.0],
+                    [15.0, 14.0, 5.0 if lat == O.D3Q19 else 0.0, 3.0]])
+    f0, _ = O.init(lat, nx_, ny, nz, bub, 2.0, 0.15, 2.0, 1e-3, 3)
+    t0 = O.totals(lat, f0)
+    f1 = O.run(lat, f0, 60, 0.9, -5.0)
+    t1 = O.totals(lat, f1)
+    assert abs(t1[0] - t0[0]) / t0[0] < 1e-13
+    assert np.abs(t1[1:]).max() / t0[0] < 1e-13
+
+
+def test_injection_ledger_and_placement():
+    """Virtual blowing agent: the mass gained equals sum_s min(r_s t, B_s) and
+    is deposited at the site after collision (so it streams to x_s + c_i)
+    with zero momentum; budgets never go negative."""
+    lat = O.D2Q9
+    c, w = O.velocities(lat)
+    n = 16
+    f0 = textbook_feq(lat, np.ones((1, n, n)), np.zeros((3, 1, n, n)))
+    sites = np.array([3 + n * 4, 11 + n * 12], dtype=np.int64)
+    rate = np.array([1e-4, 3e-4])
+    budget = np.array([0.01, 5e-3])
+    # one step at tau = 1, G = 0 from rest: rho(x_s + c_i) = 1 + w_i r_s
+    b1 = budget.copy()
+    f1 = O.run(lat, f0, 1, 1.0, 0.0, sites=sites, rate=rate, budget=b1)
+    rho1 = O.moments(lat, f1)[0][0]
+    expect = np.ones((n, n))
+    for s, r in zip(sites, rate):
+        x, y = s % n, s // n
+        for i in range(9):
+            expect[(y + c[i, 1]) % n, (x + c[i, 0]) % n] += w[i] * r
+    assert np.abs(rho1 - expect).max() < 1e-15
+    assert np.allclose(b1, budget - rate, rtol=0, atol=1e-18)
+    # ledger over 120 steps with G = -5 (site 2 exhausts after ~17 steps)
+    b = budget.copy()
+    t0 = O.totals(lat, f0)
+    T = 120
+    g = O.run(lat, f0, T, 0.9, -5.0, sites=sites, rate=rate, budget=b)
+    t1 = O.totals(lat, g)
+    added = sum(min(r * T, B) for r, B in zip(rate, budget))
+    assert abs((t1[0] - t0[0]) - added) < 1e-13 * t0[0]
+    assert np.abs(t1[1:]).max() < 1e-12
+    assert (b >= 0).all() and b[1] == 0.0
+
+
+# ---------------------------------------------------------------- phase behaviour
+
+def _run_cosine(G, steps=400):
+    n = 64
+    k = 2 * math.pi / n
+    rho = math.log(2) + 1e-3 * np.cos(k * np.arange(n)).reshape(1, 1, n)
+    f = textbook_feq(O.D2Q9, rho, np.zeros((3, 1, 1, n)))
+    g = O.run(O.D2Q9, f, steps, 1.0, G)
+    r = O.moments(O.D2Q9, g)[0][0, 0]
+    return r.max() - r.min()
+
+
+def test_phase_separation_only_below_critical_G():
+    """Uniform rho = ln 2 with a long-wave perturbation is unstable only when
+    dp/drho < 0, i.e. G < -4 for psi = 1 - exp(-rho)."""
+    assert _run_cosine(-4.8) > 2e-2      # grew by > 10x
+    assert _run_cosine(-3.2) < 2e-3      # did not grow
+
+
+def _coexistence_integral(G, eps):
+    """Mechanical-stability coexistence (Shan & Chen 1994 form):
+    p(rho_g) = p(rho_l) = p0 and int (p0 - p) psi'/psi^(1+eps) drho = 0."""
+    psi = lambda r: 1 - np.exp(-r)
+    dpsi = lambda r: np.exp(-r)
+    p = lambda r: r / 3 + G / 6 * psi(r) ** 2
+
+    def eqs(v):
+        rg, rl = v
+        p0 = p(rl)
+        I = integrate.quad(lambda r: (p0 - p(r)) * dpsi(r) / psi(r) ** (1 + eps), rg, rl,
+                           epsabs=1e-13, epsrel=1e-12)[0]
+        return [p(rg) - p(rl), I]
+
+    return optimize.fsolve(eqs, [0.15, 1.9], xtol=1e-13)
+
+
+def test_flat_interface_coexistence():
+    """A flat interface relaxes to bulk densities with equal EOS pressure
+    (momentum balance across the interface for the pairwise force) close to
+    the Shan-Chen mechanical-stability prediction."""
+    n = 64
+    pg, pl = _coexistence_integral(-5.0, 1.0)
+    bub = np.array([[0.0, 0.0, 0.0, 16.0]])
+    f, _ = O.init(O.D2Q9, n, 1, 1, bub, pl, pg, 4.0, 0.0, 0)
+    g = O.run(O.D2Q9, f, 20000, 1.0, -5.0)
+    rho = O.moments(O.D2Q9, g)[0][0, 0]
+    rg, rl = rho[0], rho[n // 2]
+    _, p = O.eos(np.array([rg, rl]), -5.0)
+    assert abs(p[0] - p[1]) < 1e-9
+    assert abs(rl / pl - 1) < 0.03 and abs(rg / pg - 1) < 0.03, (rg, rl, pg, pl)
+
+
+def test_laplace_law():
+    """Liquid drops of radius R in gas: p_in - p_out = sigma / R (2-D Laplace
+    law): linear in 1/R with a vanishing intercept."""
+    n = 64
+    dp, Rm = [], []
+    for R in (8.0, 10.0, 12.0, 14.0, 16.0):
+        drop = np.array([[n / 2, n / 2, 0.0, R]])
+        # inside the disk takes the second density: a liquid drop in gas
+        f, _ = O.init(O.D2Q9, n, n, 1, drop, 0.1555, 1.9315, 2.0, 0.0, 0)
+        g = O.run(O.D2Q9, f, 3000, 1.0, -5.0)
+        rho = O.moments(O.D2Q9, g)[0][0]
+        _, p = O.eos(rho, -5.0)
+        rin, rout = rho[n // 2, n // 2], rho[0, 0]
+        dp.append(p[n // 2, n // 2] - p[0, 0])
+        # equivalent radius from the excess liquid mass
+        Rm.append(math.sqrt(((rho - rout) / (rin - rout)).sum() / math.pi))
+    dp, Rm = np.array(dp), np.array(Rm)
+    A = np.vstack([1 / Rm, np.ones_like(Rm)]).T
+    (sigma, b), res, *_ = np.linalg.lstsq(A, dp, rcond=None)
+    r2 = 1 - res[0] / ((dp - dp.mean()) ** 2).sum()
+    assert sigma > 0 and r2 > 0.999 and abs(b) < 0.05 * dp[0], (sigma, b, r2)
+
+
+# ---------------------------------------------------------------- diagnostics
+
+@pytest.mark.parametrize("lat", LATS)
+def test_laplacian_eigenvalues(lat):
+    shape = (1, 12, 10) if lat == O.D2Q9 else (6, 12, 10)
+    nz, ny, nx_ = shape
+    ks = (2, 3, 1)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx_), indexing="ij")
+    ax = 2 * math.pi * ks[0] / nx_
+    ay = 2 * math.pi * ks[1] / ny
+    az = 2 * math.pi * ks[2] / nz if lat == O.D3Q19 else 0.0
+    p = np.cos(ax * x) * np.cos(ay * y) * np.cos(az * z)
+    lam = 2 * (math.cos(ax) - 1) + 2 * (math.cos(ay) - 1)
+    if lat == O.D3Q19:
+        lam += 2 * (math.cos(az) - 1)
+    assert np.abs(O.laplacian(lat, p) - lam * p).max() < 1e-13
+    d2 = O.line_d2(p, (0, 5, min(3, nz - 1)), 0, nx_)
+    assert np.abs(d2 - 2 * (math.cos(ax) - 1) * p[min(3, nz - 1), 5, :]).max() < 1e-14
+    d2y = O.line_d2(p, (4, 0, 0), 1, ny + 3)  # wraps around
+    yy = np.arange(ny + 3) % ny
+    assert np.abs(d2y - 2 * (math.cos(ay) - 1) * p[0, yy, 4]).max() < 1e-14
+
+
+def _labels_networkx(mask):
+    nz, ny, nx_ = mask.shape
+    g = nx.Graph()
+    dims = [(0, 0, 1), (0, 1, 0)] + ([(1, 0, 0)] if nz > 1 else [])
+    for z, y, x in zip(*np.nonzero(mask)):
+        k = x + nx_ * (y + ny * z)
+        g.add_node(k)
+        for dz, dy, dx in dims:
+            zz, yy, xx = (z + dz) % nz, (y + dy) % ny, (x + dx) % nx_
+            if mask[zz, yy, xx]:
+                g.add_edge(k, xx + nx_ * (yy + ny * zz))
+    lab = -np.ones(mask.size, dtype=np.int64)
+    comps = list(nx.connected_components(g))
+    for comp in comps:
+        m = min(comp)
+        for k in comp:
+            lab[k] = m
+    return lab.reshape(mask.shape), len(comps)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_labels_match_graph_components(seed):
+    rng = np.random.default_rng(seed)
+    lat = O.D2Q9 if seed % 2 == 0 else O.D3Q19
+    shape = (1, 9, 11) if lat == O.D2Q9 else (5, 6, 7)
+    rho = rng.uniform(0.0, 2.0, size=shape)
+    lab, n = O.label_gas(lat, rho, 0.9)
+    ref, nref = _labels_networkx(rho < 0.9)
+    assert n == nref and (lab == ref).all()
+
+
+def test_labels_wraparound_and_threshold_edge():
+    rho = np.full((1, 6, 8), 2.0)
+    rho[0, 2, 0] = rho[0, 2, 7] = 0.5    # joined through the x wrap
+    rho[0, 0, 3] = rho[0, 5, 3] = 0.5    # joined through the y wrap
+    rho[0, 4, 5] = 1.0                   # exactly at threshold: liquid
+    lab, n = O.label_gas(O.D2Q9, rho, 1.0)
+    assert n == 2
+    assert lab[0, 2, 0] == lab[0, 2, 7] == 16
+    assert lab[0, 0, 3] == lab[0, 5, 3] == 3
+    assert lab[0, 4, 5] == -1
+
+
+# ---------------------------------------------------------------- initial state, sites
+
+def test_init_profile_closed_form():
+    n = 16
+    bub = np.array([[3.0, 4.0, 0.0, 5.0]])
+    f, rho = O.init(O.D2Q9, n, n, 1, bub, 2.0, 0.15, 2.0, 0.0, 0)
+    mid = 0.5 * (2.0 + 0.15)
+    assert abs(rho[0, 4, 8] - mid) < 1e-15     # d = r
+    assert abs(rho[0, 4, 14] - mid) < 1e-15    # d = r through the wrap
+    assert abs(rho[0, 4, 3] - (0.15 + 0.5 * 1.85 * (1 + math.tanh(-5.0)))) < 1e-15
+    c, w = O.velocities(O.D2Q9)
+    assert np.abs(f - w[:, None, None, None] * rho).max() == 0
+    f2, rho2 = O.init(O.D2Q9, n, n, 1, None, 2.0, 0.15, 2.0, 1e-3, 5)
+    noise = rho2 - 2.0
+    assert np.abs(noise).max() <= 1e-3 and abs(noise.mean()) < 2e-4 and noise.std() > 4e-4
+
+
+def test_sites_spacing_and_determinism():
+    got, s = O.sample_sites(128, 128, 128, 64, 3.0, 3.0, 12.0, 0.0, 1)
+    assert got == 64
+    assert (s[:, :3] >= 0).all() and (s[:, :3] < 128).all() and (s[:, :3] == np.floor(s[:, :3])).all()
+    d = s[:, None, :3] - s[None, :, :3]
+    d = (d + 64) % 128 - 64
+    dist = np.sqrt((d ** 2).sum(-1)) + np.eye(64) * 1e9
+    assert dist.min() >= 12.0
+    got2, s2 = O.sample_sites(128, 128, 128, 64, 3.0, 3.0, 12.0, 0.0, 1)
+    assert (s2 == s).all()
+    got3, s3 = O.sample_sites(64, 64, 64, 30, 4.0, 12.0, 0.0, 4.0, 2)
+    assert got3 == 30 and (s3[:, 3] >= 4).all() and (s3[:, 3] < 12).all()
+    d = s3[:, None, :3] - s3[None, :, :3]
+    d = (d + 32) % 64 - 32
+    dist = np.sqrt((d ** 2).sum(-1))
+    need = s3[:, None, 3] + s3[None, :, 3] + 4.0
+    off = ~np.eye(30, dtype=bool)
+    assert (dist[off] >= need[off]).all()
+
+
+def test_step_cells_matches_full_step():
+    """The one-cell-at-a-time update (used on lattices too large for a full
+    oracle run) agrees with the full step."""
+    lat = O.D3Q19
+    nz, ny, nx_ = 7, 6, 9
+    bub = np.array([[4.0, 3.0, 3.0, 2.5]])
+    f0, _ = O.init(lat, nx_, ny, nz, bub, 2.0, 0.15, 2.0, 1e-3, 4)
+    f0 = O.run(lat, f0, 3, 0.8, -5.0)
+    f1 = O.run(lat, f0, 1, 0.8, -5.0)
+    cells = np.array([0, 5, 17, 100, nx_ * ny * nz - 1])
+    out = O.step_cells(lat, f0, cells, 0.8, -5.0)
+    ref = f1.reshape(19, -1)[:, cells].T
+    assert np.abs(out - ref).max() < 1e-15
