@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the Shan-Chen bubble-merging LBM hot path on GB300.
+
+One bench step = one diagnostic interval of the 128^3 D3Q19 FP32 foam
+workload (64 nucleation sites, r = 3, blowing agent 1e-4 per step, budget 50):
+100 fused collide-stream-force steps with injection, then the FP64 totals,
+the gas labelling and the per-site merge bookkeeping, all through the C ABI.
+Throughput is MLUPS = cells * 100 / seconds / 1e6.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched with torch.distributed.run: every rank advances its own
+replica of the lattice (the workload has no exchange step between
+independent lattices), the timed region is bracketed by barriers and the
+maximum time over ranks is reported.  --impl reference times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1708_01608_gb300.workloads import FOAM_128 as W  # noqa: E402
+
+METRIC = "D3Q19 Shan-Chen MLUPS (FP32, 128^3 foam, 64 sites, injection + diagnostics every 100 steps)"
+UNIT = "MLUPS"
+INNER = W["diag_every"]                       # LBM steps per bench step
+CELLS = W["nx"] * W["ny"] * W["nz"]
+Q = 19
+B_ALG = 2 * Q * 4                             # bytes per lattice update, FP32 storage
+FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per launch of the fused kernel from an ncu capture of this
+# workload (dram__bytes_read.sum + dram__bytes_write.sum); None = not captured
+# for the current kernel.
+NCU_TRAFFIC_PER_LAUNCH = None
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_bw_gbs", "hbm"):
+            if k in d:
+                v = d[k]
+                if isinstance(v, dict):
+                    v = v.get("burst", v.get("value"))
+                return float(v), "measured"
+        for k, v in d.items():
+            if "hbm" in k.lower() and isinstance(v, (int, float)):
+                return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_lattice(lbm, kernel="auto"):
+    s = W["sites"]
+    bub = lbm.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
+                           s["min_spacing"], s["min_gap"], W["seed"])
+    L = lbm.Lattice("D3Q19", W["nx"], W["ny"], W["nz"], tau=W["tau"], G=W["G"],
+                    rho0=W["rho0"], storage=W["storage"], gas_threshold=W["threshold"],
+                    kernel=kernel)
+    L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
+    rate = np.full(len(bub), W["rate"])
+    budget = np.full(len(bub), W["budget"])
+    L.inject(rate, budget)
+    return L, rate, budget
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The FP64 oracle on the host cores, bounded sample of the workload."""
+    import oracle as O
+    s = W["sites"]
+    got, bub = O.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
+                              s["min_spacing"], s["min_gap"], W["seed"])
+    f, _ = O.init(O.D3Q19, W["nx"], W["ny"], W["nz"], bub, W["rho_l"], W["rho_g"], W["width"],
+                  W["noise"], W["seed"])
+    cells = (np.floor(bub[:, 0] + 0.5) + W["nx"] * (np.floor(bub[:, 1] + 0.5)
+             + W["ny"] * np.floor(bub[:, 2] + 0.5))).astype(np.int64)
+    rate = np.full(len(bub), W["rate"])
+    budget = np.full(len(bub), W["budget"])
+    O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)  # warm
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds_target:
+        f = O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": CELLS * n / dt / 1e6, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{n} oracle time steps of the full 128^3 lattice with injection "
+                      f"({dt:.1f} s, OpenMP over all host cores)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    import oracle as O
+    s = W["sites"]
+    got, bub = O.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
+                              s["min_spacing"], s["min_gap"], W["seed"])
+    f, _ = O.init(O.D3Q19, W["nx"], W["ny"], W["nz"], bub, W["rho_l"], W["rho_g"], W["width"],
+                  W["noise"], W["seed"])
+    cells = (np.floor(bub[:, 0] + 0.5) + W["nx"] * (np.floor(bub[:, 1] + 0.5)
+             + W["ny"] * np.floor(bub[:, 2] + 0.5))).astype(np.int64)
+    rate = np.full(len(bub), W["rate"])
+    budget = np.full(len(bub), W["budget"])
+    for _ in range(warm):
+        f = O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)
+    dt = time.perf_counter() - t0
+    val = CELLS * steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": W["name"], "cells": CELLS, "sites": s["n"],
+                       "sample": "one LBM time step of the full lattice per bench step"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{steps} oracle time steps of the full 128^3 lattice"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1708_01608_gb300 import build_lib
+    if rank == 0 or not build_lib.up_to_date():
+        build_lib.build()
+    barrier(world)
+    from paper_1708_01608_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    L, rate, budget = make_lattice(lbm, args.kernel)
+
+    def bench_step(e_begin=None, e_end=None):
+        if e_begin is not None:
+            e_begin.record(stream)
+        L.step(INNER)
+        if e_end is not None:
+            e_end.record(stream)
+        L.totals()
+        L.label_gas(want_labels=False)
+        L.site_labels()
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(args.steps):
+        bench_step(*ev_step[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    ms = max_over_ranks(world, ms)
+    step_kernel_ms = sum(a.elapsed_time(b) for a, b in ev_step) / (args.steps * INNER)
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    labels = torch.empty(L.shape, dtype=torch.int32, pin_memory=True).numpy()
+    rate_h = torch.tensor(rate, dtype=torch.float64).pin_memory().numpy()
+    budget_h = L.read_budgets()
+    budget_pin = torch.tensor(budget_h, dtype=torch.float64).pin_memory().numpy()
+    import ctypes as C
+    nc = C.c_int64(0)
+    tot = np.zeros(4)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.inject(rate_h, budget_pin)                      # H2D: rates and budgets
+        L.step(INNER)
+        lbm._check(lbm.lib().lbm_label_gas(L.handle, labels.ctypes.data_as(C.c_void_p),
+                                           C.byref(nc)))  # D2H: labels
+        tot = L.totals()                                  # D2H: totals
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    h2d = rate_h.nbytes + budget_pin.nbytes
+    d2h = labels.nbytes + tot.nbytes + 8
+
+    units = CELLS * INNER * args.steps * world
+    value = units / (ms / 1e3) / 1e6
+    e2e_val = units / e2e_s / 1e6
+    peak, src = peak_hbm()
+    achieved = B_ALG * CELLS / (step_kernel_ms / 1e3) / 1e9
+    launches_per_step = INNER + 2 + 1 + 3 + 1   # steps, totals, moments, labelling, site gather
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": W["name"], "lattice": "D3Q19", "extent": [W["nx"], W["ny"], W["nz"]],
+                       "storage": W["storage"], "tau": W["tau"], "G": W["G"], "sites": W["sites"]["n"],
+                       "lbm_steps_per_bench_step": INNER, "kernel": args.kernel,
+                       "l2": "inputs larger than L2: two 159 MB population lattices",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": src,
+                         "traffic": NCU_TRAFFIC_PER_LAUNCH,
+                         "kernel": "fused_step_kernel", "bytes_per_update": B_ALG,
+                         "kernel_ms": step_kernel_ms},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    L.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "two_pass"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * lbm.h - C ABI of the GB300 Shan-Chen bubble-merging lattice Boltzmann
+ * library (method of Barzegari, Bayani & Mirbagheri, "A criterion for bubble
+ * merging in liquid metal", arXiv 1708.01608).
+ *
+ * One context = one periodic lattice on one CUDA device.  Device memory is
+ * owned by the context (allocated through the caller's allocator callbacks
+ * when given, else cudaMalloc); every host buffer is owned by the caller.
+ * Work is enqueued on the stream given in the configuration (NULL = the
+ * legacy default stream).  A context is not thread-safe.  No function throws
+ * across the ABI: each returns an lbm_status, and lbm_last_error() gives a
+ * message for the calling thread's last failure.
+ *
+ * Lattice conventions (shared by every call that takes or returns fields):
+ *   cell (x, y, z) has linear index x + nx*(y + ny*z); nz = 1 for D2Q9.
+ *   Scalar fields are nx*ny*nz doubles in that order.
+ *   Populations f_i(x, t) ("after streaming": the value that has arrived at
+ *   x) are Q fields, population-major: f[i*N + cell].
+ *   Velocity order, D2Q9 (weights 4/9, 1/9 x4, 1/36 x4):
+ *     0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
+ *   D3Q19 (weights 1/3, 1/18 x6, 1/36 x12):
+ *     0 (0,0,0) 1 (1,0,0) 2 (-1,0,0) 3 (0,1,0) 4 (0,-1,0) 5 (0,0,1) 6 (0,0,-1)
+ *     7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1)
+ *     13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
+ *
+ * The time step (Sec. 3.1 of the paper: Shan-Chen model, single relaxation
+ * time, "streams and collisions"):
+ *   rho = sum_i f_i, j = sum_i f_i c_i
+ *   psi = rho0 (1 - exp(-rho/rho0))           (Sec. 3.1, rho0 = 1 in the paper)
+ *   F   = -G psi(x) sum_i w_i psi(x + c_i) c_i (long-range attraction, Sec. 3.1)
+ *   u   = (j + tau F)/rho                      (velocity-shift forcing)
+ *   f*_i = f_i - (f_i - f_eq_i(rho, u))/tau
+ *   f*_i(x_s) += w_i dm_s at injection sites   (virtual blowing agent, Sec. 3)
+ *   f_i(x + c_i, t+1) = f*_i(x)                (periodic)
+ * EOS pressure p = rho/3 + (G/6) psi^2 (Sec. 3.1; the printed 0.166 = cs^2/2).
+ */
+#ifndef SCLBM_LBM_H
+#define SCLBM_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,   /* bad argument or configuration; nothing was changed */
+  LBM_ENOMEM = 2,   /* device allocation failed */
+  LBM_ECUDA = 3,    /* a CUDA call failed; the context should be destroyed */
+  LBM_ESTATE = 4,   /* call not valid in the current state (e.g. not seeded) */
+  LBM_ENUMERIC = 5, /* a non-finite density was found by a diagnostic */
+  LBM_ETIMEOUT = 6  /* a bounded device wait gave up; results are invalid */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+
+/* storage precision of the populations; arithmetic is FP64 for LBM_F64 and
+ * FP32 otherwise.  The 16-bit forms store f_i - w_i*rho_ref. */
+typedef enum {
+  LBM_F64 = 0,
+  LBM_F32 = 1,
+  LBM_F16_OFFSET = 2,
+  LBM_BF16_OFFSET = 3
+} lbm_storage;
+
+/* fields for lbm_read; every field is returned as doubles */
+typedef enum {
+  LBM_RHO = 0,  /* N: density */
+  LBM_PSI = 1,  /* N: pseudopotential */
+  LBM_P = 2,    /* N: EOS pressure */
+  LBM_U = 3,    /* 3N: physical velocity (j + F/2)/rho, components x, y, z */
+  LBM_F = 4,    /* Q*N: populations f_i(x, t) */
+  LBM_LAPP = 5  /* N: periodic 5-point (2-D) / 7-point (3-D) Laplacian of p */
+} lbm_field;
+
+/* step kernel selection */
+typedef enum {
+  LBM_KERNEL_AUTO = 0,    /* fused kernel with the tuned tile */
+  LBM_KERNEL_FUSED = 1,   /* one pass: TMA-staged tiles, psi halo in smem */
+  LBM_KERNEL_TWO_PASS = 2 /* psi field pass + collide/stream pass */
+} lbm_kernel;
+
+/* Optional device allocator.  alloc returns device memory of `bytes` usable
+ * on `stream` (NULL on failure); free releases it. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct {
+  int32_t lattice;      /* lbm_lattice */
+  int32_t storage;      /* lbm_storage */
+  int64_t nx, ny, nz;   /* periodic extents; nz must be 1 for D2Q9 */
+  double tau;           /* BGK relaxation time, > 0.5 */
+  double G;             /* Shan-Chen interaction strength (G < -4 separates) */
+  double rho0;          /* psi scale; 1 reproduces the paper's psi */
+  double rho_ref;       /* reference density of the 16-bit offset storage */
+  double gas_threshold; /* cells with rho < threshold are gas (labelling) */
+  int32_t kernel;       /* lbm_kernel */
+  int32_t tile;         /* fused-kernel tile id; 0 = pick automatically */
+  void *stream;         /* cudaStream_t, may be NULL */
+  lbm_alloc_fn alloc;   /* NULL: cudaMalloc/cudaFree */
+  lbm_free_fn free;
+  void *alloc_user;
+} lbm_config;
+
+typedef struct {
+  double x, y, z, r; /* centre (cell coordinates; z = 0 in 2-D) and radius */
+} lbm_bubble;
+
+/* Fill *cfg with defaults: D3Q19, F32, 64^3, tau 1, G -5, rho0 1,
+ * rho_ref 1, threshold 1, automatic kernel, default stream, cudaMalloc. */
+void lbm_config_default(lbm_config *cfg);
+
+/* Create a context on the current CUDA device and allocate its two
+ * population lattices.  Errors: EINVAL (extents < 1, nz != 1 for D2Q9,
+ * tau <= 0.5, rho0 <= 0, unknown enum), ENOMEM, ECUDA.  *out is NULL on
+ * failure. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
+
+/* Release all device memory of the context (after synchronising its
+ * stream).  NULL is ignored. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Random nucleation sites (Sec. 3: nucleation positions from a random
+ * function) drawn by rejection sampling from SplitMix64 keyed by
+ * seed ^ 0x7369746573000000.  Candidate m uses outputs 4m..4m+3 (as doubles
+ * (u >> 11) * 2^-53): centre (floor(u0 nx), floor(u1 ny), floor(u2 nz)),
+ * radius r_min + (r_max - r_min) u3; it is accepted when its minimum-image
+ * distance to every accepted centre is >= max(min_spacing, r_a + r_b +
+ * min_gap).  Pure host function; writes n bubbles to out.  Errors: EINVAL
+ * (bad sizes), ESTATE (fewer than n accepted within max_tries; *out holds
+ * the accepted ones and *got their count). */
+lbm_status lbm_sample_sites(int64_t nx, int64_t ny, int64_t nz, int32_t n,
+                            double r_min, double r_max, double min_spacing,
+                            double min_gap, uint64_t seed, int64_t max_tries,
+                            lbm_bubble *out, int32_t *got);
+
+/* Initial state (Sec. 3.1: nucleation sites in liquid): with s = min over
+ * bubbles of (minimum-image distance - r),
+ *   rho = rho_g + (rho_l - rho_g)/2 (1 + tanh(2 s / width))
+ * (rho = rho_l when n = 0), plus noise_amp*(2u - 1) with u the SplitMix64
+ * output at the cell's linear index keyed by seed ^ 0x6E6F697365000000, then
+ * f_i = w_i rho (equilibrium at rest).  The bubble centres, rounded to the
+ * nearest cell, become the injection sites (in order).  Resets the step
+ * counter, disables injection and clears the label history.  b is a host
+ * array of n bubbles (may be NULL when n = 0).  Errors: EINVAL. */
+lbm_status lbm_seed_bubbles(lbm_ctx *ctx, const lbm_bubble *b, int32_t n,
+                            double rho_l, double rho_g, double width,
+                            double noise_amp, uint64_t seed);
+
+/* Virtual blowing agent (Sec. 3: gas added to each bubble every step until
+ * the agent is finished).  rate[s] and budget[s] (host, n = number of seeded
+ * bubbles) set, per site s, the mass added per step and the total left:
+ * each step dm = min(rate, budget), budget -= dm (FP64), and w_i*dm is added
+ * to f*_i at the site cell after collision.  n = 0 disables injection.
+ * Errors: EINVAL (n not 0 or the seeded count, negative values). */
+lbm_status lbm_inject(lbm_ctx *ctx, const double *rate, const double *budget,
+                      int32_t n);
+
+/* Copy the remaining FP64 budgets (n = number of sites) to host. */
+lbm_status lbm_read_budgets(lbm_ctx *ctx, double *budget, int32_t n);
+
+/* Advance nsteps time steps (asynchronous on the context stream).  Errors:
+ * ESTATE (not seeded), EINVAL (nsteps < 0), ECUDA, or a sticky ETIMEOUT from
+ * an earlier step. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Number of steps taken since seeding. */
+int64_t lbm_step_count(const lbm_ctx *ctx);
+
+/* Wait for all work of the context; reports device-side timeouts. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Rupture criterion of Sec. 3.1 / Sec. 4: second derivative of the EOS
+ * pressure (computed in FP64 from the current populations).  line == NULL:
+ * out receives the full periodic Laplacian (count must be N).  Otherwise
+ * line = {x, y, z, axis, len}: out[m] = p(x+e) - 2p(x) + p(x-e) at the len
+ * cells (x, y, z) + m*e_axis (periodic; axis 0, 1 or 2; count must be len).
+ * Synchronous.  Errors: EINVAL, ESTATE, ENUMERIC (non-finite density). */
+lbm_status lbm_pressure_laplacian(lbm_ctx *ctx, double *out, int64_t count,
+                                  const int64_t *line);
+
+/* Gas connected-component labelling: gas cells are rho < gas_threshold
+ * (FP64 density), face-connected (4 in 2-D, 6 in 3-D) with periodic wrap;
+ * each gas cell gets the smallest linear index of its component, liquid
+ * cells -1.  labels: host array of N int32 or NULL; *ncomp receives the
+ * number of components (may be NULL).  Synchronous. */
+lbm_status lbm_label_gas(lbm_ctx *ctx, int32_t *labels, int64_t *ncomp);
+
+/* Label of each injection site's cell after the last lbm_label_gas (-1 when
+ * the cell is liquid), and the number of merge events so far: a merge event
+ * is a pair of sites whose labels differed at the previous labelling and
+ * are equal now (both gas).  site_labels may be NULL. */
+lbm_status lbm_site_labels(lbm_ctx *ctx, int32_t *site_labels, int32_t n,
+                           int64_t *merge_events);
+
+/* FP64 totals: out[0] = sum rho, out[1..3] = sum j (all cells, velocity
+ * order within a cell, fixed-order block reduction).  Synchronous. */
+lbm_status lbm_totals(lbm_ctx *ctx, double out[4]);
+
+/* Copy a field (doubles, see lbm_field) to host; bytes must be exactly the
+ * field's size.  Synchronous. */
+lbm_status lbm_read(lbm_ctx *ctx, int32_t field, double *host_dst, size_t bytes);
+
+/* Overwrite the populations with host data f[i*N + cell] (doubles, rounded
+ * to the storage precision); marks the context seeded.  bytes = Q*N*8. */
+lbm_status lbm_write_f(lbm_ctx *ctx, const double *host_src, size_t bytes);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *lbm_last_error(void);
+
+/* Library version string. */
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCLBM_LBM_H */

@@ -1,0 +1,692 @@
+// C ABI of the library: context management, host-side bookkeeping
+// (nucleation sites, injection buckets, merge events) and the calls that
+// enqueue the kernels.  See include/lbm.h for the contract of every entry
+// point.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "lattice.cuh"
+#include "lbm.h"
+
+using namespace sclbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      cudaGetLastError();                                                                    \
+      return fail(LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    }                                                                                        \
+  } while (0)
+#define CKS(expr)                       \
+  do {                                  \
+    lbm_status s_ = (expr);             \
+    if (s_ != LBM_OK) return s_;        \
+  } while (0)
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_config cfg;
+  int lat = 0, st = 0, Q = 0;
+  View v{};
+  int64_t N = 0;
+  cudaStream_t s = nullptr;
+  int device = 0;
+  size_t lat_bytes = 0;
+  DevBuf fA, fB;
+  int cur = 0;  // 0: state in fA, 1: state in fB
+  bool seeded = false;
+  int64_t steps = 0;
+  lbm_status sticky = LBM_OK;
+  // nucleation sites (user coordinates) and their cells in the view
+  std::vector<lbm_bubble> bubbles;
+  std::vector<int32_t> sx, sy, sz;
+  int32_t ninj = 0;  // > 0 while injection is on
+  DevBuf d_sx, d_sy, d_sz, d_rate, d_budget, d_goff, d_gsite, d_boff, d_blist, d_cells, d_bub;
+  int32_t ngroups = 0;
+  // fused kernel
+  int kernel = LBM_KERNEL_FUSED;
+  FusedPlan plan{};
+  CUtensorMap tmA{}, tmB{};
+  DevBuf psi_scratch;
+  // diagnostics
+  DevBuf d_err, d_rho, d_p, d_tmp, d_j, d_u, d_labels, d_ncomp, d_part, d_tot, d_site_lab;
+  std::vector<int32_t> site_labels, prev_site_labels;
+  bool have_prev = false;
+  int64_t merge_events = 0;
+};
+
+namespace {
+
+void dfree(lbm_ctx *c, DevBuf &b) {
+  if (!b.p) return;
+  if (c->cfg.alloc && c->cfg.free)
+    c->cfg.free(b.p, b.bytes, c->s, c->cfg.alloc_user);
+  else if (!c->cfg.alloc)
+    cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+lbm_status dalloc(lbm_ctx *c, DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.p && b.bytes >= bytes) return LBM_OK;
+  dfree(c, b);
+  void *p = nullptr;
+  if (c->cfg.alloc) {
+    p = c->cfg.alloc(bytes, c->s, c->cfg.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (!p) return fail(LBM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  b.p = p;
+  b.bytes = bytes;
+  return LBM_OK;
+}
+
+template <typename T>
+lbm_status upload(lbm_ctx *c, DevBuf &b, const std::vector<T> &h) {
+  CKS(dalloc(c, b, h.size() * sizeof(T)));
+  if (!h.empty()) CK(cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->s));
+  return LBM_OK;
+}
+
+int64_t wrap64(int64_t a, int64_t n) {
+  int64_t r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): k-th output of the generator whose
+// state starts at key.
+uint64_t splitmix64_at(uint64_t key, uint64_t k) {
+  uint64_t z = key + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double unit_at(uint64_t key, uint64_t k) {
+  return (double)(splitmix64_at(key, k) >> 11) * (1.0 / 9007199254740992.0);
+}
+double min_image(double d, double n) {
+  d = std::fmod(d, n);
+  if (d < 0) d += n;
+  if (d > 0.5 * n) d -= n;
+  return d;
+}
+
+lbm_status check_sticky(lbm_ctx *c) {
+  if (c->sticky != LBM_OK) return fail(c->sticky, "an earlier device error is pending on this context");
+  return LBM_OK;
+}
+
+// Read and clear nothing: report the device status word after a sync.
+lbm_status sync_and_check(lbm_ctx *c) {
+  CK(cudaStreamSynchronize(c->s));
+  int err = 0;
+  CK(cudaMemcpy(&err, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err & ERR_TMA_TIMEOUT) {
+    c->sticky = LBM_ETIMEOUT;
+    return fail(LBM_ETIMEOUT, "a step kernel gave up waiting for a TMA transfer");
+  }
+  if (err & ERR_NONFINITE) {
+    const int zero = 0;
+    CK(cudaMemcpy(c->d_err.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    return fail(LBM_ENUMERIC, "non-finite density found");
+  }
+  return LBM_OK;
+}
+
+void *lattice_ptr(lbm_ctx *c, int which) { return which == 0 ? c->fA.p : c->fB.p; }
+
+lbm_status build_buckets(lbm_ctx *c) {
+  // per fused work item, the sites it owns sorted by (z, site index)
+  const int n = (int)c->sx.size();
+  std::vector<std::pair<std::pair<int, int>, int>> keyed;
+  keyed.reserve(n);
+  for (int s = 0; s < n; ++s)
+    keyed.push_back({{fused_item_of(c->plan, c->sx[s], c->sy[s], c->sz[s]), c->sz[s]}, s});
+  std::sort(keyed.begin(), keyed.end());
+  std::vector<int32_t> off(c->plan.items + 1, 0), list(n);
+  for (int q = 0; q < n; ++q) {
+    off[keyed[q].first.first + 1]++;
+    list[q] = keyed[q].second;
+  }
+  for (int it = 0; it < c->plan.items; ++it) off[it + 1] += off[it];
+  CKS(upload(c, c->d_boff, off));
+  CKS(upload(c, c->d_blist, list));
+  return LBM_OK;
+}
+
+lbm_status ensure_diag(lbm_ctx *c) {
+  const size_t nd = (size_t)c->N * sizeof(double);
+  CKS(dalloc(c, c->d_rho, nd));
+  CKS(dalloc(c, c->d_p, nd));
+  CKS(dalloc(c, c->d_tmp, nd));
+  CKS(dalloc(c, c->d_part, 4 * sizeof(double) * diag_totals_blocks()));
+  CKS(dalloc(c, c->d_tot, 4 * sizeof(double)));
+  CKS(dalloc(c, c->d_ncomp, sizeof(unsigned long long)));
+  return LBM_OK;
+}
+
+lbm_status set_device(lbm_ctx *c) {
+  int d = -1;
+  CK(cudaGetDevice(&d));
+  if (d != c->device) CK(cudaSetDevice(c->device));
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ---- gather/scatter of one population (diag.cu) ----------------------------
+namespace sclbm {
+cudaError_t diag_gather_pop(const View &v, const void *stored, int i, double *out, cudaStream_t s);
+cudaError_t diag_store_pop(const View &v, const double *f, int i, void *stored, cudaStream_t s);
+}  // namespace sclbm
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+const char *lbm_version(void) { return "sclbm-gb300 0.1 (sm_103a)"; }
+
+void lbm_config_default(lbm_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->lattice = LBM_D3Q19;
+  cfg->storage = LBM_F32;
+  cfg->nx = cfg->ny = cfg->nz = 64;
+  cfg->tau = 1.0;
+  cfg->G = -5.0;
+  cfg->rho0 = 1.0;
+  cfg->rho_ref = 1.0;
+  cfg->gas_threshold = 1.0;
+  cfg->kernel = LBM_KERNEL_AUTO;
+  cfg->tile = 0;
+}
+
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(LBM_EINVAL, "cfg is NULL");
+  if (cfg->lattice != LBM_D2Q9 && cfg->lattice != LBM_D3Q19) return fail(LBM_EINVAL, "unknown lattice");
+  if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16_OFFSET) return fail(LBM_EINVAL, "unknown storage");
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(LBM_EINVAL, "extents must be >= 1");
+  if (cfg->lattice == LBM_D2Q9 && cfg->nz != 1) return fail(LBM_EINVAL, "D2Q9 needs nz == 1");
+  if (cfg->nx > (1 << 20) || cfg->ny > (1 << 20) || cfg->nz > (1 << 20) ||
+      cfg->nx * cfg->ny * cfg->nz > ((int64_t)1 << 31) - 1)
+    return fail(LBM_EINVAL, "lattice too large (cells must fit int32 labels)");
+  if (!(cfg->tau > 0.5) || !std::isfinite(cfg->tau)) return fail(LBM_EINVAL, "tau must be > 0.5");
+  if (!(cfg->rho0 > 0) || !std::isfinite(cfg->G)) return fail(LBM_EINVAL, "rho0 must be > 0, G finite");
+  if (cfg->kernel < LBM_KERNEL_AUTO || cfg->kernel > LBM_KERNEL_TWO_PASS)
+    return fail(LBM_EINVAL, "unknown kernel");
+  if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+    return fail(LBM_EINVAL, "alloc and free callbacks must be given together");
+
+  lbm_ctx *c = new lbm_ctx();
+  c->cfg = *cfg;
+  c->lat = cfg->lattice == LBM_D2Q9 ? D2Q9 : D3Q19;
+  c->st = cfg->storage;
+  c->Q = c->lat == D3Q19 ? 19 : 9;
+  c->s = static_cast<cudaStream_t>(cfg->stream);
+  c->v.lat = c->lat;
+  c->v.st = c->st;
+  if (c->lat == D2Q9) {  // view (nx, 1, ny)
+    c->v.NX = cfg->nx;
+    c->v.NY = 1;
+    c->v.NZ = cfg->ny;
+  } else {
+    c->v.NX = cfg->nx;
+    c->v.NY = cfg->ny;
+    c->v.NZ = cfg->nz;
+  }
+  c->v.px = (c->v.NX + 7) / 8 * 8;
+  c->v.rho_ref = cfg->rho_ref;
+  c->N = c->v.NX * c->v.NY * c->v.NZ;
+  c->kernel = cfg->kernel == LBM_KERNEL_TWO_PASS ? LBM_KERNEL_TWO_PASS : LBM_KERNEL_FUSED;
+  c->lat_bytes = (size_t)c->Q * c->v.px * c->v.NY * c->v.NZ * storage_bytes(c->st);
+
+  auto bail = [&](lbm_status st) {
+    lbm_destroy(c);
+    return st;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(LBM_ECUDA, "no CUDA device");
+  }
+  lbm_status st;
+  if ((st = dalloc(c, c->fA, c->lat_bytes)) != LBM_OK) return bail(st);
+  if ((st = dalloc(c, c->fB, c->lat_bytes)) != LBM_OK) return bail(st);
+  if ((st = dalloc(c, c->d_err, sizeof(int))) != LBM_OK) return bail(st);
+  if (cudaMemsetAsync(c->d_err.p, 0, sizeof(int), c->s) != cudaSuccess ||
+      cudaMemsetAsync(c->fA.p, 0, c->lat_bytes, c->s) != cudaSuccess ||
+      cudaMemsetAsync(c->fB.p, 0, c->lat_bytes, c->s) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LBM_ECUDA, "memset failed"));
+  }
+  if (c->kernel == LBM_KERNEL_FUSED) {
+    cudaError_t e = fused_make_plan(c->lat, c->st, cfg->tile, c->v.NX, c->v.NY, c->v.NZ, 0, &c->plan);
+    if (e != cudaSuccess) return bail(fail(LBM_EINVAL, "tile does not fit this lattice/storage"));
+    e = fused_prepare(c->lat, c->st, c->plan);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(LBM_ECUDA, std::string("fused kernel set-up: ") + cudaGetErrorString(e)));
+    }
+    if (fused_encode_tmap(c->lat, c->st, c->plan, c->fA.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px,
+                          &c->tmA) != CUDA_SUCCESS ||
+        fused_encode_tmap(c->lat, c->st, c->plan, c->fB.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px,
+                          &c->tmB) != CUDA_SUCCESS)
+      return bail(fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed"));
+  } else {
+    const size_t cs = c->st == LBM_F64 ? 8 : 4;
+    if ((st = dalloc(c, c->psi_scratch, (size_t)c->N * cs)) != LBM_OK) return bail(st);
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->s);
+  cudaGetLastError();
+  DevBuf *bufs[] = {&c->fA,     &c->fB,     &c->d_sx,    &c->d_sy,   &c->d_sz,     &c->d_rate,
+                    &c->d_budget, &c->d_goff, &c->d_gsite, &c->d_boff, &c->d_blist, &c->d_cells, &c->d_bub,
+                    &c->psi_scratch, &c->d_err, &c->d_rho, &c->d_p, &c->d_tmp, &c->d_j, &c->d_u,
+                    &c->d_labels, &c->d_ncomp, &c->d_part, &c->d_tot, &c->d_site_lab};
+  for (DevBuf *b : bufs) dfree(c, *b);
+  delete c;
+}
+
+lbm_status lbm_sample_sites(int64_t nx, int64_t ny, int64_t nz, int32_t n, double r_min,
+                            double r_max, double min_spacing, double min_gap, uint64_t seed,
+                            int64_t max_tries, lbm_bubble *out, int32_t *got) {
+  if (got) *got = 0;
+  if (nx < 1 || ny < 1 || nz < 1 || n < 0 || (n > 0 && !out) || max_tries < 0 ||
+      !(r_max >= r_min))
+    return fail(LBM_EINVAL, "bad arguments to lbm_sample_sites");
+  const uint64_t key = seed ^ 0x7369746573000000ull;
+  int32_t k = 0;
+  for (int64_t m = 0; m < max_tries && k < n; ++m) {
+    lbm_bubble b;
+    b.x = std::floor(unit_at(key, 4 * (uint64_t)m + 0) * (double)nx);
+    b.y = std::floor(unit_at(key, 4 * (uint64_t)m + 1) * (double)ny);
+    b.z = std::floor(unit_at(key, 4 * (uint64_t)m + 2) * (double)nz);
+    b.r = r_min + (r_max - r_min) * unit_at(key, 4 * (uint64_t)m + 3);
+    bool ok = true;
+    for (int32_t a = 0; a < k && ok; ++a) {
+      const double dx = min_image(b.x - out[a].x, (double)nx);
+      const double dy = min_image(b.y - out[a].y, (double)ny);
+      const double dz = min_image(b.z - out[a].z, (double)nz);
+      const double need = std::max(min_spacing, b.r + out[a].r + min_gap);
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) < need) ok = false;
+    }
+    if (ok) out[k++] = b;
+  }
+  if (got) *got = k;
+  if (k < n) return fail(LBM_ESTATE, "only " + std::to_string(k) + " of " + std::to_string(n) + " sites fit");
+  return LBM_OK;
+}
+
+lbm_status lbm_seed_bubbles(lbm_ctx *c, const lbm_bubble *b, int32_t n, double rho_l,
+                            double rho_g, double width, double noise_amp, uint64_t seed) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (n < 0 || (n > 0 && !b)) return fail(LBM_EINVAL, "bad bubble list");
+  if (!(width > 0) || !std::isfinite(rho_l) || !std::isfinite(rho_g) || !std::isfinite(noise_amp))
+    return fail(LBM_EINVAL, "width must be > 0, densities finite");
+  for (int32_t k = 0; k < n; ++k)
+    if (!std::isfinite(b[k].x) || !std::isfinite(b[k].y) || !std::isfinite(b[k].z) ||
+        !std::isfinite(b[k].r))
+      return fail(LBM_EINVAL, "non-finite bubble");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  c->bubbles.assign(b, b + n);
+  c->sx.resize(n);
+  c->sy.resize(n);
+  c->sz.resize(n);
+  std::vector<double> vb(4 * (size_t)std::max(n, 1));
+  for (int32_t k = 0; k < n; ++k) {
+    double vx = b[k].x, vy = b[k].y, vz = b[k].z;
+    if (c->lat == D2Q9) {  // user (x, y) -> view (x, 0, y)
+      vz = b[k].y;
+      vy = 0.0;
+    }
+    vb[4 * k + 0] = vx;
+    vb[4 * k + 1] = vy;
+    vb[4 * k + 2] = vz;
+    vb[4 * k + 3] = b[k].r;
+    c->sx[k] = (int32_t)wrap64((int64_t)std::floor(vx + 0.5), c->v.NX);
+    c->sy[k] = (int32_t)wrap64((int64_t)std::floor(vy + 0.5), c->v.NY);
+    c->sz[k] = (int32_t)wrap64((int64_t)std::floor(vz + 0.5), c->v.NZ);
+  }
+  CKS(ensure_diag(c));
+  CKS(upload(c, c->d_bub, vb));
+  CK(diag_init_rho(c->v, static_cast<const double *>(c->d_bub.p), n, rho_l, rho_g, width, noise_amp,
+                   seed, static_cast<double *>(c->d_rho.p), c->s));
+  c->cur = 0;
+  CK(diag_store_from_rho(c->v, static_cast<const double *>(c->d_rho.p), lattice_ptr(c, 0), c->s));
+  // site cells (view linear index) for label look-ups
+  std::vector<int32_t> cells(n);
+  for (int32_t k = 0; k < n; ++k)
+    cells[k] = (int32_t)(((int64_t)c->sz[k] * c->v.NY + c->sy[k]) * c->v.NX + c->sx[k]);
+  CKS(upload(c, c->d_cells, cells));
+  CKS(upload(c, c->d_sx, c->sx));
+  CKS(upload(c, c->d_sy, c->sy));
+  CKS(upload(c, c->d_sz, c->sz));
+  c->ninj = 0;
+  c->steps = 0;
+  c->seeded = true;
+  c->have_prev = false;
+  c->merge_events = 0;
+  c->site_labels.assign(n, -1);
+  CK(cudaStreamSynchronize(c->s));  // host staging buffers go out of scope
+  return LBM_OK;
+}
+
+lbm_status lbm_inject(lbm_ctx *c, const double *rate, const double *budget, int32_t n) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  if (n == 0) {
+    c->ninj = 0;
+    return LBM_OK;
+  }
+  if (n != (int32_t)c->sx.size() || !rate || !budget)
+    return fail(LBM_EINVAL, "n must be 0 or the number of seeded bubbles");
+  for (int32_t k = 0; k < n; ++k)
+    if (!(rate[k] >= 0) || !(budget[k] >= 0) || !std::isfinite(rate[k]) || !std::isfinite(budget[k]))
+      return fail(LBM_EINVAL, "rates and budgets must be finite and >= 0");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  std::vector<double> r(rate, rate + n), bgt(budget, budget + n);
+  // groups of sites sharing a cell, in site order (two-pass injection kernel)
+  std::map<int64_t, std::vector<int32_t>> by_cell;
+  for (int32_t k = 0; k < n; ++k)
+    by_cell[((int64_t)c->sz[k] * c->v.NY + c->sy[k]) * c->v.NX + c->sx[k]].push_back(k);
+  std::vector<int32_t> goff(1, 0), gsite;
+  for (auto &kv : by_cell) {
+    gsite.insert(gsite.end(), kv.second.begin(), kv.second.end());
+    goff.push_back((int32_t)gsite.size());
+  }
+  c->ngroups = (int32_t)by_cell.size();
+  CKS(upload(c, c->d_rate, r));
+  CKS(upload(c, c->d_budget, bgt));
+  CKS(upload(c, c->d_goff, goff));
+  CKS(upload(c, c->d_gsite, gsite));
+  if (c->kernel == LBM_KERNEL_FUSED) CKS(build_buckets(c));
+  CK(cudaStreamSynchronize(c->s));
+  c->ninj = n;
+  return LBM_OK;
+}
+
+lbm_status lbm_read_budgets(lbm_ctx *c, double *budget, int32_t n) {
+  if (!c || !budget) return fail(LBM_EINVAL, "NULL argument");
+  if (n != c->ninj) return fail(LBM_EINVAL, "n must equal the number of injection sites");
+  if (n == 0) return LBM_OK;
+  CKS(set_device(c));
+  CK(cudaMemcpyAsync(budget, c->d_budget.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s));
+  return sync_and_check(c);
+}
+
+lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(check_sticky(c));
+  CKS(set_device(c));
+  StepArgs a{};
+  a.NX = c->v.NX;
+  a.NY = c->v.NY;
+  a.NZ = c->v.NZ;
+  a.px = c->v.px;
+  a.tau = c->cfg.tau;
+  a.G = c->cfg.G;
+  a.rho0 = c->cfg.rho0;
+  a.rho_ref = c->cfg.rho_ref;
+  a.nsites = c->ninj;
+  a.site_x = static_cast<const int32_t *>(c->d_sx.p);
+  a.site_y = static_cast<const int32_t *>(c->d_sy.p);
+  a.site_z = static_cast<const int32_t *>(c->d_sz.p);
+  a.rate = static_cast<const double *>(c->d_rate.p);
+  a.budget = static_cast<double *>(c->d_budget.p);
+  a.ngroups = c->ngroups;
+  a.group_off = static_cast<const int32_t *>(c->d_goff.p);
+  a.group_site = static_cast<const int32_t *>(c->d_gsite.p);
+  a.bucket_off = static_cast<const int32_t *>(c->d_boff.p);
+  a.bucket_site = static_cast<const int32_t *>(c->d_blist.p);
+  a.err = static_cast<int *>(c->d_err.p);
+  for (int64_t t = 0; t < nsteps; ++t) {
+    a.fin = lattice_ptr(c, c->cur);
+    a.fout = lattice_ptr(c, 1 - c->cur);
+    cudaError_t e;
+    if (c->kernel == LBM_KERNEL_FUSED)
+      e = fused_launch(c->lat, c->st, c->plan, a, c->cur == 0 ? c->tmA : c->tmB, c->s);
+    else
+      e = twopass_launch(c->lat, c->st, a, c->psi_scratch.p, c->s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->sticky = LBM_ECUDA;
+      return fail(LBM_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    }
+    c->cur = 1 - c->cur;
+    ++c->steps;
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+lbm_status lbm_sync(lbm_ctx *c) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  CKS(set_device(c));
+  return sync_and_check(c);
+}
+
+static lbm_status compute_pressure(lbm_ctx *c) {
+  CKS(ensure_diag(c));
+  CK(diag_moments(c->v, lattice_ptr(c, c->cur), c->cfg.G, c->cfg.rho0,
+                  static_cast<double *>(c->d_rho.p), nullptr, nullptr, nullptr, nullptr,
+                  static_cast<double *>(c->d_p.p), static_cast<int *>(c->d_err.p), c->s));
+  return LBM_OK;
+}
+
+lbm_status lbm_pressure_laplacian(lbm_ctx *c, double *out, int64_t count, const int64_t *line) {
+  if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  if (!line) {
+    if (count != c->N) return fail(LBM_EINVAL, "count must be N for the full Laplacian");
+  } else {
+    if (line[3] < 0 || line[3] > 2 || line[4] < 0 || count != line[4])
+      return fail(LBM_EINVAL, "line = {x, y, z, axis (0..2), len}, count = len");
+    if (c->lat == D2Q9 && (line[3] == 2 || line[2] != 0))
+      return fail(LBM_EINVAL, "2-D lattice: axis must be 0 or 1 and z 0");
+  }
+  CKS(compute_pressure(c));
+  double *tmp = static_cast<double *>(c->d_tmp.p);
+  if (!line) {
+    CK(diag_laplacian(c->v, static_cast<const double *>(c->d_p.p), tmp, c->s));
+  } else {
+    int64_t x0 = line[0], y0 = line[1], z0 = line[2];
+    int axis = (int)line[3];
+    if (c->lat == D2Q9) {  // user (x, y) -> view (x, 0, y)
+      z0 = y0;
+      y0 = 0;
+      axis = axis == 1 ? 2 : 0;
+    }
+    if (line[4] > 0)
+      CK(diag_line_d2(c->v, static_cast<const double *>(c->d_p.p), wrap64(x0, c->v.NX),
+                      wrap64(y0, c->v.NY), wrap64(z0, c->v.NZ), axis, line[4], tmp, c->s));
+  }
+  if (count > 0)
+    CK(cudaMemcpyAsync(out, tmp, sizeof(double) * count, cudaMemcpyDeviceToHost, c->s));
+  return sync_and_check(c);
+}
+
+lbm_status lbm_label_gas(lbm_ctx *c, int32_t *labels, int64_t *ncomp) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(compute_pressure(c));
+  CKS(dalloc(c, c->d_labels, sizeof(int32_t) * c->N));
+  CK(diag_label(c->v, static_cast<const double *>(c->d_rho.p), c->cfg.gas_threshold,
+                static_cast<int32_t *>(c->d_labels.p),
+                static_cast<unsigned long long *>(c->d_ncomp.p), c->s));
+  const int32_t ns = (int32_t)c->sx.size();
+  if (ns > 0) {
+    CKS(dalloc(c, c->d_site_lab, sizeof(int32_t) * ns));
+    CK(diag_gather_labels(static_cast<const int32_t *>(c->d_labels.p),
+                          static_cast<const int32_t *>(c->d_cells.p), ns,
+                          static_cast<int32_t *>(c->d_site_lab.p), c->s));
+    c->site_labels.resize(ns);
+    CK(cudaMemcpyAsync(c->site_labels.data(), c->d_site_lab.p, sizeof(int32_t) * ns,
+                       cudaMemcpyDeviceToHost, c->s));
+  }
+  unsigned long long nc = 0;
+  CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
+  if (labels)
+    CK(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost, c->s));
+  CKS(sync_and_check(c));
+  if (ncomp) *ncomp = (int64_t)nc;
+  // merge events: pairs of sites with different labels before, equal now
+  if (ns > 0) {
+    if (c->have_prev) {
+      std::map<int32_t, std::map<int32_t, int64_t>> groups;  // now -> prev -> count
+      for (int32_t k = 0; k < ns; ++k)
+        if (c->site_labels[k] >= 0) groups[c->site_labels[k]][c->prev_site_labels[k]]++;
+      for (auto &g : groups) {
+        int64_t tot = 0, same = 0;
+        for (auto &p : g.second) {
+          tot += p.second;
+          same += p.second * (p.second - 1) / 2;
+        }
+        c->merge_events += tot * (tot - 1) / 2 - same;
+      }
+    }
+    c->prev_site_labels = c->site_labels;
+    c->have_prev = true;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_site_labels(lbm_ctx *c, int32_t *site_labels, int32_t n, int64_t *merge_events) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (site_labels) {
+    if (n != (int32_t)c->site_labels.size()) return fail(LBM_EINVAL, "n must equal the number of sites");
+    std::copy(c->site_labels.begin(), c->site_labels.end(), site_labels);
+  }
+  if (merge_events) *merge_events = c->merge_events;
+  return LBM_OK;
+}
+
+lbm_status lbm_totals(lbm_ctx *c, double out[4]) {
+  if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(ensure_diag(c));
+  CK(diag_totals(c->v, lattice_ptr(c, c->cur), static_cast<double *>(c->d_part.p),
+                 static_cast<double *>(c->d_tot.p), c->s));
+  CK(cudaMemcpyAsync(out, c->d_tot.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  return sync_and_check(c);
+}
+
+lbm_status lbm_read(lbm_ctx *c, int32_t field, double *dst, size_t bytes) {
+  if (!c || !dst) return fail(LBM_EINVAL, "NULL argument");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  const size_t nd = (size_t)c->N * sizeof(double);
+  size_t need;
+  switch (field) {
+    case LBM_RHO: case LBM_PSI: case LBM_P: case LBM_LAPP: need = nd; break;
+    case LBM_U: need = 3 * nd; break;
+    case LBM_F: need = (size_t)c->Q * nd; break;
+    default: return fail(LBM_EINVAL, "unknown field");
+  }
+  if (bytes != need) return fail(LBM_EINVAL, "bytes must be " + std::to_string(need));
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(ensure_diag(c));
+  double *rho = static_cast<double *>(c->d_rho.p), *p = static_cast<double *>(c->d_p.p),
+         *tmp = static_cast<double *>(c->d_tmp.p);
+  int *err = static_cast<int *>(c->d_err.p);
+  const void *cur = lattice_ptr(c, c->cur);
+  switch (field) {
+    case LBM_RHO:
+      CK(diag_moments(c->v, cur, c->cfg.G, c->cfg.rho0, rho, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, err, c->s));
+      CK(cudaMemcpyAsync(dst, rho, nd, cudaMemcpyDeviceToHost, c->s));
+      break;
+    case LBM_PSI:
+      CK(diag_moments(c->v, cur, c->cfg.G, c->cfg.rho0, nullptr, nullptr, nullptr, nullptr, tmp,
+                      nullptr, err, c->s));
+      CK(cudaMemcpyAsync(dst, tmp, nd, cudaMemcpyDeviceToHost, c->s));
+      break;
+    case LBM_P:
+      CKS(compute_pressure(c));
+      CK(cudaMemcpyAsync(dst, p, nd, cudaMemcpyDeviceToHost, c->s));
+      break;
+    case LBM_LAPP:
+      CKS(compute_pressure(c));
+      CK(diag_laplacian(c->v, p, tmp, c->s));
+      CK(cudaMemcpyAsync(dst, tmp, nd, cudaMemcpyDeviceToHost, c->s));
+      break;
+    case LBM_U: {
+      CKS(dalloc(c, c->d_j, 3 * nd));
+      double *j = static_cast<double *>(c->d_j.p);
+      CK(diag_moments(c->v, cur, c->cfg.G, c->cfg.rho0, rho, j, j + c->N, j + 2 * c->N, p, nullptr,
+                      err, c->s));
+      CKS(dalloc(c, c->d_u, 3 * nd));  // p holds psi here
+      CK(diag_velocity(c->v, c->cfg.G, rho, j, j + c->N, j + 2 * c->N, p,
+                       static_cast<double *>(c->d_u.p), c->s));
+      CK(cudaMemcpyAsync(dst, c->d_u.p, 3 * nd, cudaMemcpyDeviceToHost, c->s));
+      break;
+    }
+    case LBM_F:
+      for (int i = 0; i < c->Q; ++i) {
+        CK(diag_gather_pop(c->v, cur, i, tmp, c->s));
+        CK(cudaMemcpyAsync(dst + (size_t)i * c->N, tmp, nd, cudaMemcpyDeviceToHost, c->s));
+      }
+      break;
+  }
+  return sync_and_check(c);
+}
+
+lbm_status lbm_write_f(lbm_ctx *c, const double *src, size_t bytes) {
+  if (!c || !src) return fail(LBM_EINVAL, "NULL argument");
+  const size_t nd = (size_t)c->N * sizeof(double);
+  if (bytes != (size_t)c->Q * nd) return fail(LBM_EINVAL, "bytes must be Q*N*8");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(ensure_diag(c));
+  double *tmp = static_cast<double *>(c->d_tmp.p);
+  for (int i = 0; i < c->Q; ++i) {
+    CK(cudaMemcpyAsync(tmp, src + (size_t)i * c->N, nd, cudaMemcpyHostToDevice, c->s));
+    CK(diag_store_pop(c->v, tmp, i, lattice_ptr(c, c->cur), c->s));
+  }
+  CK(cudaStreamSynchronize(c->s));
+  c->seeded = true;
+  return LBM_OK;
+}
+
+}  // extern "C"

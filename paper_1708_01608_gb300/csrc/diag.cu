@@ -1,0 +1,539 @@
+// State conversion and diagnostics kernels, all in FP64 arithmetic:
+// initial state, population gather/scatter, moments, EOS pressure and its
+// Laplacian (the rupture criterion of Sec. 3.1 / Sec. 4 of the paper), FP64
+// totals, and connected-component labelling of gas cells.
+//
+// Stored populations are in pull form: stored_i(y) = f_i(y + c_i).
+#include <type_traits>
+
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace sclbm {
+
+namespace {
+
+struct Idx {
+  int x, y, z;
+};
+__device__ __forceinline__ Idx idx_of(int64_t k, const View &v) {
+  Idx c;
+  c.x = (int)(k % v.NX);
+  const int64_t r = k / v.NX;
+  c.y = (int)(r % v.NY);
+  c.z = (int)(r / v.NY);
+  return c;
+}
+__device__ __forceinline__ int wr(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+__device__ __forceinline__ int64_t lin(int x, int y, int z, const View &v) {
+  return ((int64_t)z * v.NY + y) * v.NX + x;
+}
+__device__ __forceinline__ int64_t sidx(int i, int x, int y, int z, const View &v) {
+  return (int64_t)i * v.px * v.NY * v.NZ + ((int64_t)z * v.NY + y) * v.px + x;
+}
+
+template <int ST>
+__device__ __forceinline__ double load_d(const void *p, int64_t k, double wref) {
+  using S = Storage<ST>;
+  return (double)S::load(static_cast<const typename S::T *>(p)[k], (typename S::C)wref);
+}
+template <int ST>
+__device__ __forceinline__ void store_d(void *p, int64_t k, double v, double wref) {
+  using S = Storage<ST>;
+  using C = typename S::C;
+  static_cast<typename S::T *>(p)[k] = S::store((C)v, (C)wref);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): the k-th output of the generator
+// whose state starts at key.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t key, uint64_t k) {
+  uint64_t z = key + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+constexpr int TPB = 256;
+inline int nblocks(int64_t n) {
+  const int64_t b = (n + TPB - 1) / TPB;
+  return (int)(b < 1 ? 1 : (b > 262144 ? 262144 : b));
+}
+#define GRID_LOOP(k, n) \
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (n); \
+       k += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ double min_image(double d, double n) {
+  d = fmod(d, n);
+  if (d < 0) d += n;
+  if (d > 0.5 * n) d -= n;
+  return d;
+}
+
+__global__ void k_init_rho(const View v, const double *bub, int32_t nb, double rho_l,
+                           double rho_g, double width, double amp, uint64_t key, double *rho) {
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+    double r = rho_l;
+    if (nb > 0) {
+      double s = INFINITY;
+      for (int b = 0; b < nb; ++b) {
+        const double dx = min_image((double)c.x - bub[4 * b + 0], (double)v.NX);
+        const double dy = min_image((double)c.y - bub[4 * b + 1], (double)v.NY);
+        const double dz = min_image((double)c.z - bub[4 * b + 2], (double)v.NZ);
+        const double d = sqrt(dx * dx + dy * dy + dz * dz) - bub[4 * b + 3];
+        s = d < s ? d : s;
+      }
+      r = rho_g + 0.5 * (rho_l - rho_g) * (1.0 + tanh(2.0 * s / width));
+    }
+    if (amp != 0.0) {
+      const double u = (double)(splitmix64_at(key, (uint64_t)k) >> 11) * (1.0 / 9007199254740992.0);
+      r += amp * (2.0 * u - 1.0);
+    }
+    rho[k] = r;
+  }
+}
+
+template <int LAT, int ST>
+__global__ void k_store_from(const View v, const double *src, int from_f, void *stored) {
+  using L = Lattice<LAT>;
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      // stored_i(y) = f_i(y + c_i)
+      const int64_t t = lin(wr(c.x + L::cx(i), (int)v.NX), wr(c.y + L::cy(i), (int)v.NY),
+                            wr(c.z + L::cz(i), (int)v.NZ), v);
+      const double val = from_f ? src[(int64_t)i * N + t] : L::w(i) * src[t];
+      store_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), val, L::w(i) * v.rho_ref);
+    }
+  }
+}
+
+template <int LAT, int ST>
+__global__ void k_gather_f(const View v, const void *stored, double *f) {
+  using L = Lattice<LAT>;
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      f[(int64_t)i * N + k] =
+          load_d<ST>(stored,
+                     sidx(i, wr(c.x - L::cx(i), (int)v.NX), wr(c.y - L::cy(i), (int)v.NY),
+                          wr(c.z - L::cz(i), (int)v.NZ), v),
+                     L::w(i) * v.rho_ref);
+  }
+}
+
+// one population: out(x) = f_i(x) = stored_i(x - c_i)
+template <int LAT, int ST>
+__global__ void k_gather_pop(const View v, const void *stored, int i, double *out) {
+  using L = Lattice<LAT>;
+  int cx = 0, cy = 0, cz = 0;
+  double w = 0;
+#pragma unroll
+  for (int m = 0; m < L::Q; ++m)
+    if (m == i) {
+      cx = L::cx(m);
+      cy = L::cy(m);
+      cz = L::cz(m);
+      w = L::w(m);
+    }
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+    out[k] = load_d<ST>(stored,
+                        sidx(i, wr(c.x - cx, (int)v.NX), wr(c.y - cy, (int)v.NY),
+                             wr(c.z - cz, (int)v.NZ), v),
+                        w * v.rho_ref);
+  }
+}
+
+// one population: stored_i(y) = f_i(y + c_i) from canonical f_i (N doubles)
+template <int LAT, int ST>
+__global__ void k_store_pop(const View v, const double *f, int i, void *stored) {
+  using L = Lattice<LAT>;
+  int cx = 0, cy = 0, cz = 0;
+  double w = 0;
+#pragma unroll
+  for (int m = 0; m < L::Q; ++m)
+    if (m == i) {
+      cx = L::cx(m);
+      cy = L::cy(m);
+      cz = L::cz(m);
+      w = L::w(m);
+    }
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+    const int64_t t = lin(wr(c.x + cx, (int)v.NX), wr(c.y + cy, (int)v.NY), wr(c.z + cz, (int)v.NZ), v);
+    store_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), f[t], w * v.rho_ref);
+  }
+}
+
+// per-cell FP64 moments (sum in velocity order) in the view's axes
+template <int LAT, int ST>
+__device__ __forceinline__ void cell_moments(const View &v, const void *stored, const Idx &c,
+                                             double &rho, double &jx, double &jy, double &jz) {
+  using L = Lattice<LAT>;
+  rho = jx = jy = jz = 0.0;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const double f = load_d<ST>(stored,
+                                sidx(i, wr(c.x - L::cx(i), (int)v.NX),
+                                     wr(c.y - L::cy(i), (int)v.NY), wr(c.z - L::cz(i), (int)v.NZ),
+                                     v),
+                                L::w(i) * v.rho_ref);
+    rho += f;
+    jx += L::cx(i) * f;
+    jy += L::cy(i) * f;
+    jz += L::cz(i) * f;
+  }
+}
+
+template <int LAT, int ST>
+__global__ void k_moments(const View v, const void *stored, double G, double rho0, double *rho,
+                          double *jx, double *jy, double *jz, double *psi, double *p, int *err) {
+  const int64_t N = v.NX * v.NY * v.NZ;
+  bool bad = false;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+    double r, a, b, d;
+    cell_moments<LAT, ST>(v, stored, c, r, a, b, d);
+    if (!isfinite(r)) bad = true;
+    const double s = rho0 * (1.0 - exp(-r / rho0));
+    if (rho) rho[k] = r;
+    if (jx) jx[k] = a;
+    if (jy) jy[k] = b;
+    if (jz) jz[k] = d;
+    if (psi) psi[k] = s;
+    if (p) p[k] = r / 3.0 + G / 6.0 * s * s;
+  }
+  if (bad && err) atomicOr(err, ERR_NONFINITE);
+}
+
+template <int LAT>
+__global__ void k_velocity(const View v, double G, const double *rho, const double *jx,
+                           const double *jy, const double *jz, const double *psi, double *u) {
+  using L = Lattice<LAT>;
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+    double sx = 0, sy = 0, sz = 0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+      const double wp = L::w(i) * psi[lin(wr(c.x + L::cx(i), (int)v.NX),
+                                          wr(c.y + L::cy(i), (int)v.NY),
+                                          wr(c.z + L::cz(i), (int)v.NZ), v)];
+      sx += L::cx(i) * wp;
+      sy += L::cy(i) * wp;
+      sz += L::cz(i) * wp;
+    }
+    const double gp = -G * psi[k];
+    const double ux = (jx[k] + 0.5 * gp * sx) / rho[k];
+    const double uy = (jy[k] + 0.5 * gp * sy) / rho[k];
+    const double uz = (jz[k] + 0.5 * gp * sz) / rho[k];
+    if (LAT == D2Q9) {  // view (x, 1, y) -> user (x, y)
+      u[k] = ux;
+      u[N + k] = uz;
+      u[2 * N + k] = 0.0;
+    } else {
+      u[k] = ux;
+      u[N + k] = uy;
+      u[2 * N + k] = uz;
+    }
+  }
+}
+
+__global__ void k_laplacian(const View v, const double *p, double *lap) {
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+    const double pc = p[k];
+    double s = p[lin(wr(c.x + 1, (int)v.NX), c.y, c.z, v)] - 2.0 * pc +
+               p[lin(wr(c.x - 1, (int)v.NX), c.y, c.z, v)];
+    s += p[lin(c.x, wr(c.y + 1, (int)v.NY), c.z, v)] - 2.0 * pc +
+         p[lin(c.x, wr(c.y - 1, (int)v.NY), c.z, v)];
+    s += p[lin(c.x, c.y, wr(c.z + 1, (int)v.NZ), v)] - 2.0 * pc +
+         p[lin(c.x, c.y, wr(c.z - 1, (int)v.NZ), v)];
+    lap[k] = s;
+  }
+}
+
+__global__ void k_line_d2(const View v, const double *p, int x0, int y0, int z0, int axis,
+                          int64_t len, double *out) {
+  GRID_LOOP(m, len) {
+    const int ex = axis == 0, ey = axis == 1, ez = axis == 2;
+    const int x = wr((int)(x0 + m * ex), (int)v.NX), y = wr((int)(y0 + m * ey), (int)v.NY),
+              z = wr((int)(z0 + m * ez), (int)v.NZ);
+    out[m] = p[lin(wr(x + ex, (int)v.NX), wr(y + ey, (int)v.NY), wr(z + ez, (int)v.NZ), v)] -
+             2.0 * p[lin(x, y, z, v)] +
+             p[lin(wr(x - ex, (int)v.NX), wr(y - ey, (int)v.NY), wr(z - ez, (int)v.NZ), v)];
+  }
+}
+
+// Fixed-order FP64 block sums: block b sums a fixed set of cells in a fixed
+// tree, so repeated calls give identical bits.
+constexpr int TOT_BLOCKS = 1024;
+template <int LAT, int ST>
+__global__ void __launch_bounds__(TPB) k_totals(const View v, const void *stored, double *part) {
+  __shared__ double sh[4][TPB];
+  const int64_t N = v.NX * v.NY * v.NZ;
+  double m = 0, a = 0, b = 0, d = 0;
+  for (int64_t k = blockIdx.x * (int64_t)TPB + threadIdx.x; k < N; k += (int64_t)TOT_BLOCKS * TPB) {
+    double r, x, y, z;
+    cell_moments<LAT, ST>(v, stored, idx_of(k, v), r, x, y, z);
+    m += r;
+    a += x;
+    b += y;
+    d += z;
+  }
+  sh[0][threadIdx.x] = m;
+  sh[1][threadIdx.x] = a;
+  sh[2][threadIdx.x] = b;
+  sh[3][threadIdx.x] = d;
+  __syncthreads();
+  for (int w = TPB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 4; ++q) part[4 * blockIdx.x + q] = sh[q][0];
+}
+
+template <int LAT>
+__global__ void __launch_bounds__(TPB) k_totals_final(const double *part, double *out) {
+  __shared__ double sh[4][TPB];
+  double acc[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < TOT_BLOCKS; b += TPB)
+    for (int q = 0; q < 4; ++q) acc[q] += part[4 * b + q];
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = TPB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sh[0][0];
+    out[1] = sh[1][0];
+    if (LAT == D2Q9) {  // view (x, 1, y) -> user (x, y)
+      out[2] = sh[3][0];
+      out[3] = 0.0;
+    } else {
+      out[2] = sh[2][0];
+      out[3] = sh[3][0];
+    }
+  }
+}
+
+// ---- connected components (union-find, links always from the larger root
+// to the smaller, so every root is its component's minimum index) ---------
+__device__ __forceinline__ int32_t uf_find(const int32_t *L, int32_t x) {
+  int32_t p = L[x];
+  while (p != x) {
+    x = p;
+    p = L[x];
+  }
+  return x;
+}
+__device__ __forceinline__ void uf_union(int32_t *L, int32_t a, int32_t b) {
+  bool done = false;
+  while (!done) {
+    a = uf_find(L, a);
+    b = uf_find(L, b);
+    if (a < b) {
+      const int32_t old = atomicMin(&L[b], a);
+      done = old == b;
+      b = old;
+    } else if (b < a) {
+      const int32_t old = atomicMin(&L[a], b);
+      done = old == a;
+      a = old;
+    } else {
+      done = true;
+    }
+  }
+}
+
+__global__ void k_ccl_init(int64_t N, const double *rho, double thr, int32_t *L) {
+  GRID_LOOP(k, N) L[k] = rho[k] < thr ? (int32_t)k : -1;
+}
+__global__ void k_ccl_union(const View v, int32_t *L) {
+  const int64_t N = v.NX * v.NY * v.NZ;
+  GRID_LOOP(k, N) {
+    if (L[k] < 0) continue;
+    const Idx c = idx_of(k, v);
+    const int64_t nbr[3] = {lin(wr(c.x + 1, (int)v.NX), c.y, c.z, v),
+                            lin(c.x, wr(c.y + 1, (int)v.NY), c.z, v),
+                            lin(c.x, c.y, wr(c.z + 1, (int)v.NZ), v)};
+    for (int q = 0; q < 3; ++q) {
+      const int64_t m = nbr[q];
+      if (m != k && L[m] >= 0) uf_union(L, (int32_t)k, (int32_t)m);
+    }
+  }
+}
+__global__ void k_ccl_compress(int64_t N, int32_t *L, unsigned long long *ncomp) {
+  unsigned int roots = 0;
+  GRID_LOOP(k, N) {
+    if (L[k] < 0) continue;
+    const int32_t r = uf_find(L, (int32_t)k);
+    L[k] = r;
+    roots += (r == (int32_t)k);
+  }
+  if (roots) atomicAdd(ncomp, (unsigned long long)roots);
+}
+__global__ void k_gather_labels(const int32_t *L, const int32_t *cells, int32_t n, int32_t *out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) out[s] = L[cells[s]];
+}
+
+}  // namespace
+
+// ---- host wrappers ----------------------------------------------------------
+// Calls fn(integral_constant<lattice>, integral_constant<storage>).
+template <typename Fn>
+static void dispatch(const View &v, Fn &&fn) {
+  using D3 = std::integral_constant<int, D3Q19>;
+  using D2 = std::integral_constant<int, D2Q9>;
+  using F64 = std::integral_constant<int, ST_F64>;
+  using F32 = std::integral_constant<int, ST_F32>;
+  using F16 = std::integral_constant<int, ST_F16>;
+  using B16 = std::integral_constant<int, ST_BF16>;
+  if (v.lat == D3Q19) {
+    switch (v.st) {
+      case ST_F64: fn(D3{}, F64{}); break;
+      case ST_F32: fn(D3{}, F32{}); break;
+      case ST_F16: fn(D3{}, F16{}); break;
+      default: fn(D3{}, B16{}); break;
+    }
+  } else {
+    switch (v.st) {
+      case ST_F64: fn(D2{}, F64{}); break;
+      case ST_F32: fn(D2{}, F32{}); break;
+      case ST_F16: fn(D2{}, F16{}); break;
+      default: fn(D2{}, B16{}); break;
+    }
+  }
+}
+
+static int64_t ncells(const View &v) { return v.NX * v.NY * v.NZ; }
+
+cudaError_t diag_init_rho(const View &v, const double *bub, int32_t nb, double rho_l,
+                          double rho_g, double width, double noise_amp, uint64_t seed,
+                          double *rho, cudaStream_t s) {
+  k_init_rho<<<nblocks(ncells(v)), TPB, 0, s>>>(v, bub, nb, rho_l, rho_g, width, noise_amp,
+                                                seed ^ 0x6E6F697365000000ull, rho);
+  return cudaGetLastError();
+}
+
+static cudaError_t store_from(const View &v, const double *src, int from_f, void *stored,
+                              cudaStream_t s) {
+  dispatch(v, [&](auto L, auto S) {
+    k_store_from<decltype(L)::value, decltype(S)::value>
+        <<<nblocks(ncells(v)), TPB, 0, s>>>(v, src, from_f, stored);
+  });
+  return cudaGetLastError();
+}
+cudaError_t diag_store_from_f(const View &v, const double *f, void *stored, cudaStream_t s) {
+  return store_from(v, f, 1, stored, s);
+}
+cudaError_t diag_store_from_rho(const View &v, const double *rho, void *stored, cudaStream_t s) {
+  return store_from(v, rho, 0, stored, s);
+}
+
+cudaError_t diag_gather_f(const View &v, const void *stored, double *f, cudaStream_t s) {
+  dispatch(v, [&](auto L, auto S) {
+    k_gather_f<decltype(L)::value, decltype(S)::value>
+        <<<nblocks(ncells(v)), TPB, 0, s>>>(v, stored, f);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t diag_gather_pop(const View &v, const void *stored, int i, double *out,
+                            cudaStream_t s) {
+  dispatch(v, [&](auto L, auto S) {
+    k_gather_pop<decltype(L)::value, decltype(S)::value>
+        <<<nblocks(ncells(v)), TPB, 0, s>>>(v, stored, i, out);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t diag_store_pop(const View &v, const double *f, int i, void *stored, cudaStream_t s) {
+  dispatch(v, [&](auto L, auto S) {
+    k_store_pop<decltype(L)::value, decltype(S)::value>
+        <<<nblocks(ncells(v)), TPB, 0, s>>>(v, f, i, stored);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t diag_moments(const View &v, const void *stored, double G, double rho0, double *rho,
+                         double *jx, double *jy, double *jz, double *psi, double *p, int *err,
+                         cudaStream_t s) {
+  dispatch(v, [&](auto L, auto S) {
+    k_moments<decltype(L)::value, decltype(S)::value>
+        <<<nblocks(ncells(v)), TPB, 0, s>>>(v, stored, G, rho0, rho, jx, jy, jz, psi, p, err);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t diag_velocity(const View &v, double G, const double *rho, const double *jx,
+                          const double *jy, const double *jz, const double *psi, double *u,
+                          cudaStream_t s) {
+  if (v.lat == D3Q19)
+    k_velocity<D3Q19><<<nblocks(ncells(v)), TPB, 0, s>>>(v, G, rho, jx, jy, jz, psi, u);
+  else
+    k_velocity<D2Q9><<<nblocks(ncells(v)), TPB, 0, s>>>(v, G, rho, jx, jy, jz, psi, u);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_laplacian(const View &v, const double *p, double *lap, cudaStream_t s) {
+  k_laplacian<<<nblocks(ncells(v)), TPB, 0, s>>>(v, p, lap);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_line_d2(const View &v, const double *p, int64_t x0, int64_t y0, int64_t z0,
+                         int axis, int64_t len, double *out, cudaStream_t s) {
+  k_line_d2<<<nblocks(len), TPB, 0, s>>>(v, p, (int)x0, (int)y0, (int)z0, axis, len, out);
+  return cudaGetLastError();
+}
+
+int diag_totals_blocks() { return TOT_BLOCKS; }
+
+cudaError_t diag_totals(const View &v, const void *stored, double *partials, double *out4,
+                        cudaStream_t s) {
+  dispatch(v, [&](auto L, auto S) {
+    k_totals<decltype(L)::value, decltype(S)::value><<<TOT_BLOCKS, TPB, 0, s>>>(v, stored, partials);
+  });
+  if (v.lat == D3Q19)
+    k_totals_final<D3Q19><<<1, TPB, 0, s>>>(partials, out4);
+  else
+    k_totals_final<D2Q9><<<1, TPB, 0, s>>>(partials, out4);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_label(const View &v, const double *rho, double thr, int32_t *labels,
+                       unsigned long long *ncomp_dev, cudaStream_t s) {
+  const int64_t N = ncells(v);
+  cudaError_t e = cudaMemsetAsync(ncomp_dev, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_ccl_init<<<nblocks(N), TPB, 0, s>>>(N, rho, thr, labels);
+  k_ccl_union<<<nblocks(N), TPB, 0, s>>>(v, labels);
+  k_ccl_compress<<<nblocks(N), TPB, 0, s>>>(N, labels, ncomp_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_gather_labels(const int32_t *labels, const int32_t *cells, int32_t n,
+                               int32_t *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_labels<<<(n + TPB - 1) / TPB, TPB, 0, s>>>(labels, cells, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace sclbm

@@ -1,0 +1,114 @@
+// Internal interfaces between the translation units of the library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sclbm {
+
+// Everything a step kernel needs.  Cells are addressed in the kernels'
+// three-dimensional view (D2Q9 on (nx, 1, ny)); the population arrays are
+// f[i][z][y][x] with a row pitch px >= NX (elements), planes of px*NY and
+// population blocks of px*NY*NZ.  fin holds the post-collision populations
+// of the previous step at their origin cell (pull form), fout receives the
+// post-collision populations of this step.
+struct StepArgs {
+  const void *fin;
+  void *fout;
+  int64_t NX, NY, NZ, px;
+  double tau, G, rho0, rho_ref;
+  // injection (virtual blowing agent); nsites == 0 disables it
+  int32_t nsites;
+  const int32_t *site_x, *site_y, *site_z;  // view coordinates per site
+  const double *rate;
+  double *budget;
+  // sites grouped by cell (site order inside a group) for the two-pass
+  // injection kernel: group g holds group_site[group_off[g] .. group_off[g+1])
+  int32_t ngroups;
+  const int32_t *group_off;
+  const int32_t *group_site;
+  // per work item lists of sites, sorted by (z, site), for the fused kernel
+  const int32_t *bucket_off;
+  const int32_t *bucket_site;
+  int *err;  // device status word (ERR_* bits)
+};
+
+// fused-kernel launch plan
+struct FusedPlan {
+  int tile;      // tile id (see fused_tile_shape)
+  int bx, by;    // interior tile of one CTA
+  int nstage;    // TMA pipeline depth
+  int tiles_x, tiles_y, nzc, zlen;
+  int items;     // tiles_x * tiles_y * nzc CTAs
+  int threads;
+  int smem;      // dynamic shared memory bytes
+  int box_w, box_h;
+};
+
+// Tile shapes: returns false when the id is unknown for the lattice.
+bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage);
+// Fill *plan for a lattice; nzc <= 0 picks the number of z chunks from the
+// SM count.  Returns cudaErrorInvalidValue when the tile does not fit.
+cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ,
+                            int nzc, FusedPlan *plan);
+// Encode the 4-D TMA descriptor of one population lattice for a plan.
+CUresult fused_encode_tmap(int lat, int st, const FusedPlan &plan, const void *base,
+                           int64_t NX, int64_t NY, int64_t NZ, int64_t px, CUtensorMap *tm);
+cudaError_t fused_launch(int lat, int st, const FusedPlan &plan, const StepArgs &a,
+                         const CUtensorMap &tm_in, cudaStream_t s);
+// work item (CTA) owning a view cell, for the injection buckets
+int fused_item_of(const FusedPlan &plan, int64_t x, int64_t y, int64_t z);
+
+// per-storage entry points (one translation unit each)
+cudaError_t fused_launch_f64(int lat, const FusedPlan &, const StepArgs &, const CUtensorMap &,
+                             cudaStream_t);
+cudaError_t fused_launch_f32(int lat, const FusedPlan &, const StepArgs &, const CUtensorMap &,
+                             cudaStream_t);
+cudaError_t fused_launch_h16(int lat, int st, const FusedPlan &, const StepArgs &,
+                             const CUtensorMap &, cudaStream_t);
+cudaError_t fused_prepare(int lat, int st, const FusedPlan &plan);  // set smem attribute
+cudaError_t fused_prepare_f64(int lat, const FusedPlan &);
+cudaError_t fused_prepare_f32(int lat, const FusedPlan &);
+cudaError_t fused_prepare_h16(int lat, int st, const FusedPlan &);
+
+// two-pass path: psi field pass, then collide/stream (+ injection kernel)
+cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi_scratch, cudaStream_t s);
+
+// ---- diagnostics / state kernels (diag.cu) --------------------------------
+struct View {
+  int lat, st;
+  int64_t NX, NY, NZ, px;
+  double rho_ref;
+};
+// initial density field (doubles, N) from bubbles (view coordinates, x y z r)
+cudaError_t diag_init_rho(const View &v, const double *bub, int32_t nb, double rho_l,
+                          double rho_g, double width, double noise_amp, uint64_t seed,
+                          double *rho, cudaStream_t s);
+// stored populations from canonical f_i(x) (doubles, Q*N), or from rho at rest
+cudaError_t diag_store_from_f(const View &v, const double *f, void *stored, cudaStream_t s);
+cudaError_t diag_store_from_rho(const View &v, const double *rho, void *stored, cudaStream_t s);
+// canonical f_i(x) (doubles, Q*N) from stored populations
+cudaError_t diag_gather_f(const View &v, const void *stored, double *f, cudaStream_t s);
+// FP64 moments: any output may be null; sets ERR_NONFINITE in err
+cudaError_t diag_moments(const View &v, const void *stored, double G, double rho0, double *rho,
+                         double *jx, double *jy, double *jz, double *psi, double *p, int *err,
+                         cudaStream_t s);
+// physical velocity (j + F/2)/rho from rho, j and psi fields
+cudaError_t diag_velocity(const View &v, double G, const double *rho, const double *jx,
+                          const double *jy, const double *jz, const double *psi, double *u,
+                          cudaStream_t s);
+cudaError_t diag_laplacian(const View &v, const double *p, double *lap, cudaStream_t s);
+cudaError_t diag_line_d2(const View &v, const double *p, int64_t x0, int64_t y0, int64_t z0,
+                         int axis, int64_t len, double *out, cudaStream_t s);
+// FP64 totals (M, Jx, Jy, Jz) in user axes; partials must hold 4*diag_totals_blocks() doubles
+int diag_totals_blocks();
+cudaError_t diag_totals(const View &v, const void *stored, double *partials, double *out4,
+                        cudaStream_t s);
+// connected components of rho < thr; labels N int32; count -> *ncomp_dev (int64)
+cudaError_t diag_label(const View &v, const double *rho, double thr, int32_t *labels,
+                       unsigned long long *ncomp_dev, cudaStream_t s);
+cudaError_t diag_gather_labels(const int32_t *labels, const int32_t *cells, int32_t n,
+                               int32_t *out, cudaStream_t s);
+
+}  // namespace sclbm

@@ -1,0 +1,175 @@
+// Lattice tables, storage codecs and small PTX helpers of the GB300 library.
+//
+// Kernels see every lattice as three-dimensional: D3Q19 on (nx, ny, nz) and
+// D2Q9 on the view (nx, 1, ny), whose velocity (cx, cy) becomes
+// (cx, 0, cy).  The memory layout f[i][z][y][x] of the two is identical, so
+// the user-facing order of cells and populations does not change.  All
+// kernels march along the view's z axis.
+//
+// Velocity order (user axes) follows the public header: D2Q9
+// rest, +x, +y, -x, -y, (1,1), (-1,1), (-1,-1), (1,-1); D3Q19 rest, the six
+// axis directions (+x,-x,+y,-y,+z,-z) and the twelve edge directions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace sclbm {
+
+enum { D2Q9 = 0, D3Q19 = 1 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+template <int LAT>
+struct Lattice;
+
+// D2Q9 in the 3-D view (x, 1, y): cy of the 2-D set goes to the z slot.
+template <>
+struct Lattice<D2Q9> {
+  static constexpr int Q = 9;
+  static constexpr bool HAS_Y = false;  // no velocity moves along the view's y
+  __host__ __device__ static constexpr int cx(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int) { return 0; }
+  __host__ __device__ static constexpr int cz(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+
+template <>
+struct Lattice<D3Q19> {
+  static constexpr int Q = 19;
+  static constexpr bool HAS_Y = true;
+  // rest, +x, -x, +y, -y, +z, -z,
+  // (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+  // (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)
+               ? 1
+               : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17)
+               ? 1
+               : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18)
+               ? 1
+               : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+// ---- storage codecs -------------------------------------------------------
+// T = stored type, C = arithmetic type.  16-bit forms hold f - w_i*rho_ref.
+template <int ST>
+struct Storage;
+
+template <>
+struct Storage<ST_F64> {
+  using T = double;
+  using C = double;
+  __device__ static C load(T v, C) { return v; }
+  __device__ static T store(C v, C) { return v; }
+};
+template <>
+struct Storage<ST_F32> {
+  using T = float;
+  using C = float;
+  __device__ static C load(T v, C) { return v; }
+  __device__ static T store(C v, C) { return v; }
+};
+template <>
+struct Storage<ST_F16> {
+  using T = __half;
+  using C = float;
+  __device__ static C load(T v, C wref) { return wref + __half2float(v); }
+  __device__ static T store(C v, C wref) { return __float2half_rn(v - wref); }
+};
+template <>
+struct Storage<ST_BF16> {
+  using T = __nv_bfloat16;
+  using C = float;
+  __device__ static C load(T v, C wref) { return wref + __bfloat162float(v); }
+  __device__ static T store(C v, C wref) { return __float2bfloat16_rn(v - wref); }
+};
+
+inline size_t storage_bytes(int st) { return st == ST_F64 ? 8 : (st == ST_F32 ? 4 : 2); }
+
+// psi(rho) = rho0 (1 - exp(-rho/rho0))
+__device__ __forceinline__ double psi_of(double rho, double rho0, double inv_rho0) {
+  return rho0 * (1.0 - exp(-rho * inv_rho0));
+}
+__device__ __forceinline__ float psi_of(float rho, float rho0, float inv_rho0) {
+  return rho0 * (1.0f - expf(-rho * inv_rho0));
+}
+
+// ---- small PTX helpers ----------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for a phase with a time limit; false when the limit passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+// 4-D tiled TMA load (coordinates x, y, z, population) completing on bar.
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0, int c1, int c2,
+                                            int c3, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const void *tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+}
+
+// error bits reported through the context's device status word
+enum { ERR_TMA_TIMEOUT = 1, ERR_NONFINITE = 2 };
+
+}  // namespace sclbm

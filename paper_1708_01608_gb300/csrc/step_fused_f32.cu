@@ -1,0 +1,10 @@
+// Fused step kernels, FP32 storage and arithmetic.
+#include "step_fused.cuh"
+
+namespace sclbm {
+cudaError_t fused_launch_f32(int lat, const FusedPlan &p, const StepArgs &a, const CUtensorMap &tm,
+                             cudaStream_t s) {
+  return fused_launch_st<ST_F32>(lat, p, a, tm, s);
+}
+cudaError_t fused_prepare_f32(int lat, const FusedPlan &p) { return fused_prepare_st<ST_F32>(lat, p); }
+}  // namespace sclbm

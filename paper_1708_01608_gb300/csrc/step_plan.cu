@@ -1,0 +1,144 @@
+// Host side of the fused step: tile table, launch plan, TMA descriptors and
+// dispatch to the per-storage translation units.
+#include <algorithm>
+
+#include "step_fused.cuh"
+
+namespace sclbm {
+
+bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage) {
+  (void)st;
+#define SCLBM_T(id, BX, BY, NS) \
+  case id:                      \
+    *bx = BX;                   \
+    *by = BY;                   \
+    *nstage = NS;               \
+    return true;
+  if (lat == D3Q19) {
+    switch (tile) { SCLBM_D3Q19_TILES(SCLBM_T) }
+  } else {
+    switch (tile) { SCLBM_D2Q9_TILES(SCLBM_T) }
+  }
+#undef SCLBM_T
+  return false;
+}
+
+// Same arithmetic as FusedK, evaluated on the host.
+static int fused_smem_bytes(int lat, int st, int bx, int by, int ns, int *box_w, int *box_h) {
+  const int Q = lat == D3Q19 ? 19 : 9;
+  const int hy = lat == D3Q19 ? 1 : 0;
+  const int sz = (int)storage_bytes(st);
+  const int csz = st == ST_F64 ? 8 : 4;
+  const int hx = std::max(2, 16 / sz);
+  const int bw = bx + 2 * hx, bh = by + 2 * hy;
+  const int box_stride = (bw * bh * sz + 127) / 128 * 128;
+  const int ring = (4 * (bx + 2) * (by + 2 * hy) * csz + 15) / 16 * 16;
+  int nsub = (bw + 255) / 256;
+  while (nsub <= bw && (bw % nsub != 0 || ((bw / nsub) * sz) % 16 != 0)) ++nsub;
+  *box_w = bw / nsub;  // width of one TMA box
+  *box_h = bh;
+  return ns * Q * box_stride + ring + ns * 8 + 128;
+}
+
+cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ, int nzc,
+                            FusedPlan *p) {
+  int bx, by, ns;
+  if (tile <= 0) tile = (lat == D3Q19) ? 1 : 1;
+  if (!fused_tile_shape(lat, st, tile, &bx, &by, &ns)) return cudaErrorInvalidValue;
+  p->tile = tile;
+  p->bx = bx;
+  p->by = by;
+  p->nstage = ns;
+  p->threads = bx * by;
+  p->smem = fused_smem_bytes(lat, st, bx, by, ns, &p->box_w, &p->box_h);
+  int dev = 0, nsm = 0, smem_optin = 0, smem_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (p->smem > smem_optin) return cudaErrorInvalidValue;
+  p->tiles_x = (int)((NX + bx - 1) / bx);
+  p->tiles_y = (int)((NY + by - 1) / by);
+  const int ntiles = p->tiles_x * p->tiles_y;
+  if (nzc <= 0) {
+    // one wave: as many z chunks as keep every resident slot busy
+    int per_sm = std::max(1, std::min(smem_sm / (p->smem + 1024), 2048 / p->threads));
+    const int slots = nsm * per_sm;
+    nzc = std::max(1, slots / std::max(1, ntiles));
+    nzc = (int)std::min<int64_t>(nzc, std::max<int64_t>(1, NZ / 4));
+  }
+  nzc = (int)std::min<int64_t>(std::max(nzc, 1), NZ);
+  p->zlen = (int)((NZ + nzc - 1) / nzc);
+  p->nzc = (int)((NZ + p->zlen - 1) / p->zlen);
+  p->items = ntiles * p->nzc;
+  return cudaSuccess;
+}
+
+int fused_item_of(const FusedPlan &p, int64_t x, int64_t y, int64_t z) {
+  const int tx = (int)(x / p.bx), ty = (int)(y / p.by), zc = (int)(z / p.zlen);
+  return (zc * p.tiles_y + ty) * p.tiles_x + tx;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+CUresult fused_encode_tmap(int lat, int st, const FusedPlan &p, const void *base, int64_t NX,
+                           int64_t NY, int64_t NZ, int64_t px, CUtensorMap *tm) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return CUDA_ERROR_NOT_FOUND;
+  const int Q = lat == D3Q19 ? 19 : 9;
+  const size_t sz = storage_bytes(st);
+  CUtensorMapDataType dt = st == ST_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : st == ST_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : st == ST_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  cuuint64_t dims[4] = {(cuuint64_t)NX, (cuuint64_t)NY, (cuuint64_t)NZ, (cuuint64_t)Q};
+  cuuint64_t strides[3] = {(cuuint64_t)(px * sz), (cuuint64_t)(px * NY * sz),
+                           (cuuint64_t)(px * NY * NZ * sz)};
+  cuuint32_t box[4] = {(cuuint32_t)p.box_w, (cuuint32_t)p.box_h, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(tm, dt, 4, const_cast<void *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+cudaError_t fused_launch(int lat, int st, const FusedPlan &p, const StepArgs &a,
+                         const CUtensorMap &tm, cudaStream_t s) {
+  switch (st) {
+    case ST_F64:
+      return fused_launch_f64(lat, p, a, tm, s);
+    case ST_F32:
+      return fused_launch_f32(lat, p, a, tm, s);
+    default:
+      return fused_launch_h16(lat, st, p, a, tm, s);
+  }
+}
+
+cudaError_t fused_prepare(int lat, int st, const FusedPlan &p) {
+  switch (st) {
+    case ST_F64:
+      return fused_prepare_f64(lat, p);
+    case ST_F32:
+      return fused_prepare_f32(lat, p);
+    default:
+      return fused_prepare_h16(lat, st, p);
+  }
+}
+
+}  // namespace sclbm

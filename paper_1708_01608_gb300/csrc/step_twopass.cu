@@ -1,0 +1,165 @@
+// Two-pass Shan-Chen step: pass 1 computes psi(x) for every cell from the
+// gathered populations; pass 2 gathers the populations again, takes psi of
+// the neighbours from that field, collides and writes.  The blowing-agent
+// injection runs as a third, one-thread-per-site kernel.  This path moves
+// 3*Q*S + 2*sizeof(psi) bytes per update instead of the fused kernel's
+// 2*Q*S; it is kept as a simple, independently written comparison path.
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace sclbm {
+
+struct Cell {
+  int x, y, z;
+};
+
+__device__ __forceinline__ Cell cell_of(int64_t k, int64_t NX, int64_t NY) {
+  Cell c;
+  c.x = (int)(k % NX);
+  const int64_t r = k / NX;
+  c.y = (int)(r % NY);
+  c.z = (int)(r / NY);
+  return c;
+}
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+template <int LAT, int ST>
+__global__ void tp_psi_kernel(const StepArgs a, typename Storage<ST>::C *psi) {
+  using L = Lattice<LAT>;
+  using S = Storage<ST>;
+  using T = typename S::T;
+  using C = typename S::C;
+  const int64_t N = a.NX * a.NY * a.NZ;
+  const int64_t plane = a.px * a.NY, pop = plane * a.NZ;
+  const T *f = static_cast<const T *>(a.fin);
+  const C rho0 = (C)a.rho0, inv_rho0 = (C)(1.0 / a.rho0);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const Cell c = cell_of(k, a.NX, a.NY);
+    C rho = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const int sx = wrapi(c.x - L::cx(i), (int)a.NX), sy = wrapi(c.y - L::cy(i), (int)a.NY),
+                sz = wrapi(c.z - L::cz(i), (int)a.NZ);
+      rho += S::load(f[i * pop + sz * plane + sy * a.px + sx], (C)(L::w(i) * a.rho_ref));
+    }
+    psi[k] = psi_of(rho, rho0, inv_rho0);
+  }
+}
+
+template <int LAT, int ST>
+__global__ void tp_collide_kernel(const StepArgs a, const typename Storage<ST>::C *psi) {
+  using L = Lattice<LAT>;
+  using S = Storage<ST>;
+  using T = typename S::T;
+  using C = typename S::C;
+  const int64_t N = a.NX * a.NY * a.NZ;
+  const int64_t plane = a.px * a.NY, pop = plane * a.NZ;
+  const T *f = static_cast<const T *>(a.fin);
+  T *g = static_cast<T *>(a.fout);
+  const C G = (C)a.G, tau = (C)a.tau, omega = (C)(1.0 / a.tau);
+  const int NX = (int)a.NX, NY = (int)a.NY, NZ = (int)a.NZ;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const Cell c = cell_of(k, a.NX, a.NY);
+    C fi[L::Q];
+    C rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const int sx = wrapi(c.x - L::cx(i), NX), sy = wrapi(c.y - L::cy(i), NY),
+                sz = wrapi(c.z - L::cz(i), NZ);
+      fi[i] = S::load(f[i * pop + sz * plane + sy * a.px + sx], (C)(L::w(i) * a.rho_ref));
+      rho += fi[i];
+      jx += (C)L::cx(i) * fi[i];
+      jy += (C)L::cy(i) * fi[i];
+      jz += (C)L::cz(i) * fi[i];
+    }
+    C sx = 0, sy = 0, sz = 0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+      const int nx_ = wrapi(c.x + L::cx(i), NX), ny_ = wrapi(c.y + L::cy(i), NY),
+                nz_ = wrapi(c.z + L::cz(i), NZ);
+      const C wp = (C)L::w(i) * psi[((int64_t)nz_ * NY + ny_) * NX + nx_];
+      sx += (C)L::cx(i) * wp;
+      sy += (C)L::cy(i) * wp;
+      sz += (C)L::cz(i) * wp;
+    }
+    const C gp = -G * psi[k];
+    const C ir = (C)1 / rho;
+    const C ux = (jx + tau * gp * sx) * ir, uy = (jy + tau * gp * sy) * ir,
+            uz = (jz + tau * gp * sz) * ir;
+    const C uu = (C)1.5 * (ux * ux + uy * uy + uz * uz);
+    T *o = g + (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
+      const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
+      o[i * pop] = S::store(fi[i] - omega * (fi[i] - feq), (C)(L::w(i) * a.rho_ref));
+    }
+  }
+}
+
+// One thread per distinct site cell: deposits the blowing-agent mass of every
+// site of that cell (budgets updated in site order).
+template <int LAT, int ST>
+__global__ void tp_inject_kernel(const StepArgs a) {
+  using L = Lattice<LAT>;
+  using S = Storage<ST>;
+  using T = typename S::T;
+  using C = typename S::C;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.ngroups) return;
+  double dm = 0.0;
+  int s0 = -1;
+  for (int q = a.group_off[g]; q < a.group_off[g + 1]; ++q) {
+    const int s = a.group_site[q];
+    s0 = s;
+    const double b = a.budget[s];
+    if (b > 0.0) {
+      const double d = fmin(a.rate[s], b);
+      a.budget[s] = b - d;
+      dm += d;
+    }
+  }
+  if (dm == 0.0 || s0 < 0) return;
+  const int64_t plane = a.px * a.NY, pop = plane * a.NZ;
+  T *o = static_cast<T *>(a.fout) + (int64_t)a.site_z[s0] * plane + (int64_t)a.site_y[s0] * a.px +
+         a.site_x[s0];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const C wref = (C)(L::w(i) * a.rho_ref);
+    o[i * pop] = S::store(S::load(o[i * pop], wref) + (C)(L::w(i) * dm), wref);
+  }
+}
+
+template <int LAT, int ST>
+static cudaError_t tp_launch_t(const StepArgs &a, void *psi, cudaStream_t s) {
+  using C = typename Storage<ST>::C;
+  const int64_t N = a.NX * a.NY * a.NZ;
+  const int threads = 256;
+  const int blocks = (int)((N + threads - 1) / threads < 1048576 ? (N + threads - 1) / threads
+                                                                  : 1048576);
+  tp_psi_kernel<LAT, ST><<<blocks, threads, 0, s>>>(a, static_cast<C *>(psi));
+  tp_collide_kernel<LAT, ST><<<blocks, threads, 0, s>>>(a, static_cast<const C *>(psi));
+  if (a.nsites > 0) tp_inject_kernel<LAT, ST><<<(a.ngroups + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi, cudaStream_t s) {
+  if (lat == D3Q19) {
+    switch (st) {
+      case ST_F64: return tp_launch_t<D3Q19, ST_F64>(a, psi, s);
+      case ST_F32: return tp_launch_t<D3Q19, ST_F32>(a, psi, s);
+      case ST_F16: return tp_launch_t<D3Q19, ST_F16>(a, psi, s);
+      default: return tp_launch_t<D3Q19, ST_BF16>(a, psi, s);
+    }
+  }
+  switch (st) {
+    case ST_F64: return tp_launch_t<D2Q9, ST_F64>(a, psi, s);
+    case ST_F32: return tp_launch_t<D2Q9, ST_F32>(a, psi, s);
+    case ST_F16: return tp_launch_t<D2Q9, ST_F16>(a, psi, s);
+    default: return tp_launch_t<D2Q9, ST_BF16>(a, psi, s);
+  }
+}
+
+}  // namespace sclbm

@@ -1,0 +1,290 @@
+"""Python binding of the C ABI in ``include/lbm.h`` (ctypes; argument
+marshalling only).
+
+Every step of the method runs in the CUDA kernels of ``libsclbm.so``; this
+module converts numpy arrays and Python values into the C structures and
+raises :class:`LBMError` on any non-OK status.  PyTorch, when present, only
+provides device memory (its caching allocator, through the allocator
+callbacks of the config) and the current CUDA stream.
+
+There is no CPU fallback: if the library has not been built the import of
+this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsclbm.so")
+
+# enums (include/lbm.h)
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENUMERIC, ETIMEOUT = range(7)
+D2Q9, D3Q19 = 0, 1
+F64, F32, F16_OFFSET, BF16_OFFSET = 0, 1, 2, 3
+RHO, PSI, P, U, F, LAPP = range(6)
+KERNEL_AUTO, KERNEL_FUSED, KERNEL_TWO_PASS = 0, 1, 2
+
+STORAGE = {"f64": F64, "f32": F32, "f16": F16_OFFSET, "bf16": BF16_OFFSET}
+LATTICE = {"D2Q9": D2Q9, "D3Q19": D3Q19}
+KERNEL = {"auto": KERNEL_AUTO, "fused": KERNEL_FUSED, "two_pass": KERNEL_TWO_PASS}
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENUMERIC",
+                6: "ETIMEOUT"}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int32), ("storage", C.c_int32),
+        ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
+        ("tau", C.c_double), ("G", C.c_double), ("rho0", C.c_double),
+        ("rho_ref", C.c_double), ("gas_threshold", C.c_double),
+        ("kernel", C.c_int32), ("tile", C.c_int32),
+        ("stream", C.c_void_p),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+    ]
+
+
+class Bubble(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("r", C.c_double)]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    P_ = C.c_void_p
+    i32, i64, u64, d, sz = C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
+    sig = {
+        "lbm_config_default": (None, [C.POINTER(Config)]),
+        "lbm_create": (i32, [C.POINTER(Config), C.POINTER(P_)]),
+        "lbm_destroy": (None, [P_]),
+        "lbm_sample_sites": (i32, [i64, i64, i64, i32, d, d, d, d, u64, i64, P_, C.POINTER(i32)]),
+        "lbm_seed_bubbles": (i32, [P_, P_, i32, d, d, d, d, u64]),
+        "lbm_inject": (i32, [P_, P_, P_, i32]),
+        "lbm_read_budgets": (i32, [P_, P_, i32]),
+        "lbm_step": (i32, [P_, i64]),
+        "lbm_step_count": (i64, [P_]),
+        "lbm_sync": (i32, [P_]),
+        "lbm_pressure_laplacian": (i32, [P_, P_, i64, P_]),
+        "lbm_label_gas": (i32, [P_, P_, C.POINTER(i64)]),
+        "lbm_site_labels": (i32, [P_, P_, i32, C.POINTER(i64)]),
+        "lbm_totals": (i32, [P_, P_]),
+        "lbm_read": (i32, [P_, i32, P_, sz]),
+        "lbm_write_f": (i32, [P_, P_, sz]),
+        "lbm_last_error": (C.c_char_p, []),
+        "lbm_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+# every symbol the header declares (checked by the CPU tests)
+EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites",
+           "lbm_seed_bubbles", "lbm_inject", "lbm_read_budgets", "lbm_step", "lbm_step_count",
+           "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_site_labels",
+           "lbm_totals", "lbm_read", "lbm_write_f", "lbm_last_error", "lbm_version")
+
+
+def lib():
+    return _lib
+
+
+def _check(st: int):
+    if st != OK:
+        raise LBMError(st, _lib.lbm_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def version() -> str:
+    return _lib.lbm_version().decode()
+
+
+def sample_sites(nx, ny, nz, n, r_min, r_max, min_spacing=0.0, min_gap=0.0, seed=0,
+                 max_tries=10_000_000):
+    """Random nucleation sites (host sampler of the library): (n, 4) x, y, z, r."""
+    out = (Bubble * max(n, 1))()
+    got = C.c_int32(0)
+    _check(_lib.lbm_sample_sites(nx, ny, nz, n, r_min, r_max, min_spacing, min_gap,
+                                 seed & (2**64 - 1), max_tries, C.cast(out, C.c_void_p),
+                                 C.byref(got)))
+    return np.array([[b.x, b.y, b.z, b.r] for b in out[:n]], dtype=np.float64).reshape(-1, 4)
+
+
+class _TorchMemory:
+    """Allocator callbacks backed by torch's CUDA caching allocator."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+
+        def alloc(nbytes, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0))
+            except Exception:  # reported to C as a NULL pointer -> ENOMEM
+                return None
+
+        def free(ptr, nbytes, stream, user):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+class Lattice:
+    """One periodic Shan-Chen lattice on the current CUDA device."""
+
+    def __init__(self, lattice="D3Q19", nx=64, ny=64, nz=1, tau=1.0, G=-5.0, rho0=1.0,
+                 storage="f32", rho_ref=1.0, gas_threshold=1.0, kernel="auto", tile=0,
+                 stream: Optional[int] = None, torch_memory: bool = True):
+        cfg = Config()
+        _lib.lbm_config_default(C.byref(cfg))
+        cfg.lattice = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
+        cfg.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+        cfg.tau, cfg.G, cfg.rho0 = float(tau), float(G), float(rho0)
+        cfg.rho_ref, cfg.gas_threshold = float(rho_ref), float(gas_threshold)
+        cfg.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
+        cfg.tile = int(tile)
+        self._mem = None
+        if torch_memory:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    self._mem = _TorchMemory()
+                    if stream is None:
+                        stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                self._mem = None
+        if self._mem is not None:
+            cfg.alloc, cfg.free = self._mem.alloc, self._mem.free
+        cfg.stream = stream or None
+        self.cfg = cfg
+        self.q = 9 if cfg.lattice == D2Q9 else 19
+        self.shape = (cfg.nz, cfg.ny, cfg.nx)
+        self.n = cfg.nx * cfg.ny * cfg.nz
+        self.nsites = 0
+        h = C.c_void_p()
+        _check(_lib.lbm_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- set-up
+    def seed_bubbles(self, bubbles, rho_l, rho_g, width=2.0, noise_amp=0.0, seed=0):
+        b = np.ascontiguousarray(np.zeros((0, 4)) if bubbles is None else bubbles,
+                                 dtype=np.float64).reshape(-1, 4)
+        self.nsites = len(b)
+        _check(_lib.lbm_seed_bubbles(self._h, _ptr(b) if len(b) else None, len(b), rho_l, rho_g,
+                                     width, noise_amp, seed & (2**64 - 1)))
+
+    def inject(self, rate, budget):
+        r = np.ascontiguousarray(rate, dtype=np.float64).reshape(-1)
+        b = np.ascontiguousarray(budget, dtype=np.float64).reshape(-1)
+        _check(_lib.lbm_inject(self._h, _ptr(r) if len(r) else None,
+                               _ptr(b) if len(b) else None, len(r)))
+        self._ninj = len(r)
+
+    def read_budgets(self):
+        out = np.empty(getattr(self, "_ninj", 0))
+        _check(_lib.lbm_read_budgets(self._h, _ptr(out), len(out)))
+        return out
+
+    def write_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.q * self.n
+        _check(_lib.lbm_write_f(self._h, _ptr(f), f.nbytes))
+
+    # -- time stepping
+    def step(self, n=1):
+        _check(_lib.lbm_step(self._h, int(n)))
+
+    def sync(self):
+        _check(_lib.lbm_sync(self._h))
+
+    @property
+    def steps(self):
+        return int(_lib.lbm_step_count(self._h))
+
+    # -- diagnostics
+    def read(self, field):
+        field = {"rho": RHO, "psi": PSI, "p": P, "u": U, "f": F, "lapp": LAPP}.get(field, field)
+        comps = {U: 3, F: self.q}.get(field, 1)
+        out = np.empty((comps,) + self.shape) if comps > 1 else np.empty(self.shape)
+        _check(_lib.lbm_read(self._h, int(field), _ptr(out), out.nbytes))
+        return out
+
+    def pressure_laplacian(self, line=None):
+        """Full periodic Laplacian of p (line None) or the second difference
+        along line = (x, y, z, axis, length)."""
+        if line is None:
+            out = np.empty(self.shape)
+            _check(_lib.lbm_pressure_laplacian(self._h, _ptr(out), out.size, None))
+            return out
+        ln = np.ascontiguousarray(line, dtype=np.int64)
+        out = np.empty(int(ln[4]))
+        _check(_lib.lbm_pressure_laplacian(self._h, _ptr(out), out.size, _ptr(ln)))
+        return out
+
+    def label_gas(self, want_labels=True):
+        """(labels int32 shaped like the lattice or None, number of components)."""
+        lab = np.empty(self.shape, dtype=np.int32) if want_labels else None
+        nc = C.c_int64(0)
+        _check(_lib.lbm_label_gas(self._h, _ptr(lab) if want_labels else None, C.byref(nc)))
+        return lab, int(nc.value)
+
+    def site_labels(self):
+        out = np.empty(self.nsites, dtype=np.int32)
+        ev = C.c_int64(0)
+        _check(_lib.lbm_site_labels(self._h, _ptr(out) if self.nsites else None, self.nsites,
+                                    C.byref(ev)))
+        return out, int(ev.value)
+
+    def totals(self):
+        out = np.zeros(4)
+        _check(_lib.lbm_totals(self._h, _ptr(out)))
+        return out

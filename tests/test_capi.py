@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/lbm.h declares, validates its arguments without touching a GPU, and
+its host-side site sampler agrees bit for bit with the oracle's."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import lbm_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    return lbm_mod()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(lbm):
+    names = declared_functions()
+    assert len(names) >= 18
+    lib = C.CDLL(lbm.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lbm.EXPORTS)
+
+
+def test_version(lbm):
+    assert "sm_103a" in lbm.version()
+
+
+@pytest.mark.parametrize("kw", [
+    dict(lattice="D2Q9", nz=2), dict(nx=0), dict(tau=0.5), dict(tau=float("nan")),
+    dict(rho0=0.0), dict(storage=7), dict(kernel=9), dict(lattice=5)])
+def test_create_rejects_bad_config_without_gpu(lbm, kw):
+    args = dict(lattice="D3Q19", nx=8, ny=8, nz=8, torch_memory=False)
+    args.update(kw)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Lattice(**args)
+    assert e.value.status == lbm.EINVAL
+
+
+def test_null_arguments(lbm):
+    L = lbm.lib()
+    assert L.lbm_create(None, None) == lbm.EINVAL
+    assert L.lbm_step(None, 1) == lbm.EINVAL
+    assert L.lbm_sync(None) == lbm.EINVAL
+    assert L.lbm_step_count(None) == -1
+    L.lbm_destroy(None)
+    assert "NULL" in L.lbm_last_error().decode()
+
+
+@pytest.mark.parametrize("args", [
+    (128, 128, 128, 64, 3.0, 3.0, 12.0, 0.0, 1),
+    (64, 64, 64, 30, 4.0, 12.0, 0.0, 4.0, 2),
+    (512, 512, 1, 40, 8.0, 20.0, 0.0, 3.0, 7),
+])
+def test_site_sampler_matches_oracle(lbm, args):
+    s = lbm.sample_sites(*args)
+    got, so = O.sample_sites(*args)
+    assert got == args[3] and (s == so).all()
+
+
+def test_site_sampler_reports_overfull(lbm):
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.sample_sites(16, 16, 1, 50, 3.0, 3.0, 8.0, 0.0, 1, max_tries=10000)
+    assert e.value.status == lbm.ESTATE

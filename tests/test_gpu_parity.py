@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (element-wise on the populations f_i(x, t), relative to max|f|):
+FP64 storage 1e-12 and FP32 storage 1e-5, the bounds the north-star
+workload states; integer results (labels, component counts, site labels) are
+bit-exact.  Diagnostics are compared on the same population state, so that
+decisions taken in floating point (rho < threshold) see identical inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import LAT, lbm_mod, rel_err, site_cells
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lbm_mod()
+
+
+def run_pair(lbm, lat, nx, ny, nz, storage, kernel, tile, bubbles, steps, tau=0.9, G=-5.0,
+             rho_l=2.0, rho_g=0.15, width=2.0, noise=1e-3, seed=3, rate=None, budget=None):
+    """Seed both sides, start the oracle from the GPU's stored initial state,
+    advance both, return (gpu f, oracle f, gpu budgets, oracle budgets, L)."""
+    L = lbm.Lattice(lat, nx, ny, nz, tau=tau, G=G, storage=storage, kernel=kernel, tile=tile)
+    b = np.asarray(bubbles, dtype=float).reshape(-1, 4)
+    L.seed_bubbles(b, rho_l, rho_g, width, noise, seed)
+    f0 = L.read("f")
+    ob = None
+    if rate is not None:
+        L.inject(rate, budget)
+        ob = np.array(budget, dtype=float)
+    L.step(steps)
+    fg = L.read("f")
+    sites = site_cells(lat, b, nx, ny, nz) if rate is not None else None
+    fo = O.run(LAT[lat], f0, steps, tau, G, sites=sites,
+               rate=None if rate is None else np.asarray(rate, float), budget=ob)
+    bg = L.read_budgets() if rate is not None else None
+    return fg, fo, bg, ob, L
+
+
+def test_initial_state_matches_oracle(lbm):
+    for lat, (nx, ny, nz), bub in [("D3Q19", (20, 18, 16), [[5, 6, 7, 4.0], [15, 12, 3, 3.0]]),
+                                   ("D2Q9", (40, 30, 1), [[10, 10, 0, 6.0], [31, 25, 0, 5.5]])]:
+        L = lbm.Lattice(lat, nx, ny, nz, storage="f64")
+        L.seed_bubbles(np.array(bub, float), 2.0, 0.15, 2.0, 1e-3, 11)
+        fo, rho_o = O.init(LAT[lat], nx, ny, nz, np.array(bub, float), 2.0, 0.15, 2.0, 1e-3, 11)
+        assert rel_err(L.read("f"), fo) < 1e-15
+        assert rel_err(L.read("rho"), rho_o) < 1e-15
+        L.close()
+
+
+CASES = [
+    # lattice, extents (ragged against the tiles), storage, kernel, tile
+    ("D3Q19", (40, 28, 20), "f64", "fused", 1),
+    ("D3Q19", (40, 28, 20), "f32", "fused", 1),
+    ("D3Q19", (70, 13, 9), "f32", "fused", 2),
+    ("D3Q19", (70, 13, 9), "f32", "fused", 3),
+    ("D3Q19", (36, 20, 12), "f32", "fused", 4),
+    ("D3Q19", (40, 28, 20), "f64", "two_pass", 0),
+    ("D3Q19", (40, 28, 20), "f32", "two_pass", 0),
+    ("D2Q9", (300, 37, 1), "f64", "fused", 1),
+    ("D2Q9", (300, 37, 1), "f32", "fused", 2),
+    ("D2Q9", (130, 21, 1), "f32", "fused", 3),
+    ("D2Q9", (130, 21, 1), "f64", "two_pass", 0),
+]
+
+
+@pytest.mark.parametrize("lat,ext,storage,kernel,tile", CASES)
+def test_step_parity_with_injection(lbm, lat, ext, storage, kernel, tile):
+    nx, ny, nz = ext
+    if lat == "D3Q19":
+        bub = [[6, 5, 4, 3.0], [nx - 3, ny - 2, nz - 1, 2.5], [20, 14, 10, 3.5]]
+    else:
+        bub = [[8, 6, 0, 4.0], [nx - 2, ny - 1, 0, 3.0], [60, 20, 0, 5.0]]
+    rate = [2e-3, 1e-3, 5e-4]
+    budget = [0.05, 0.2, 0.01]
+    fg, fo, bg, bo, L = run_pair(lbm, lat, nx, ny, nz, storage, kernel, tile, bub, 60,
+                                 rate=rate, budget=budget)
+    assert rel_err(fg, fo) < TOL[storage], rel_err(fg, fo)
+    assert np.abs(bg - bo).max() < 1e-15
+    L.close()
+
+
+@pytest.mark.parametrize("lat,ext", [("D3Q19", (1, 1, 5)), ("D3Q19", (3, 2, 1)),
+                                     ("D3Q19", (5, 9, 2)), ("D2Q9", (2, 3, 1)),
+                                     ("D2Q9", (1, 7, 1)), ("D3Q19", (33, 9, 3))])
+@pytest.mark.parametrize("kernel", ["fused", "two_pass"])
+def test_tiny_and_degenerate_lattices(lbm, lat, ext, kernel):
+    nx, ny, nz = ext
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
+    q = 19 if lat == "D3Q19" else 9
+    c, w = O.velocities(LAT[lat])
+    rho = rng.uniform(0.1, 2.0, size=(nz, ny, nx))
+    f0 = w[:, None, None, None] * rho[None] * rng.uniform(0.9, 1.1, size=(q, nz, ny, nx))
+    L = lbm.Lattice(lat, nx, ny, nz, tau=0.8, G=-5.0, storage="f64", kernel=kernel)
+    L.write_f(f0)
+    L.step(7)
+    fo = O.run(LAT[lat], f0, 7, 0.8, -5.0)
+    assert rel_err(L.read("f"), fo) < 1e-12
+    L.close()
+
+
+def test_two_sites_in_one_cell(lbm):
+    nx, ny, nz = 24, 16, 8
+    bub = np.array([[5, 5, 5, 3.0], [5.2, 4.9, 5.1, 2.0], [15, 10, 2, 2.0]])
+    rate, budget = [1e-3, 2e-3, 1e-3], [0.02, 0.01, 1.0]
+    for kernel in ("fused", "two_pass"):
+        fg, fo, bg, bo, L = run_pair(lbm, "D3Q19", nx, ny, nz, "f64", kernel, 0, bub, 30,
+                                     rate=rate, budget=budget)
+        assert rel_err(fg, fo) < 1e-12
+        assert np.abs(bg - bo).max() < 1e-15
+        L.close()
+
+
+def test_two_disks_128_fp64_1000_steps(lbm):
+    """The 128^2 two-disk D2Q9 case (4-cell gap, tanh width 2, noise 1e-3)."""
+    from paper_1708_01608_gb300.workloads import TWO_DISKS_128 as W
+    fg, fo, _, _, L = run_pair(lbm, "D2Q9", 128, 128, 1, "f64", "fused", 0, W["bubbles"], 1000,
+                               tau=W["tau"], G=W["G"], rho_l=W["rho_l"], rho_g=W["rho_g"],
+                               width=W["width"], noise=W["noise"], seed=W["seed"])
+    assert rel_err(fg, fo) < 1e-12, rel_err(fg, fo)
+    L.close()
+
+
+def test_diagnostics_on_same_state(lbm):
+    nx, ny, nz = 40, 28, 20
+    bub = [[6, 5, 4, 4.0], [20, 14, 10, 5.0], [30, 20, 12, 4.0], [33, 24, 3, 3.0]]
+    _, _, _, _, L = run_pair(lbm, "D3Q19", nx, ny, nz, "f32", "fused", 1, bub, 40)
+    f = L.read("f")
+    rho, jx, jy, jz = O.moments(O.D3Q19, f)
+    psi, p = O.eos(rho, -5.0)
+    # density, pressure and its Laplacian
+    assert rel_err(L.read("rho"), rho) < 1e-15
+    assert rel_err(L.read("p"), p) < 1e-14
+    lap = O.laplacian(O.D3Q19, p)
+    assert np.abs(L.pressure_laplacian() - lap).max() < 1e-13
+    assert np.abs(L.read("lapp") - lap).max() < 1e-13
+    line = O.line_d2(p, (3, 14, 10), 0, 37)
+    assert np.abs(L.pressure_laplacian((3, 14, 10, 0, 37)) - line).max() < 1e-13
+    line_z = O.line_d2(p, (20, 14, 15), 2, 25)
+    assert np.abs(L.pressure_laplacian((20, 14, 15, 2, 25)) - line_z).max() < 1e-13
+    # physical velocity (j + F/2)/rho
+    F = O.force(O.D3Q19, psi, -5.0)
+    u = np.stack([(jx + 0.5 * F[0]) / rho, (jy + 0.5 * F[1]) / rho, (jz + 0.5 * F[2]) / rho])
+    assert np.abs(L.read("u") - u).max() < 1e-14
+    # labels: bit-exact
+    lab, n = L.label_gas()
+    lab_o, n_o = O.label_gas(O.D3Q19, rho, 1.0)
+    assert n == n_o and (lab == lab_o).all()
+    # totals
+    t = L.totals()
+    to = O.totals(O.D3Q19, f)
+    assert abs(t[0] - to[0]) < 1e-12 * to[0] and np.abs(t[1:] - to[1:]).max() < 1e-10
+    L.close()
+
+
+def test_labels_2d_wrap_and_sites(lbm):
+    nx, ny = 64, 48
+    bub = np.array([[2, 24, 0, 6.0], [62, 24, 0, 6.0], [30, 1, 0, 5.0], [40, 30, 0, 4.0]])
+    L = lbm.Lattice("D2Q9", nx, ny, 1, storage="f64")
+    L.seed_bubbles(bub, 2.0, 0.15, 2.0, 0.0, 0)
+    lab, n = L.label_gas()
+    _, rho = O.init(O.D2Q9, nx, ny, 1, bub, 2.0, 0.15, 2.0, 0.0, 0)
+    lab_o, n_o = O.label_gas(O.D2Q9, L.read("rho"), 1.0)
+    assert n == n_o == 3 and (lab == lab_o).all()
+    sl, ev = L.site_labels()
+    cells = site_cells("D2Q9", bub, nx, ny, 1)
+    assert (sl == lab_o.reshape(-1)[cells]).all() and sl[0] == sl[1] and ev == 0
+    L.close()
+
+
+def test_merge_event_count(lbm):
+    """Two disks 1 cell apart merge (unmodified Shan-Chen): one merge event."""
+    L = lbm.Lattice("D2Q9", 96, 64, 1, storage="f64", tau=1.0)
+    L.seed_bubbles(np.array([[36, 32, 0, 10.0], [57, 32, 0, 10.0]]), 2.0, 0.15, 2.0, 0.0, 0)
+    L.label_gas(False)
+    s0, ev0 = L.site_labels()
+    assert s0[0] != s0[1] and ev0 == 0
+    L.step(3000)
+    L.label_gas(False)
+    s1, ev1 = L.site_labels()
+    f = L.read("f")
+    rho = O.moments(O.D2Q9, f)[0]
+    lab_o, _ = O.label_gas(O.D2Q9, rho, 1.0)
+    cells = site_cells("D2Q9", [[36, 32, 0, 0], [57, 32, 0, 0]], 96, 64, 1)
+    assert (s1 == lab_o.reshape(-1)[cells]).all()
+    assert ev1 == (1 if s1[0] == s1[1] and s1[0] >= 0 else 0)
+    L.close()
+
+
+def test_conservation_fp32_full_foam_128(lbm):
+    """128^3 FP32 foam with the bench's launch plan: mass ledger and momentum."""
+    from paper_1708_01608_gb300.workloads import FOAM_128 as W
+    s = W["sites"]
+    bub = lbm.sample_sites(128, 128, 128, s["n"], s["r_min"], s["r_max"], s["min_spacing"],
+                           s["min_gap"], W["seed"])
+    L = lbm.Lattice("D3Q19", 128, 128, 128, tau=W["tau"], G=W["G"], storage="f32")
+    L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
+    t0 = L.totals()
+    L.inject(np.full(len(bub), W["rate"]), np.full(len(bub), W["budget"]))
+    L.step(100)
+    t1 = L.totals()
+    added = len(bub) * W["rate"] * 100
+    print("mass", t0, t1, t1[0] - t0[0], added)
+    # FP32 storage rounds every population each step: the ledger holds to a
+    # few ulp of the total mass per step
+    assert abs((t1[0] - t0[0]) - added) < 0.02 * added
+    assert np.abs(t1[1:]).max() < 1e-7 * t0[0]
+    assert np.allclose(L.read_budgets(), W["budget"] - 100 * W["rate"], rtol=0, atol=1e-12)
+    L.close()
+
+
+def test_full_size_sampled_cells_fp32(lbm):
+    """128^3 FP32, bench launch plan: one step checked cell by cell."""
+    from paper_1708_01608_gb300.workloads import FOAM_128 as W
+    s = W["sites"]
+    bub = lbm.sample_sites(128, 128, 128, s["n"], s["r_min"], s["r_max"], s["min_spacing"],
+                           s["min_gap"], W["seed"])
+    L = lbm.Lattice("D3Q19", 128, 128, 128, tau=W["tau"], G=W["G"], storage="f32")
+    L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
+    L.step(20)
+    f0 = L.read("f")
+    L.step(1)
+    f1 = L.read("f").reshape(19, -1)
+    rng = np.random.default_rng(0)
+    cells = np.concatenate([rng.integers(0, 128**3, 400),
+                            site_cells("D3Q19", bub, 128, 128, 128)[:16],
+                            [0, 127, 128 * 127, 128**3 - 1]])
+    ref = O.step_cells(O.D3Q19, f0, cells, W["tau"], W["G"])
+    got = f1[:, cells].T
+    assert rel_err(got, ref) < 1e-5
+    L.close()
+
+
+def test_deterministic_bits(lbm):
+    out = []
+    for _ in range(2):
+        L = lbm.Lattice("D3Q19", 40, 28, 20, storage="f32", tau=0.9)
+        L.seed_bubbles(np.array([[6, 5, 4, 3.0], [20, 14, 10, 4.0]]), 2.0, 0.15, 2.0, 1e-3, 5)
+        L.inject([1e-3, 1e-3], [0.1, 0.1])
+        L.step(25)
+        out.append(L.read("f"))
+        L.close()
+    assert (out[0] == out[1]).all()
+
+
+def test_fused_matches_two_pass_fp32(lbm):
+    res = []
+    for kernel in ("fused", "two_pass"):
+        L = lbm.Lattice("D3Q19", 64, 48, 40, storage="f32", tau=0.8, kernel=kernel)
+        L.seed_bubbles(np.array([[10, 10, 10, 5.0], [40, 30, 20, 6.0]]), 2.0, 0.15, 2.0, 1e-3, 9)
+        L.step(50)
+        res.append(L.read("f"))
+        L.close()
+    assert rel_err(res[0], res[1]) < 1e-6
