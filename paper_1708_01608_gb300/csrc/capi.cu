@@ -67,7 +67,7 @@ struct lbm_ctx {
   // fused kernel
   int kernel = LBM_KERNEL_FUSED;
   FusedPlan plan{};
-  CUtensorMap tmA{}, tmB{};
+  FusedMaps tmA{}, tmB{};
   DevBuf psi_scratch;
   // diagnostics
   DevBuf d_err, d_rho, d_p, d_tmp, d_j, d_u, d_labels, d_ncomp, d_part, d_tot, d_site_lab;
@@ -287,15 +287,23 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
   }
   if (c->kernel == LBM_KERNEL_FUSED) {
     cudaError_t e = fused_make_plan(c->lat, c->st, cfg->tile, c->v.NX, c->v.NY, c->v.NZ, 0, &c->plan);
-    if (e != cudaSuccess) return bail(fail(LBM_EINVAL, "tile does not fit this lattice/storage"));
-    e = fused_prepare(c->lat, c->st, c->plan);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (cfg->kernel == LBM_KERNEL_FUSED)
+        return bail(fail(LBM_EINVAL, "fused kernel: unknown tile, tile too large for this storage, "
+                                     "or nx not a multiple of 16 bytes of elements"));
+      c->kernel = LBM_KERNEL_TWO_PASS;  // automatic choice falls back to the two-pass path
+    }
+  }
+  if (c->kernel == LBM_KERNEL_FUSED) {
+    cudaError_t e = fused_prepare(c->lat, c->st, c->plan);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return bail(fail(LBM_ECUDA, std::string("fused kernel set-up: ") + cudaGetErrorString(e)));
     }
-    if (fused_encode_tmap(c->lat, c->st, c->plan, c->fA.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px,
+    if (fused_encode_maps(c->lat, c->st, c->plan, c->fA.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px,
                           &c->tmA) != CUDA_SUCCESS ||
-        fused_encode_tmap(c->lat, c->st, c->plan, c->fB.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px,
+        fused_encode_maps(c->lat, c->st, c->plan, c->fB.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px,
                           &c->tmB) != CUDA_SUCCESS)
       return bail(fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed"));
   } else {

@@ -3,7 +3,7 @@
 // Laplacian (the rupture criterion of Sec. 3.1 / Sec. 4 of the paper), FP64
 // totals, and connected-component labelling of gas cells.
 //
-// Stored populations are in pull form: stored_i(y) = f_i(y + c_i).
+// Stored populations are in push form: stored_i(x) = f_i(x, t).
 #include <type_traits>
 
 #include "internal.h"
@@ -105,10 +105,7 @@ __global__ void k_store_from(const View v, const double *src, int from_f, void *
     const Idx c = idx_of(k, v);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      // stored_i(y) = f_i(y + c_i)
-      const int64_t t = lin(wr(c.x + L::cx(i), (int)v.NX), wr(c.y + L::cy(i), (int)v.NY),
-                            wr(c.z + L::cz(i), (int)v.NZ), v);
-      const double val = from_f ? src[(int64_t)i * N + t] : L::w(i) * src[t];
+      const double val = from_f ? src[(int64_t)i * N + k] : L::w(i) * src[k];
       store_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), val, L::w(i) * v.rho_ref);
     }
   }
@@ -122,15 +119,11 @@ __global__ void k_gather_f(const View v, const void *stored, double *f) {
     const Idx c = idx_of(k, v);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      f[(int64_t)i * N + k] =
-          load_d<ST>(stored,
-                     sidx(i, wr(c.x - L::cx(i), (int)v.NX), wr(c.y - L::cy(i), (int)v.NY),
-                          wr(c.z - L::cz(i), (int)v.NZ), v),
-                     L::w(i) * v.rho_ref);
+      f[(int64_t)i * N + k] = load_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), L::w(i) * v.rho_ref);
   }
 }
 
-// one population: out(x) = f_i(x) = stored_i(x - c_i)
+// one population: out(x) = f_i(x) = stored_i(x)
 template <int LAT, int ST>
 __global__ void k_gather_pop(const View v, const void *stored, int i, double *out) {
   using L = Lattice<LAT>;
@@ -147,14 +140,11 @@ __global__ void k_gather_pop(const View v, const void *stored, int i, double *ou
   const int64_t N = v.NX * v.NY * v.NZ;
   GRID_LOOP(k, N) {
     const Idx c = idx_of(k, v);
-    out[k] = load_d<ST>(stored,
-                        sidx(i, wr(c.x - cx, (int)v.NX), wr(c.y - cy, (int)v.NY),
-                             wr(c.z - cz, (int)v.NZ), v),
-                        w * v.rho_ref);
+    out[k] = load_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), w * v.rho_ref);
   }
 }
 
-// one population: stored_i(y) = f_i(y + c_i) from canonical f_i (N doubles)
+// one population: stored_i(x) = f_i(x) from canonical f_i (N doubles)
 template <int LAT, int ST>
 __global__ void k_store_pop(const View v, const double *f, int i, void *stored) {
   using L = Lattice<LAT>;
@@ -171,8 +161,7 @@ __global__ void k_store_pop(const View v, const double *f, int i, void *stored) 
   const int64_t N = v.NX * v.NY * v.NZ;
   GRID_LOOP(k, N) {
     const Idx c = idx_of(k, v);
-    const int64_t t = lin(wr(c.x + cx, (int)v.NX), wr(c.y + cy, (int)v.NY), wr(c.z + cz, (int)v.NZ), v);
-    store_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), f[t], w * v.rho_ref);
+    store_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), f[k], w * v.rho_ref);
   }
 }
 
@@ -184,11 +173,7 @@ __device__ __forceinline__ void cell_moments(const View &v, const void *stored, 
   rho = jx = jy = jz = 0.0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const double f = load_d<ST>(stored,
-                                sidx(i, wr(c.x - L::cx(i), (int)v.NX),
-                                     wr(c.y - L::cy(i), (int)v.NY), wr(c.z - L::cz(i), (int)v.NZ),
-                                     v),
-                                L::w(i) * v.rho_ref);
+    const double f = load_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), L::w(i) * v.rho_ref);
     rho += f;
     jx += L::cx(i) * f;
     jy += L::cy(i) * f;

@@ -10,9 +10,8 @@ namespace sclbm {
 // Everything a step kernel needs.  Cells are addressed in the kernels'
 // three-dimensional view (D2Q9 on (nx, 1, ny)); the population arrays are
 // f[i][z][y][x] with a row pitch px >= NX (elements), planes of px*NY and
-// population blocks of px*NY*NZ.  fin holds the post-collision populations
-// of the previous step at their origin cell (pull form), fout receives the
-// post-collision populations of this step.
+// population blocks of px*NY*NZ.  fin holds f_i(x, t) at x (push form: the
+// populations that have arrived), fout receives f_i(x, t+1).
 struct StepArgs {
   const void *fin;
   void *fout;
@@ -34,6 +33,13 @@ struct StepArgs {
   int *err;  // device status word (ERR_* bits)
 };
 
+// TMA descriptors of one population lattice for the fused kernel: the
+// column box, the left/right halo-column box, the top/bottom halo-row box and
+// the corner box (all over the 4-D tensor x, y, z, population)
+struct FusedMaps {
+  CUtensorMap main, col, row, crn;
+};
+
 // fused-kernel launch plan
 struct FusedPlan {
   int tile;      // tile id (see fused_tile_shape)
@@ -43,30 +49,34 @@ struct FusedPlan {
   int items;     // tiles_x * tiles_y * nzc CTAs
   int threads;
   int smem;      // dynamic shared memory bytes
-  int box_w, box_h;
+  int hx;        // halo columns per box (16 bytes of elements)
 };
 
 // Tile shapes: returns false when the id is unknown for the lattice.
 bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage);
 // Fill *plan for a lattice; nzc <= 0 picks the number of z chunks from the
-// SM count.  Returns cudaErrorInvalidValue when the tile does not fit.
+// SM count.  Returns cudaErrorInvalidValue when the tile does not fit or nx
+// is not a multiple of the 16-byte halo width.
 cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ,
                             int nzc, FusedPlan *plan);
-// Encode the 4-D TMA descriptor of one population lattice for a plan.
-CUresult fused_encode_tmap(int lat, int st, const FusedPlan &plan, const void *base,
-                           int64_t NX, int64_t NY, int64_t NZ, int64_t px, CUtensorMap *tm);
+// Encode the TMA descriptors of one population lattice for a plan.
+CUresult fused_encode_maps(int lat, int st, const FusedPlan &plan, const void *base,
+                           int64_t NX, int64_t NY, int64_t NZ, int64_t px, FusedMaps *tm);
 cudaError_t fused_launch(int lat, int st, const FusedPlan &plan, const StepArgs &a,
-                         const CUtensorMap &tm_in, cudaStream_t s);
+                         const FusedMaps &tm_in, cudaStream_t s);
 // work item (CTA) owning a view cell, for the injection buckets
 int fused_item_of(const FusedPlan &plan, int64_t x, int64_t y, int64_t z);
 
 // per-storage entry points (one translation unit each)
-cudaError_t fused_launch_f64(int lat, const FusedPlan &, const StepArgs &, const CUtensorMap &,
+cudaError_t fused_launch_f64(int lat, const FusedPlan &, const StepArgs &, const FusedMaps &,
                              cudaStream_t);
-cudaError_t fused_launch_f32(int lat, const FusedPlan &, const StepArgs &, const CUtensorMap &,
+cudaError_t fused_launch_f32(int lat, const FusedPlan &, const StepArgs &, const FusedMaps &,
                              cudaStream_t);
 cudaError_t fused_launch_h16(int lat, int st, const FusedPlan &, const StepArgs &,
-                             const CUtensorMap &, cudaStream_t);
+                             const FusedMaps &, cudaStream_t);
+int fused_smem_f64(int lat, int tile);
+int fused_smem_f32(int lat, int tile);
+int fused_smem_h16(int lat, int st, int tile);
 cudaError_t fused_prepare(int lat, int st, const FusedPlan &plan);  // set smem attribute
 cudaError_t fused_prepare_f64(int lat, const FusedPlan &);
 cudaError_t fused_prepare_f32(int lat, const FusedPlan &);

@@ -1,20 +1,23 @@
 // Fused Shan-Chen collide-stream-force step (one kernel per time step).
 //
-// A CTA owns a BX x BY column of the lattice (x, y) and marches along z
-// through a chunk of planes.  For every destination plane P it stages, with
-// one 4-D TMA box per population, the post-collision populations that stream
-// into the column and its one-cell halo ring (pull scheme: population i of
-// destination cell x comes from x - c_i).  From the staged plane it computes
-// rho and psi of every cell of the column plus halo; psi lives in a ring of
-// four planes in shared memory, so the Shan-Chen force of plane P - 1, which
-// needs psi of planes P - 2 .. P, is available without a second pass over
-// the populations.  The interior cell's own populations are kept in
-// registers for the next iteration's collision.  Each cell is read from HBM
-// once and written once per step; halo cells are re-read from L2.
+// Populations are stored in push form: stored_i(x) = f_i(x, t), the value
+// that has arrived at x.  A CTA owns a BX x BY column of the lattice (x, y)
+// and marches along z through a chunk of planes.  For every plane P it
+// stages, with TMA, the populations of the column and of its one-cell halo
+// ring: one 4-D box {BX, BY, 1, Q} for the column (all Q populations in one
+// copy), boxes of HX columns for the left and right halo, one-row boxes for
+// the top and bottom halo and four corner boxes.  Each halo box is addressed
+// with already-wrapped coordinates, so periodic seams need no special case;
+// x boxes start on 16-byte boundaries (HX = 16 bytes of elements), which is
+// why the fused path needs nx to be a multiple of HX.
 //
-// Periodic seams: TMA fills out-of-range boxes with zeros; CTAs whose halo
-// crosses the x or y boundary overwrite those elements with the wrapped
-// values using plain loads (the z coordinate is wrapped before the copy).
+// From the staged plane it computes rho and psi of the column and halo into
+// a ring of four psi planes in shared memory; the interior cells'
+// populations stay in registers, and one iteration later the plane is
+// collided with psi of the planes above and below already in the ring.  The
+// post-collision populations are pushed to x + c_i with plain coalesced
+// stores.  Each population is read from HBM once and written once per step;
+// halo boxes are re-read from L2.
 //
 // Every wait on a TMA transaction is bounded (1 s); on timeout the CTA sets
 // ERR_TMA_TIMEOUT in the status word, waits (bounded) for its other copies
@@ -26,6 +29,8 @@
 
 namespace sclbm {
 
+constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+
 template <int LAT, int ST, int BX_, int BY_, int NS_>
 struct FusedK {
   using L = Lattice<LAT>;
@@ -35,48 +40,44 @@ struct FusedK {
   static constexpr int BX = BX_, BY = BY_, NS = NS_;
   static constexpr int Q = L::Q;
   static constexpr int HY = L::HAS_Y ? 1 : 0;
-  // x halo of the staged box: at least 2 source columns, rounded so that the
-  // box starts on a 16-byte boundary
-  static constexpr int HX = (16 / (int)sizeof(T)) > 2 ? 16 / (int)sizeof(T) : 2;
-  static constexpr int BW = BX + 2 * HX;
-  static constexpr int BH = BY + 2 * HY;
-  static constexpr int BOX_BYTES = BW * BH * (int)sizeof(T);
-  // a TMA box is at most 256 elements wide: rows wider than that are loaded
-  // as NSUB side-by-side boxes of SUBW elements (16-byte multiples), which
-  // is contiguous in shared memory only for single-row boxes
-  static constexpr int pick_nsub() {
-    for (int n = (BW + 255) / 256; n <= BW; ++n)
-      if (BW % n == 0 && ((BW / n) * (int)sizeof(T)) % 16 == 0) return n;
-    return -1;
-  }
-  static constexpr int NSUB = pick_nsub();
-  static constexpr int SUBW = BW / NSUB;
-  static_assert(NSUB > 0 && (NSUB == 1 || BH == 1), "unsupported tile width");
-  static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
-  static constexpr int STAGE_BYTES = Q * BOX_STRIDE;
+  static constexpr int SZ = (int)sizeof(T);
+  static constexpr int HX = 16 / SZ;  // halo columns loaded (one is used)
+  // staged boxes of one plane, each at a 128-byte aligned offset
+  static constexpr int MAIN_B = BX * BY * Q * SZ;  // [Q][BY][BX]
+  static constexpr int COL_B = HX * BY * Q * SZ;   // [Q][BY][HX]
+  static constexpr int ROW_B = BX * Q * SZ;        // [Q][BX]
+  static constexpr int CRN_B = HX * Q * SZ;        // [Q][HX]
+  static constexpr int OFF_L = round128(MAIN_B);
+  static constexpr int OFF_R = OFF_L + round128(COL_B);
+  static constexpr int OFF_T = OFF_R + round128(COL_B);
+  static constexpr int OFF_B = OFF_T + (HY ? round128(ROW_B) : 0);
+  static constexpr int OFF_TL = OFF_B + (HY ? round128(ROW_B) : 0);
+  static constexpr int OFF_TR = OFF_TL + (HY ? round128(CRN_B) : 0);
+  static constexpr int OFF_BL = OFF_TR + (HY ? round128(CRN_B) : 0);
+  static constexpr int OFF_BR = OFF_BL + (HY ? round128(CRN_B) : 0);
+  static constexpr int STAGE_BYTES = OFF_BR + (HY ? round128(CRN_B) : 0);
+  static constexpr int TX_BYTES = MAIN_B + 2 * COL_B + (HY ? 2 * ROW_B + 4 * CRN_B : 0);
   static constexpr int PW = BX + 2;
   static constexpr int PH = BY + 2 * HY;
   static constexpr int RING_BYTES = (4 * PW * PH * (int)sizeof(C) + 15) / 16 * 16;
   static constexpr int NT = BX * BY;
   static constexpr int SMEM = NS * STAGE_BYTES + RING_BYTES + NS * 8 + 128;
+  static_assert(BX <= 256 && BY <= 256 && Q <= 256, "TMA box dimensions are limited to 256");
+  static_assert(BX % HX == 0, "tiles must start on 16-byte boundaries");
+  static_assert(STAGE_BYTES % 128 == 0, "TMA destinations must be 128-byte aligned");
 };
-
-__device__ __forceinline__ int imod(int a, int n) {
-  int r = a % n;
-  return r < 0 ? r + n : r;
-}
 
 template <int LAT, int ST, int BX, int BY, int NS>
 __global__ void __launch_bounds__(BX *BY)
-    fused_step_kernel(const __grid_constant__ CUtensorMap tm, const StepArgs a, const int tiles_x,
+    fused_step_kernel(const __grid_constant__ FusedMaps tm, const StepArgs a, const int tiles_x,
                       const int tiles_y, const int zlen) {
   using K = FusedK<LAT, ST, BX, BY, NS>;
   using L = typename K::L;
   using S = typename K::S;
   using T = typename K::T;
   using C = typename K::C;
-  constexpr int Q = K::Q, HY = K::HY, HX = K::HX, BW = K::BW, PW = K::PW, PH = K::PH,
-                NT = K::NT;
+  constexpr int Q = K::Q, HY = K::HY, HX = K::HX, PW = K::PW, PH = K::PH, NT = K::NT;
+  constexpr bool F64 = sizeof(C) == 8;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
@@ -93,14 +94,16 @@ __global__ void __launch_bounds__(BX *BY)
   const int BXe = min(BX, NX - x0), BYe = min(BY, NY - y0);
   const int zs = zc * zlen, ze = min(NZ, zs + zlen);
   if (zs >= ze) return;
-  const int NPL = ze - zs + 2;  // staged destination planes zs-1 .. ze
-  const bool seam =
-      (x0 < 2) || (x0 + BXe + 2 > NX) || (HY && ((y0 < 2) || (y0 + BYe + 2 > NY)));
+  const int NPL = ze - zs + 2;  // staged planes zs-1 .. ze
   const bool active = tx < BXe && ty < BYe;
+  // wrapped coordinates of the halo boxes
+  const int xl = x0 == 0 ? NX - HX : x0 - HX;
+  const int xr = x0 + BXe == NX ? 0 : x0 + BXe;
+  const int yt = y0 == 0 ? NY - 1 : y0 - 1;
+  const int yb = y0 + BYe == NY ? 0 : y0 + BYe;
 
   const int64_t plane = a.px * a.NY;
   const int64_t popstride = plane * a.NZ;
-  const T *fin = static_cast<const T *>(a.fin);
   T *fout = static_cast<T *>(a.fout);
 
   const C G = (C)a.G, tau = (C)a.tau, omega = (C)(1.0 / a.tau), rho0 = (C)a.rho0,
@@ -113,23 +116,30 @@ __global__ void __launch_bounds__(BX *BY)
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
     fence_proxy_async_smem();
-    prefetch_tmap(&tm);
+    prefetch_tmap(&tm.main);
+    prefetch_tmap(&tm.col);
+    if (HY) {
+      prefetch_tmap(&tm.row);
+      prefetch_tmap(&tm.crn);
+    }
   }
   __syncthreads();
 
-  auto box = [&](int s, int i) -> const T * {
-    return reinterpret_cast<const T *>(smem + s * K::STAGE_BYTES + i * K::BOX_STRIDE);
-  };
   auto issue = [&](int k) {
     const int P = zs - 1 + k, s = k % NS;
-    mbar_arrive_expect_tx(&bars[s], (uint32_t)(Q * K::BOX_BYTES));
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-#pragma unroll
-      for (int j = 0; j < K::NSUB; ++j)
-        tma_load_4d(smem + s * K::STAGE_BYTES + i * K::BOX_STRIDE + j * K::SUBW * (int)sizeof(T),
-                    &tm, x0 - HX + j * K::SUBW, y0 - HY - L::cy(i), imod(P - L::cz(i), NZ), i,
-                    &bars[s]);
+    const int zp = P < 0 ? P + NZ : (P >= NZ ? P - NZ : P);
+    uint8_t *st = smem + s * K::STAGE_BYTES;
+    mbar_arrive_expect_tx(&bars[s], (uint32_t)K::TX_BYTES);
+    tma_load_4d(st, &tm.main, x0, y0, zp, 0, &bars[s]);
+    tma_load_4d(st + K::OFF_L, &tm.col, xl, y0, zp, 0, &bars[s]);
+    tma_load_4d(st + K::OFF_R, &tm.col, xr, y0, zp, 0, &bars[s]);
+    if (HY) {
+      tma_load_4d(st + K::OFF_T, &tm.row, x0, yt, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_B, &tm.row, x0, yb, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_TL, &tm.crn, xl, yt, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_TR, &tm.crn, xr, yt, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_BL, &tm.crn, xl, yb, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_BR, &tm.crn, xr, yb, zp, 0, &bars[s]);
     }
   };
   if (tid == 0) {
@@ -142,6 +152,11 @@ __global__ void __launch_bounds__(BX *BY)
     send = a.bucket_off[item + 1];
   }
 
+  // destination coordinates of the push, fixed per thread (periodic)
+  const int x = x0 + tx, y = y0 + ty;
+  const int xm = x == 0 ? NX - 1 : x - 1, xp = x + 1 >= NX ? 0 : x + 1;
+  const int ym = y == 0 ? NY - 1 : y - 1, yp = y + 1 >= NY ? 0 : y + 1;
+
   C cur[Q], nxt[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) cur[i] = nxt[i] = 0;
@@ -150,44 +165,8 @@ __global__ void __launch_bounds__(BX *BY)
     const int s = k % NS;
     const int P = zs - 1 + k;
     const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((k / NS) & 1), 1000000000ull);
-
-    if (seam) {
-      // Wrapped halo elements: TMA read zeros outside [0,NX) x [0,NY).
-      const int rowsA = BYe + 2 * HY;
-      const int nA = Q * rowsA * 4;
-      const int nB = HY ? Q * 4 * (BXe + 4) : 0;
-      for (int e = tid; e < nA + nB; e += NT) {
-        int i, dy, lc;
-        if (e < nA) {
-          i = e / (rowsA * 4);
-          const int r = e % (rowsA * 4);
-          dy = r / 4 - HY;
-          const int j = r % 4;
-          lc = j < 2 ? j - 2 : BXe + j - 2;
-        } else {
-          const int e2 = e - nA;
-          i = e2 / (4 * (BXe + 4));
-          const int r = e2 % (4 * (BXe + 4));
-          const int rs = r / (BXe + 4);
-          dy = rs == 0 ? -1 : (rs == 1 ? 0 : (rs == 2 ? BYe - 1 : BYe));
-          lc = r % (BXe + 4) - 2;
-        }
-        int cyi = 0, czi = 0;
-#pragma unroll
-        for (int m = 0; m < Q; ++m)
-          if (m == i) {
-            cyi = L::cy(m);
-            czi = L::cz(m);
-          }
-        const int gx = x0 + lc, gy = y0 + dy - cyi;
-        if (gx >= 0 && gx < NX && gy >= 0 && gy < NY) continue;
-        const int64_t src = (int64_t)i * popstride + (int64_t)imod(P - czi, NZ) * plane +
-                            (int64_t)imod(gy, NY) * a.px + imod(gx, NX);
-        T *dst = reinterpret_cast<T *>(smem + s * K::STAGE_BYTES + i * K::BOX_STRIDE);
-        dst[(dy + HY) * BW + lc + HX] = fin[src];
-      }
-      __syncthreads();
-    }
+    const uint8_t *st = smem + s * K::STAGE_BYTES;
+    const T *mainb = reinterpret_cast<const T *>(st);
 
     // ---- psi of plane P for the column and its halo ring
     C *rk = ring + (k & 3) * PW * PH;
@@ -195,7 +174,7 @@ __global__ void __launch_bounds__(BX *BY)
       C rho = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const C v = S::load(box(s, i)[(ty + HY) * BW + tx - L::cx(i) + HX], wref[i]);
+        const C v = S::load(mainb[(i * BY + ty) * BX + tx], wref[i]);
         nxt[i] = v;
         rho += v;
       }
@@ -220,10 +199,34 @@ __global__ void __launch_bounds__(BX *BY)
         dx = h == 0 ? -1 : BXe;
         dy = 0;
       }
+      // staged box holding (dx, dy): element of population 0 and the
+      // distance between populations
+      const int cxr = dx < 0 ? 0 : (dx >= BXe ? 2 : 1);
+      const int cyr = dy < 0 ? 0 : (dy >= BYe ? 2 : 1);
+      int off, e, pstride;
+      if (cyr == 1) {
+        if (cxr == 1) {
+          off = 0;
+          e = dy * BX + dx;
+          pstride = BY * BX;
+        } else {
+          off = cxr == 0 ? K::OFF_L : K::OFF_R;
+          e = dy * HX + (cxr == 0 ? HX - 1 : 0);
+          pstride = BY * HX;
+        }
+      } else if (cxr == 1) {
+        off = cyr == 0 ? K::OFF_T : K::OFF_B;
+        e = dx;
+        pstride = BX;
+      } else {
+        off = cyr == 0 ? (cxr == 0 ? K::OFF_TL : K::OFF_TR) : (cxr == 0 ? K::OFF_BL : K::OFF_BR);
+        e = cxr == 0 ? HX - 1 : 0;
+        pstride = HX;
+      }
+      const T *b = reinterpret_cast<const T *>(st + off) + e;
       C rho = 0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
-        rho += S::load(box(s, i)[(dy + HY) * BW + dx - L::cx(i) + HX], wref[i]);
+      for (int i = 0; i < Q; ++i) rho += S::load(b[i * pstride], wref[i]);
       rk[(dy + HY) * PW + dx + 1] = psi_of(rho, rho0, inv_rho0);
     }
 
@@ -236,12 +239,9 @@ __global__ void __launch_bounds__(BX *BY)
       }
       return;
     }
-    if (tid == 0 && k + NS < NPL) {
-      fence_proxy_async_smem();
-      issue(k + NS);
-    }
+    if (tid == 0 && k + NS < NPL) issue(k + NS);
 
-    // ---- collide plane P - 1 (needs psi of P - 2, P - 1, P)
+    // ---- collide plane P - 1 (needs psi of P - 2, P - 1, P) and push
     if (k >= 2) {
       const int Pc = P - 1;
       double dm = 0.0;  // blowing-agent mass deposited in this cell this step
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(BX *BY)
         for (int q = sp; q < send; ++q) {
           const int sidx = a.bucket_site[q];
           if (a.site_z[sidx] != Pc) break;
-          if (active && a.site_x[sidx] == x0 + tx && a.site_y[sidx] == y0 + ty) {
+          if (active && a.site_x[sidx] == x && a.site_y[sidx] == y) {
             const double b = a.budget[sidx];
             if (b > 0.0) {
               const double d = fmin(a.rate[sidx], b);
@@ -284,17 +284,40 @@ __global__ void __launch_bounds__(BX *BY)
         }
         const C gp = -G * p0[c0];
         const C Fx = gp * sx, Fy = gp * sy, Fz = gp * sz;
-        const C ir = (C)1 / rho;
-        const C ux = (jx + tau * Fx) * ir, uy = (jy + tau * Fy) * ir, uz = (jz + tau * Fz) * ir;
+        C ux, uy, uz;
+        if (F64) {  // FP64 keeps the oracle's operation order
+          ux = (jx + tau * Fx) / rho;
+          uy = (jy + tau * Fy) / rho;
+          uz = (jz + tau * Fz) / rho;
+        } else {
+          const C ir = (C)1 / rho;
+          ux = (jx + tau * Fx) * ir;
+          uy = (jy + tau * Fy) * ir;
+          uz = (jz + tau * Fz) * ir;
+        }
         const C uu = (C)1.5 * (ux * ux + uy * uy + uz * uz);
-        T *o = fout + (int64_t)Pc * plane + (int64_t)(y0 + ty) * a.px + x0 + tx;
+        const int zm = Pc == 0 ? NZ - 1 : Pc - 1, zp = Pc + 1 >= NZ ? 0 : Pc + 1;
+        // FP32: the rest population takes rho minus the moving ones, so the
+        // collision conserves mass to rounding (FP32 weights do not sum to 1)
+        constexpr int i0 = F64 ? 0 : 1;
+        C moved = 0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        for (int i = i0; i < Q; ++i) {
           const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
           const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
-          C fs = cur[i] - omega * (cur[i] - feq);
+          C fs = F64 ? cur[i] - (cur[i] - feq) / tau : cur[i] - omega * (cur[i] - feq);
+          moved += fs;
           if (dm != 0.0) fs += (C)(L::w(i) * dm);
-          o[(int64_t)i * popstride] = S::store(fs, wref[i]);
+          const int X = L::cx(i) > 0 ? xp : (L::cx(i) < 0 ? xm : x);
+          const int Y = L::cy(i) > 0 ? yp : (L::cy(i) < 0 ? ym : y);
+          const int Z = L::cz(i) > 0 ? zp : (L::cz(i) < 0 ? zm : Pc);
+          fout[(int64_t)i * popstride + (int64_t)Z * plane + (int64_t)Y * a.px + X] =
+              S::store(fs, wref[i]);
+        }
+        if (!F64) {
+          C fs0 = rho - moved;
+          if (dm != 0.0) fs0 += (C)(L::w(0) * dm);
+          fout[(int64_t)Pc * plane + (int64_t)y * a.px + x] = S::store(fs0, wref[0]);
         }
       }
     }
@@ -311,7 +334,7 @@ cudaError_t fused_prepare_t() {
 }
 
 template <int LAT, int ST, int BX, int BY, int NS>
-cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const CUtensorMap &tm,
+cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const FusedMaps &tm,
                            cudaStream_t s) {
   using K = FusedK<LAT, ST, BX, BY, NS>;
   fused_step_kernel<LAT, ST, BX, BY, NS>
@@ -319,25 +342,21 @@ cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const CUtensor
   return cudaGetLastError();
 }
 
-template <int LAT, int ST, int BX, int BY, int NS>
-int fused_smem_t() {
-  return FusedK<LAT, ST, BX, BY, NS>::SMEM;
-}
-
 // Tile table shared by every storage type: id -> (BX, BY, NS).
 #define SCLBM_D3Q19_TILES(X) \
   X(1, 32, 8, 3)             \
   X(2, 32, 4, 4)             \
   X(3, 64, 4, 3)             \
-  X(4, 64, 8, 2)
+  X(4, 64, 8, 2)             \
+  X(5, 128, 4, 2)
 #define SCLBM_D2Q9_TILES(X) \
   X(1, 256, 1, 4)           \
   X(2, 128, 1, 4)           \
-  X(3, 512, 1, 4)
+  X(3, 64, 1, 6)
 
 // Dispatch of one storage type over the tile table.
 template <int ST>
-cudaError_t fused_launch_st(int lat, const FusedPlan &p, const StepArgs &a, const CUtensorMap &tm,
+cudaError_t fused_launch_st(int lat, const FusedPlan &p, const StepArgs &a, const FusedMaps &tm,
                             cudaStream_t s) {
 #define SCLBM_X3(id, bx, by, ns) \
   case id:                       \
@@ -371,6 +390,24 @@ cudaError_t fused_prepare_st(int lat, const FusedPlan &p) {
 #undef SCLBM_X3
 #undef SCLBM_X2
   return cudaErrorInvalidValue;
+}
+
+template <int ST>
+int fused_smem_st(int lat, int tile) {
+#define SCLBM_X3(id, bx, by, ns) \
+  case id:                       \
+    return FusedK<D3Q19, ST, bx, by, ns>::SMEM;
+#define SCLBM_X2(id, bx, by, ns) \
+  case id:                       \
+    return FusedK<D2Q9, ST, bx, by, ns>::SMEM;
+  if (lat == D3Q19) {
+    switch (tile) { SCLBM_D3Q19_TILES(SCLBM_X3) }
+  } else {
+    switch (tile) { SCLBM_D2Q9_TILES(SCLBM_X2) }
+  }
+#undef SCLBM_X3
+#undef SCLBM_X2
+  return -1;
 }
 
 }  // namespace sclbm

@@ -3,11 +3,14 @@
 
 namespace sclbm {
 cudaError_t fused_launch_h16(int lat, int st, const FusedPlan &p, const StepArgs &a,
-                             const CUtensorMap &tm, cudaStream_t s) {
+                             const FusedMaps &tm, cudaStream_t s) {
   return st == ST_F16 ? fused_launch_st<ST_F16>(lat, p, a, tm, s)
                       : fused_launch_st<ST_BF16>(lat, p, a, tm, s);
 }
 cudaError_t fused_prepare_h16(int lat, int st, const FusedPlan &p) {
   return st == ST_F16 ? fused_prepare_st<ST_F16>(lat, p) : fused_prepare_st<ST_BF16>(lat, p);
+}
+int fused_smem_h16(int lat, int st, int tile) {
+  return st == ST_F16 ? fused_smem_st<ST_F16>(lat, tile) : fused_smem_st<ST_BF16>(lat, tile);
 }
 }  // namespace sclbm

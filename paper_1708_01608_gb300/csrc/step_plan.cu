@@ -23,41 +23,34 @@ bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage) 
   return false;
 }
 
-// Same arithmetic as FusedK, evaluated on the host.
-static int fused_smem_bytes(int lat, int st, int bx, int by, int ns, int *box_w, int *box_h) {
-  const int Q = lat == D3Q19 ? 19 : 9;
-  const int hy = lat == D3Q19 ? 1 : 0;
-  const int sz = (int)storage_bytes(st);
-  const int csz = st == ST_F64 ? 8 : 4;
-  const int hx = std::max(2, 16 / sz);
-  const int bw = bx + 2 * hx, bh = by + 2 * hy;
-  const int box_stride = (bw * bh * sz + 127) / 128 * 128;
-  const int ring = (4 * (bx + 2) * (by + 2 * hy) * csz + 15) / 16 * 16;
-  int nsub = (bw + 255) / 256;
-  while (nsub <= bw && (bw % nsub != 0 || ((bw / nsub) * sz) % 16 != 0)) ++nsub;
-  *box_w = bw / nsub;  // width of one TMA box
-  *box_h = bh;
-  return ns * Q * box_stride + ring + ns * 8 + 128;
+static int fused_smem_bytes(int lat, int st, int tile) {
+  switch (st) {
+    case ST_F64: return fused_smem_f64(lat, tile);
+    case ST_F32: return fused_smem_f32(lat, tile);
+    default: return fused_smem_h16(lat, st, tile);
+  }
 }
 
 cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ, int nzc,
                             FusedPlan *p) {
   int bx, by, ns;
-  if (tile <= 0) tile = (lat == D3Q19) ? 1 : 1;
+  if (tile <= 0) tile = 1;
   if (!fused_tile_shape(lat, st, tile, &bx, &by, &ns)) return cudaErrorInvalidValue;
   p->tile = tile;
   p->bx = bx;
   p->by = by;
   p->nstage = ns;
   p->threads = bx * by;
-  p->smem = fused_smem_bytes(lat, st, bx, by, ns, &p->box_w, &p->box_h);
+  p->hx = (int)(16 / storage_bytes(st));
+  p->smem = fused_smem_bytes(lat, st, tile);
+  if (NX % p->hx != 0) return cudaErrorInvalidValue;  // halo boxes must start on 16 bytes
   int dev = 0, nsm = 0, smem_optin = 0, smem_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  if (p->smem > smem_optin) return cudaErrorInvalidValue;
+  if (p->smem <= 0 || p->smem > smem_optin) return cudaErrorInvalidValue;
   p->tiles_x = (int)((NX + bx - 1) / bx);
   p->tiles_y = (int)((NY + by - 1) / by);
   const int ntiles = p->tiles_x * p->tiles_y;
@@ -98,8 +91,8 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-CUresult fused_encode_tmap(int lat, int st, const FusedPlan &p, const void *base, int64_t NX,
-                           int64_t NY, int64_t NZ, int64_t px, CUtensorMap *tm) {
+CUresult fused_encode_maps(int lat, int st, const FusedPlan &p, const void *base, int64_t NX,
+                           int64_t NY, int64_t NZ, int64_t px, FusedMaps *tm) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return CUDA_ERROR_NOT_FOUND;
   const int Q = lat == D3Q19 ? 19 : 9;
@@ -111,15 +104,21 @@ CUresult fused_encode_tmap(int lat, int st, const FusedPlan &p, const void *base
   cuuint64_t dims[4] = {(cuuint64_t)NX, (cuuint64_t)NY, (cuuint64_t)NZ, (cuuint64_t)Q};
   cuuint64_t strides[3] = {(cuuint64_t)(px * sz), (cuuint64_t)(px * NY * sz),
                            (cuuint64_t)(px * NY * NZ * sz)};
-  cuuint32_t box[4] = {(cuuint32_t)p.box_w, (cuuint32_t)p.box_h, 1, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
-  return enc(tm, dt, 4, const_cast<void *>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const cuuint32_t bx = p.bx, by = p.by, hx = p.hx, q = Q;
+  const cuuint32_t boxes[4][4] = {{bx, by, 1, q}, {hx, by, 1, q}, {bx, 1, 1, q}, {hx, 1, 1, q}};
+  CUtensorMap *maps[4] = {&tm->main, &tm->col, &tm->row, &tm->crn};
+  for (int m = 0; m < 4; ++m) {
+    CUresult r = enc(maps[m], dt, 4, const_cast<void *>(base), dims, strides, boxes[m], estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return r;
+  }
+  return CUDA_SUCCESS;
 }
 
 cudaError_t fused_launch(int lat, int st, const FusedPlan &p, const StepArgs &a,
-                         const CUtensorMap &tm, cudaStream_t s) {
+                         const FusedMaps &tm, cudaStream_t s) {
   switch (st) {
     case ST_F64:
       return fused_launch_f64(lat, p, a, tm, s);

@@ -1,6 +1,6 @@
-// Two-pass Shan-Chen step: pass 1 computes psi(x) for every cell from the
-// gathered populations; pass 2 gathers the populations again, takes psi of
-// the neighbours from that field, collides and writes.  The blowing-agent
+// Two-pass Shan-Chen step (push form, stored_i(x) = f_i(x, t)): pass 1
+// computes psi(x) for every cell; pass 2 reads the populations again, takes
+// psi of the neighbours from that field, collides and pushes f*_i to x + c_i.  The blowing-agent
 // injection runs as a third, one-thread-per-site kernel.  This path moves
 // 3*Q*S + 2*sizeof(psi) bytes per update instead of the fused kernel's
 // 2*Q*S; it is kept as a simple, independently written comparison path.
@@ -36,13 +36,10 @@ __global__ void tp_psi_kernel(const StepArgs a, typename Storage<ST>::C *psi) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = cell_of(k, a.NX, a.NY);
+    const int64_t o = (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
     C rho = 0;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      const int sx = wrapi(c.x - L::cx(i), (int)a.NX), sy = wrapi(c.y - L::cy(i), (int)a.NY),
-                sz = wrapi(c.z - L::cz(i), (int)a.NZ);
-      rho += S::load(f[i * pop + sz * plane + sy * a.px + sx], (C)(L::w(i) * a.rho_ref));
-    }
+    for (int i = 0; i < L::Q; ++i) rho += S::load(f[i * pop + o], (C)(L::w(i) * a.rho_ref));
     psi[k] = psi_of(rho, rho0, inv_rho0);
   }
 }
@@ -64,11 +61,10 @@ __global__ void tp_collide_kernel(const StepArgs a, const typename Storage<ST>::
     const Cell c = cell_of(k, a.NX, a.NY);
     C fi[L::Q];
     C rho = 0, jx = 0, jy = 0, jz = 0;
+    const int64_t own = (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      const int sx = wrapi(c.x - L::cx(i), NX), sy = wrapi(c.y - L::cy(i), NY),
-                sz = wrapi(c.z - L::cz(i), NZ);
-      fi[i] = S::load(f[i * pop + sz * plane + sy * a.px + sx], (C)(L::w(i) * a.rho_ref));
+      fi[i] = S::load(f[i * pop + own], (C)(L::w(i) * a.rho_ref));
       rho += fi[i];
       jx += (C)L::cx(i) * fi[i];
       jy += (C)L::cy(i) * fi[i];
@@ -85,33 +81,46 @@ __global__ void tp_collide_kernel(const StepArgs a, const typename Storage<ST>::
       sz += (C)L::cz(i) * wp;
     }
     const C gp = -G * psi[k];
-    const C ir = (C)1 / rho;
-    const C ux = (jx + tau * gp * sx) * ir, uy = (jy + tau * gp * sy) * ir,
-            uz = (jz + tau * gp * sz) * ir;
+    C ux, uy, uz;
+    if (sizeof(C) == 8) {  // FP64 keeps the oracle's operation order
+      ux = (jx + tau * gp * sx) / rho;
+      uy = (jy + tau * gp * sy) / rho;
+      uz = (jz + tau * gp * sz) / rho;
+    } else {
+      const C ir = (C)1 / rho;
+      ux = (jx + tau * gp * sx) * ir;
+      uy = (jy + tau * gp * sy) * ir;
+      uz = (jz + tau * gp * sz) * ir;
+    }
     const C uu = (C)1.5 * (ux * ux + uy * uy + uz * uz);
-    T *o = g + (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
+    constexpr int i0 = sizeof(C) == 8 ? 0 : 1;
+    C moved = 0;  // FP32: rest population = rho - moving ones (mass to rounding)
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
+    for (int i = i0; i < L::Q; ++i) {
       const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
       const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
-      o[i * pop] = S::store(fi[i] - omega * (fi[i] - feq), (C)(L::w(i) * a.rho_ref));
+      const C fs = sizeof(C) == 8 ? fi[i] - (fi[i] - feq) / tau : fi[i] - omega * (fi[i] - feq);
+      moved += fs;
+      const int X = wrapi(c.x + L::cx(i), NX), Y = wrapi(c.y + L::cy(i), NY),
+                Z = wrapi(c.z + L::cz(i), NZ);
+      g[i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X] =
+          S::store(fs, (C)(L::w(i) * a.rho_ref));
     }
+    if (sizeof(C) == 4) g[own] = S::store(rho - moved, (C)(L::w(0) * a.rho_ref));
   }
 }
 
-// One thread per distinct site cell: deposits the blowing-agent mass of every
-// site of that cell (budgets updated in site order).
 template <int LAT, int ST>
 __global__ void tp_inject_kernel(const StepArgs a) {
   using L = Lattice<LAT>;
   using S = Storage<ST>;
   using T = typename S::T;
   using C = typename S::C;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.ngroups) return;
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.ngroups) return;
   double dm = 0.0;
   int s0 = -1;
-  for (int q = a.group_off[g]; q < a.group_off[g + 1]; ++q) {
+  for (int q = a.group_off[gi]; q < a.group_off[gi + 1]; ++q) {
     const int s = a.group_site[q];
     s0 = s;
     const double b = a.budget[s];
@@ -122,13 +131,17 @@ __global__ void tp_inject_kernel(const StepArgs a) {
     }
   }
   if (dm == 0.0 || s0 < 0) return;
+  // the deposit is part of f* at the site, which has been pushed to x_s + c_i
   const int64_t plane = a.px * a.NY, pop = plane * a.NZ;
-  T *o = static_cast<T *>(a.fout) + (int64_t)a.site_z[s0] * plane + (int64_t)a.site_y[s0] * a.px +
-         a.site_x[s0];
+  T *g = static_cast<T *>(a.fout);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
+    const int X = wrapi(a.site_x[s0] + L::cx(i), (int)a.NX),
+              Y = wrapi(a.site_y[s0] + L::cy(i), (int)a.NY),
+              Z = wrapi(a.site_z[s0] + L::cz(i), (int)a.NZ);
+    T *o = g + i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X;
     const C wref = (C)(L::w(i) * a.rho_ref);
-    o[i * pop] = S::store(S::load(o[i * pop], wref) + (C)(L::w(i) * dm), wref);
+    *o = S::store(S::load(*o, wref) + (C)(L::w(i) * dm), wref);
   }
 }
 
