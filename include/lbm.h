@@ -104,7 +104,14 @@ typedef struct {
   lbm_alloc_fn alloc;   /* NULL: cudaMalloc/cudaFree */
   lbm_free_fn free;
   void *alloc_user;
+  int32_t debug_flags;  /* 0 in normal use.  LBM_DEBUG_WITHHOLD_TMA: every
+                           fused-kernel CTA skips the TMA copies of its
+                           second staged plane, so that its bounded wait
+                           (1 s) expires and lbm_sync reports LBM_ETIMEOUT;
+                           exercises the timeout path without a fault */
 } lbm_config;
+
+#define LBM_DEBUG_WITHHOLD_TMA 1
 
 typedef struct {
   double x, y, z, r; /* centre (cell coordinates; z = 0 in 2-D) and radius */
@@ -167,6 +174,20 @@ lbm_status lbm_read_budgets(lbm_ctx *ctx, double *budget, int32_t n);
  * ESTATE (not seeded), EINVAL (nsteps < 0), ECUDA, or a sticky ETIMEOUT from
  * an earlier step. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Autotuner: time every fused-kernel tile that fits this lattice and storage
+ * (two warm-up steps, then `steps` timed steps each, starting from the
+ * current state) and keep the fastest for later lbm_step calls.  The
+ * populations, budgets and step counter are restored afterwards, so the
+ * call has no effect on results.  *best_tile and *best_ms (either may be
+ * NULL) receive the chosen tile id and its time per step.  Errors: ESTATE
+ * (not seeded), EINVAL (two-pass context, steps < 1), ENOMEM, ECUDA. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *best_tile, double *best_ms);
+
+/* Launch plan of the step kernel: out = {kernel (lbm_kernel), tile id,
+ * tile x extent, tile y extent, z chunks, CTAs per step}; tile fields are 0
+ * for the two-pass kernel. */
+lbm_status lbm_plan_info(const lbm_ctx *ctx, int32_t out[6]);
 
 /* Number of steps taken since seeding. */
 int64_t lbm_step_count(const lbm_ctx *ctx);

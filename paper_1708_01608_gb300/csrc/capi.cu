@@ -234,8 +234,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(LBM_EINVAL, "extents must be >= 1");
   if (cfg->lattice == LBM_D2Q9 && cfg->nz != 1) return fail(LBM_EINVAL, "D2Q9 needs nz == 1");
   if (cfg->nx > (1 << 20) || cfg->ny > (1 << 20) || cfg->nz > (1 << 20) ||
-      cfg->nx * cfg->ny * cfg->nz > ((int64_t)1 << 31) - 1)
-    return fail(LBM_EINVAL, "lattice too large (cells must fit int32 labels)");
+      ((cfg->nx + 7) / 8 * 8) * cfg->ny * cfg->nz > ((int64_t)1 << 31) - 1)
+    return fail(LBM_EINVAL, "lattice too large (padded cells must fit 32-bit offsets)");
   if (!(cfg->tau > 0.5) || !std::isfinite(cfg->tau)) return fail(LBM_EINVAL, "tau must be > 0.5");
   if (!(cfg->rho0 > 0) || !std::isfinite(cfg->G)) return fail(LBM_EINVAL, "rho0 must be > 0, G finite");
   if (cfg->kernel < LBM_KERNEL_AUTO || cfg->kernel > LBM_KERNEL_TWO_PASS)
@@ -482,9 +482,18 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.bucket_off = static_cast<const int32_t *>(c->d_boff.p);
   a.bucket_site = static_cast<const int32_t *>(c->d_blist.p);
   a.err = static_cast<int *>(c->d_err.p);
+  a.debug_flags = c->cfg.debug_flags;
+  a.tau_f = (float)c->cfg.tau;
+  a.omega_f = (float)(1.0 / c->cfg.tau);
+  a.G_f = (float)c->cfg.G;
+  a.rho0_f = (float)c->cfg.rho0;
+  a.inv_rho0_f = (float)(1.0 / c->cfg.rho0);
+  a.rho_ref_f = (float)c->cfg.rho_ref;
+  const size_t pop_bytes = (size_t)c->v.px * c->v.NY * c->v.NZ * storage_bytes(c->st);
   for (int64_t t = 0; t < nsteps; ++t) {
     a.fin = lattice_ptr(c, c->cur);
     a.fout = lattice_ptr(c, 1 - c->cur);
+    for (int i = 0; i < c->Q; ++i) a.out_pop[i] = static_cast<char *>(a.fout) + i * pop_bytes;
     cudaError_t e;
     if (c->kernel == LBM_KERNEL_FUSED)
       e = fused_launch(c->lat, c->st, c->plan, a, c->cur == 0 ? c->tmA : c->tmB, c->s);
@@ -502,6 +511,113 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
 }
 
 int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+lbm_status lbm_plan_info(const lbm_ctx *c, int32_t out[6]) {
+  if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+  const bool fused = c->kernel == LBM_KERNEL_FUSED;
+  out[0] = c->kernel;
+  out[1] = fused ? c->plan.tile : 0;
+  out[2] = fused ? c->plan.bx : 0;
+  out[3] = fused ? c->plan.by : 0;
+  out[4] = fused ? c->plan.nzc : 0;
+  out[5] = fused ? c->plan.items : 0;
+  return LBM_OK;
+}
+
+// switch the fused kernel to another plan: smem attribute, descriptors and
+// the per-CTA injection buckets
+static lbm_status use_plan(lbm_ctx *c, const FusedPlan &p) {
+  CK(fused_prepare(c->lat, c->st, p));
+  FusedMaps ma, mb;
+  if (fused_encode_maps(c->lat, c->st, p, c->fA.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px, &ma) !=
+          CUDA_SUCCESS ||
+      fused_encode_maps(c->lat, c->st, p, c->fB.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px, &mb) !=
+          CUDA_SUCCESS)
+    return fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed");
+  c->plan = p;
+  c->tmA = ma;
+  c->tmB = mb;
+  if (c->ninj > 0) CKS(build_buckets(c));
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best_tile, double *best_ms) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
+  if (c->kernel != LBM_KERNEL_FUSED) return fail(LBM_EINVAL, "autotuning applies to the fused kernel");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  // save the state: current lattice, budgets, step counter
+  DevBuf save_f, save_b;
+  lbm_status st = dalloc(c, save_f, c->lat_bytes);
+  if (st != LBM_OK) return st;
+  const size_t bbytes = sizeof(double) * (size_t)std::max(c->ninj, 1);
+  if ((st = dalloc(c, save_b, bbytes)) != LBM_OK) {
+    dfree(c, save_f);
+    return st;
+  }
+  const int cur0 = c->cur;
+  const int64_t steps0 = c->steps;
+  auto restore = [&]() -> lbm_status {
+    CK(cudaMemcpyAsync(lattice_ptr(c, cur0), save_f.p, c->lat_bytes, cudaMemcpyDeviceToDevice, c->s));
+    if (c->ninj > 0)
+      CK(cudaMemcpyAsync(c->d_budget.p, save_b.p, sizeof(double) * c->ninj,
+                         cudaMemcpyDeviceToDevice, c->s));
+    c->cur = cur0;
+    c->steps = steps0;
+    return LBM_OK;
+  };
+  auto body = [&]() -> lbm_status {
+    CK(cudaMemcpyAsync(save_f.p, lattice_ptr(c, cur0), c->lat_bytes, cudaMemcpyDeviceToDevice, c->s));
+    if (c->ninj > 0)
+      CK(cudaMemcpyAsync(save_b.p, c->d_budget.p, sizeof(double) * c->ninj,
+                         cudaMemcpyDeviceToDevice, c->s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    FusedPlan best{};
+    float best_t = 1e30f;
+    for (int tile = 1; tile < 64; ++tile) {
+      int bx, by, ns;
+      if (!fused_tile_shape(c->lat, c->st, tile, &bx, &by, &ns)) continue;
+      FusedPlan p;
+      if (fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, 0, &p) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      CKS(use_plan(c, p));
+      CKS(lbm_step(c, 2));
+      CK(cudaEventRecord(e0, c->s));
+      CKS(lbm_step(c, steps));
+      CK(cudaEventRecord(e1, c->s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= steps;
+      CKS(restore());
+      if (ms < best_t) {
+        best_t = ms;
+        best = p;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best.tile == 0) return fail(LBM_ECUDA, "no tile could be timed");
+    CKS(use_plan(c, best));
+    if (best_tile) *best_tile = best.tile;
+    if (best_ms) *best_ms = best_t;
+    return LBM_OK;
+  };
+  st = body();
+  if (st != LBM_OK) restore();
+  cudaError_t e = cudaStreamSynchronize(c->s);
+  dfree(c, save_f);
+  dfree(c, save_b);
+  if (st == LBM_OK && e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
+  if (st == LBM_OK) st = sync_and_check(c);
+  return st;
+}
 
 lbm_status lbm_sync(lbm_ctx *c) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");

@@ -37,14 +37,11 @@ __device__ __forceinline__ int64_t sidx(int i, int x, int y, int z, const View &
 
 template <int ST>
 __device__ __forceinline__ double load_d(const void *p, int64_t k, double wref) {
-  using S = Storage<ST>;
-  return (double)S::load(static_cast<const typename S::T *>(p)[k], (typename S::C)wref);
+  return decode_f<ST>(static_cast<const typename Storage<ST>::T *>(p)[k], wref);
 }
 template <int ST>
 __device__ __forceinline__ void store_d(void *p, int64_t k, double v, double wref) {
-  using S = Storage<ST>;
-  using C = typename S::C;
-  static_cast<typename S::T *>(p)[k] = S::store((C)v, (C)wref);
+  static_cast<typename Storage<ST>::T *>(p)[k] = encode_f<ST>(v, wref);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014): the k-th output of the generator

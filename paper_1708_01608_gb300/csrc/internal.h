@@ -17,6 +17,10 @@ struct StepArgs {
   void *fout;
   int64_t NX, NY, NZ, px;
   double tau, G, rho0, rho_ref;
+  // the same constants in FP32 (the FP32-arithmetic kernels use no FP64)
+  float tau_f, omega_f, G_f, rho0_f, inv_rho0_f, rho_ref_f;
+  // base of every population block of fout (push destinations)
+  void *out_pop[19];
   // injection (virtual blowing agent); nsites == 0 disables it
   int32_t nsites;
   const int32_t *site_x, *site_y, *site_z;  // view coordinates per site
@@ -31,6 +35,7 @@ struct StepArgs {
   const int32_t *bucket_off;
   const int32_t *bucket_site;
   int *err;  // device status word (ERR_* bits)
+  int debug_flags;  // LBM_DEBUG_* bits of the configuration
 };
 
 // TMA descriptors of one population lattice for the fused kernel: the

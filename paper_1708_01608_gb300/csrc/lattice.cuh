@@ -38,6 +38,10 @@ struct Lattice<D2Q9> {
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
   }
+  // pairs of opposite velocities: (1,3) (2,4) (5,7) (6,8)
+  static constexpr int NP = 4;
+  __host__ __device__ static constexpr int rep(int k) { return k < 2 ? 1 + k : 3 + k; }
+  __host__ __device__ static constexpr int opp(int i) { return i + 2; }
 };
 
 template <>
@@ -65,10 +69,19 @@ struct Lattice<D3Q19> {
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
   }
+  // pairs of opposite velocities: (1,2) (3,4) ... (17,18)
+  static constexpr int NP = 9;
+  __host__ __device__ static constexpr int rep(int k) { return 2 * k + 1; }
+  __host__ __device__ static constexpr int opp(int i) { return i + 1; }
 };
 
 // ---- storage codecs -------------------------------------------------------
-// T = stored type, C = arithmetic type.  16-bit forms hold f - w_i*rho_ref.
+// T = stored type, C = arithmetic type.  FP64 stores f_i itself.  The FP32
+// and 16-bit forms store the offset g_i = f_i - w_i*rho_ref and the FP32
+// kernels do their arithmetic on offsets: round-off then scales with |g|,
+// which is small wherever rho is near rho_ref (the bulk liquid), instead of
+// with |f| (the shifted-distribution technique of Skordos, Phys. Rev. E 48,
+// 4823 (1993)).  load/store convert between T and C without the offset.
 template <int ST>
 struct Storage;
 
@@ -76,30 +89,45 @@ template <>
 struct Storage<ST_F64> {
   using T = double;
   using C = double;
-  __device__ static C load(T v, C) { return v; }
-  __device__ static T store(C v, C) { return v; }
+  static constexpr bool OFFSET = false;
+  __device__ static C load(T v) { return v; }
+  __device__ static T store(C v) { return v; }
 };
 template <>
 struct Storage<ST_F32> {
   using T = float;
   using C = float;
-  __device__ static C load(T v, C) { return v; }
-  __device__ static T store(C v, C) { return v; }
+  static constexpr bool OFFSET = true;
+  __device__ static C load(T v) { return v; }
+  __device__ static T store(C v) { return v; }
 };
 template <>
 struct Storage<ST_F16> {
   using T = __half;
   using C = float;
-  __device__ static C load(T v, C wref) { return wref + __half2float(v); }
-  __device__ static T store(C v, C wref) { return __float2half_rn(v - wref); }
+  static constexpr bool OFFSET = true;
+  __device__ static C load(T v) { return __half2float(v); }
+  __device__ static T store(C v) { return __float2half_rn(v); }
 };
 template <>
 struct Storage<ST_BF16> {
   using T = __nv_bfloat16;
   using C = float;
-  __device__ static C load(T v, C wref) { return wref + __bfloat162float(v); }
-  __device__ static T store(C v, C wref) { return __float2bfloat16_rn(v - wref); }
+  static constexpr bool OFFSET = true;
+  __device__ static C load(T v) { return __bfloat162float(v); }
+  __device__ static T store(C v) { return __float2bfloat16_rn(v); }
 };
+
+// f_i from a stored value and back, in double (diagnostics, state I/O)
+template <int ST>
+__device__ __forceinline__ double decode_f(typename Storage<ST>::T v, double wref) {
+  return Storage<ST>::OFFSET ? wref + (double)Storage<ST>::load(v) : (double)Storage<ST>::load(v);
+}
+template <int ST>
+__device__ __forceinline__ typename Storage<ST>::T encode_f(double f, double wref) {
+  using C = typename Storage<ST>::C;
+  return Storage<ST>::store(Storage<ST>::OFFSET ? (C)(f - wref) : (C)f);
+}
 
 inline size_t storage_bytes(int st) { return st == ST_F64 ? 8 : (st == ST_F32 ? 4 : 2); }
 

@@ -106,11 +106,12 @@ __global__ void __launch_bounds__(BX *BY)
   const int64_t popstride = plane * a.NZ;
   T *fout = static_cast<T *>(a.fout);
 
-  const C G = (C)a.G, tau = (C)a.tau, omega = (C)(1.0 / a.tau), rho0 = (C)a.rho0,
-          inv_rho0 = (C)(1.0 / a.rho0);
-  C wref[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) wref[i] = (C)(L::w(i) * a.rho_ref);
+  // constants in the arithmetic type (FP32 kernels execute no FP64 at all)
+  const C G = F64 ? (C)a.G : (C)a.G_f, tau = F64 ? (C)a.tau : (C)a.tau_f,
+          omega = F64 ? (C)(1.0 / a.tau) : (C)a.omega_f, rho0 = F64 ? (C)a.rho0 : (C)a.rho0_f,
+          inv_rho0 = F64 ? (C)(1.0 / a.rho0) : (C)a.inv_rho0_f;
+  // offset storage: the staged values are g_i = f_i - w_i rho_ref
+  const C rho_ref = S::OFFSET ? (C)a.rho_ref_f : (C)0;
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(BX *BY)
   __syncthreads();
 
   auto issue = [&](int k) {
+    if ((a.debug_flags & 1) && k == 1) return;  // test hook: let the wait expire
     const int P = zs - 1 + k, s = k % NS;
     const int zp = P < 0 ? P + NZ : (P >= NZ ? P - NZ : P);
     uint8_t *st = smem + s * K::STAGE_BYTES;
@@ -157,6 +159,61 @@ __global__ void __launch_bounds__(BX *BY)
   const int xm = x == 0 ? NX - 1 : x - 1, xp = x + 1 >= NX ? 0 : x + 1;
   const int ym = y == 0 ? NY - 1 : y - 1, yp = y + 1 >= NY ? 0 : y + 1;
 
+  // The halo cell this thread computes psi for (at most one: nhalo <= NT),
+  // as a byte offset of its population 0 inside a stage, the element
+  // distance between populations and its slot in a psi plane.
+  const int nhalo = HY ? 2 * (BXe + 2) + 2 * BYe : 2;
+  int h_off = 0, h_pstride = 0, h_slot = 0;
+  if (tid < nhalo) {
+    int dx, dy;
+    const int h = tid;
+    if (HY) {
+      if (h < BXe + 2) {
+        dx = h - 1;
+        dy = -1;
+      } else if (h < 2 * (BXe + 2)) {
+        dx = h - (BXe + 2) - 1;
+        dy = BYe;
+      } else {
+        const int h2 = h - 2 * (BXe + 2);
+        dx = h2 < BYe ? -1 : BXe;
+        dy = h2 < BYe ? h2 : h2 - BYe;
+      }
+    } else {
+      dx = h == 0 ? -1 : BXe;
+      dy = 0;
+    }
+    const int cxr = dx < 0 ? 0 : (dx >= BXe ? 2 : 1);
+    const int cyr = dy < 0 ? 0 : (dy >= BYe ? 2 : 1);
+    int off, e;
+    if (cyr == 1) {
+      if (cxr == 1) {
+        off = 0;
+        e = dy * BX + dx;
+        h_pstride = BY * BX;
+      } else {
+        off = cxr == 0 ? K::OFF_L : K::OFF_R;
+        e = dy * HX + (cxr == 0 ? HX - 1 : 0);
+        h_pstride = BY * HX;
+      }
+    } else if (cxr == 1) {
+      off = cyr == 0 ? K::OFF_T : K::OFF_B;
+      e = dx;
+      h_pstride = BX;
+    } else {
+      off = cyr == 0 ? (cxr == 0 ? K::OFF_TL : K::OFF_TR) : (cxr == 0 ? K::OFF_BL : K::OFF_BR);
+      e = cxr == 0 ? HX - 1 : 0;
+      h_pstride = HX;
+    }
+    h_off = off + e * (int)sizeof(T);
+    h_slot = (dy + HY) * PW + dx + 1;
+  }
+  static_assert(!HY || 2 * (BX + 2) + 2 * BY <= NT, "one halo cell per thread at most");
+
+  // 32-bit offsets of the push destinations inside a population block
+  const int32_t ox[3] = {xm, x, xp};
+  const int32_t oy[3] = {(int32_t)(ym * a.px), (int32_t)(y * a.px), (int32_t)(yp * a.px)};
+
   C cur[Q], nxt[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) cur[i] = nxt[i] = 0;
@@ -174,60 +231,18 @@ __global__ void __launch_bounds__(BX *BY)
       C rho = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const C v = S::load(mainb[(i * BY + ty) * BX + tx], wref[i]);
+        const C v = S::load(mainb[(i * BY + ty) * BX + tx]);
         nxt[i] = v;
         rho += v;
       }
-      rk[(ty + HY) * PW + tx + 1] = psi_of(rho, rho0, inv_rho0);
+      rk[(ty + HY) * PW + tx + 1] = psi_of(rho_ref + rho, rho0, inv_rho0);
     }
-    const int nhalo = HY ? 2 * (BXe + 2) + 2 * BYe : 2;
-    for (int h = tid; h < nhalo; h += NT) {
-      int dx, dy;
-      if (HY) {
-        if (h < BXe + 2) {
-          dx = h - 1;
-          dy = -1;
-        } else if (h < 2 * (BXe + 2)) {
-          dx = h - (BXe + 2) - 1;
-          dy = BYe;
-        } else {
-          const int h2 = h - 2 * (BXe + 2);
-          dx = h2 < BYe ? -1 : BXe;
-          dy = h2 < BYe ? h2 : h2 - BYe;
-        }
-      } else {
-        dx = h == 0 ? -1 : BXe;
-        dy = 0;
-      }
-      // staged box holding (dx, dy): element of population 0 and the
-      // distance between populations
-      const int cxr = dx < 0 ? 0 : (dx >= BXe ? 2 : 1);
-      const int cyr = dy < 0 ? 0 : (dy >= BYe ? 2 : 1);
-      int off, e, pstride;
-      if (cyr == 1) {
-        if (cxr == 1) {
-          off = 0;
-          e = dy * BX + dx;
-          pstride = BY * BX;
-        } else {
-          off = cxr == 0 ? K::OFF_L : K::OFF_R;
-          e = dy * HX + (cxr == 0 ? HX - 1 : 0);
-          pstride = BY * HX;
-        }
-      } else if (cxr == 1) {
-        off = cyr == 0 ? K::OFF_T : K::OFF_B;
-        e = dx;
-        pstride = BX;
-      } else {
-        off = cyr == 0 ? (cxr == 0 ? K::OFF_TL : K::OFF_TR) : (cxr == 0 ? K::OFF_BL : K::OFF_BR);
-        e = cxr == 0 ? HX - 1 : 0;
-        pstride = HX;
-      }
-      const T *b = reinterpret_cast<const T *>(st + off) + e;
+    if (tid < nhalo) {
+      const T *b = reinterpret_cast<const T *>(st + h_off);
       C rho = 0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) rho += S::load(b[i * pstride], wref[i]);
-      rk[(dy + HY) * PW + dx + 1] = psi_of(rho, rho0, inv_rho0);
+      for (int i = 0; i < Q; ++i) rho += S::load(b[i * h_pstride]);
+      rk[h_slot] = psi_of(rho_ref + rho, rho0, inv_rho0);
     }
 
     if (__syncthreads_or(!ok)) {
@@ -245,6 +260,7 @@ __global__ void __launch_bounds__(BX *BY)
     if (k >= 2) {
       const int Pc = P - 1;
       double dm = 0.0;  // blowing-agent mass deposited in this cell this step
+      bool site = false;
       if (a.nsites > 0) {
         while (sp < send && a.site_z[a.bucket_site[sp]] < Pc) ++sp;
         for (int q = sp; q < send; ++q) {
@@ -256,6 +272,7 @@ __global__ void __launch_bounds__(BX *BY)
               const double d = fmin(a.rate[sidx], b);
               a.budget[sidx] = b - d;
               dm += d;
+              site = true;
             }
           }
         }
@@ -265,59 +282,93 @@ __global__ void __launch_bounds__(BX *BY)
         const C *p0 = ring + ((k - 1) & 3) * PW * PH;
         const C *pp = ring + (k & 3) * PW * PH;
         const int c0 = (ty + HY) * PW + tx + 1;
-        C rho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          rho += cur[i];
-          jx += (C)L::cx(i) * cur[i];
-          jy += (C)L::cy(i) * cur[i];
-          jz += (C)L::cz(i) * cur[i];
-        }
-        C sx = 0, sy = 0, sz = 0;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const C *pl = L::cz(i) < 0 ? pm : (L::cz(i) > 0 ? pp : p0);
-          const C wp = (C)L::w(i) * pl[c0 + L::cy(i) * PW + L::cx(i)];
-          sx += (C)L::cx(i) * wp;
-          sy += (C)L::cy(i) * wp;
-          sz += (C)L::cz(i) * wp;
-        }
-        const C gp = -G * p0[c0];
-        const C Fx = gp * sx, Fy = gp * sy, Fz = gp * sz;
-        C ux, uy, uz;
-        if (F64) {  // FP64 keeps the oracle's operation order
-          ux = (jx + tau * Fx) / rho;
-          uy = (jy + tau * Fy) / rho;
-          uz = (jz + tau * Fz) / rho;
-        } else {
-          const C ir = (C)1 / rho;
-          ux = (jx + tau * Fx) * ir;
-          uy = (jy + tau * Fy) * ir;
-          uz = (jz + tau * Fz) * ir;
-        }
-        const C uu = (C)1.5 * (ux * ux + uy * uy + uz * uz);
         const int zm = Pc == 0 ? NZ - 1 : Pc - 1, zp = Pc + 1 >= NZ ? 0 : Pc + 1;
-        // FP32: the rest population takes rho minus the moving ones, so the
-        // collision conserves mass to rounding (FP32 weights do not sum to 1)
-        constexpr int i0 = F64 ? 0 : 1;
-        C moved = 0;
+        const int32_t oz[3] = {(int32_t)(zm * plane), (int32_t)(Pc * plane), (int32_t)(zp * plane)};
+        auto dst = [&](int i) -> T * {
+          return static_cast<T *>(a.out_pop[i]) + (oz[L::cz(i) + 1] + oy[L::cy(i) + 1] + ox[L::cx(i) + 1]);
+        };
+        auto psi_at = [&](int i) -> C {
+          const C *pl = L::cz(i) < 0 ? pm : (L::cz(i) > 0 ? pp : p0);
+          return pl[c0 + L::cy(i) * PW + L::cx(i)];
+        };
+        if constexpr (F64) {
+          // FP64: the oracle's operation order, velocity by velocity
+          C rho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-        for (int i = i0; i < Q; ++i) {
-          const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
-          const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
-          C fs = F64 ? cur[i] - (cur[i] - feq) / tau : cur[i] - omega * (cur[i] - feq);
-          moved += fs;
-          if (dm != 0.0) fs += (C)(L::w(i) * dm);
-          const int X = L::cx(i) > 0 ? xp : (L::cx(i) < 0 ? xm : x);
-          const int Y = L::cy(i) > 0 ? yp : (L::cy(i) < 0 ? ym : y);
-          const int Z = L::cz(i) > 0 ? zp : (L::cz(i) < 0 ? zm : Pc);
-          fout[(int64_t)i * popstride + (int64_t)Z * plane + (int64_t)Y * a.px + X] =
-              S::store(fs, wref[i]);
-        }
-        if (!F64) {
-          C fs0 = rho - moved;
-          if (dm != 0.0) fs0 += (C)(L::w(0) * dm);
-          fout[(int64_t)Pc * plane + (int64_t)y * a.px + x] = S::store(fs0, wref[0]);
+          for (int i = 0; i < Q; ++i) {
+            rho += cur[i];
+            jx += (C)L::cx(i) * cur[i];
+            jy += (C)L::cy(i) * cur[i];
+            jz += (C)L::cz(i) * cur[i];
+          }
+          C sx = 0, sy = 0, sz = 0;
+#pragma unroll
+          for (int i = 1; i < Q; ++i) {
+            const C wp = (C)L::w(i) * psi_at(i);
+            sx += (C)L::cx(i) * wp;
+            sy += (C)L::cy(i) * wp;
+            sz += (C)L::cz(i) * wp;
+          }
+          const C gp = -G * p0[c0];
+          const C ux = (jx + tau * (gp * sx)) / rho, uy = (jy + tau * (gp * sy)) / rho,
+                  uz = (jz + tau * (gp * sz)) / rho;
+          const C uu = (C)1.5 * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
+            const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
+            C fs = cur[i] - (cur[i] - feq) / tau;
+            if (site) fs += L::w(i) * dm;
+            *dst(i) = S::store(fs);
+          }
+        } else {
+          // FP32 on offsets g_i = f_i - w_i rho_ref: with R = sum g (so that
+          // rho = rho_ref + R) the equilibrium offset is
+          //   w_i (R + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)),
+          // evaluated for opposite velocities in pairs.  The rest population
+          // takes R minus the moving ones, so mass is conserved to rounding.
+          C R = cur[0], jx = 0, jy = 0, jz = 0, sx = 0, sy = 0, sz = 0;
+#pragma unroll
+          for (int k2 = 0; k2 < L::NP; ++k2) {
+            const int i = L::rep(k2), o = L::opp(L::rep(k2));
+            R += cur[i] + cur[o];
+            const C d = cur[i] - cur[o];
+            jx += (C)L::cx(i) * d;
+            jy += (C)L::cy(i) * d;
+            jz += (C)L::cz(i) * d;
+            const C dp = (C)L::w(i) * (psi_at(i) - psi_at(o));
+            sx += (C)L::cx(i) * dp;
+            sy += (C)L::cy(i) * dp;
+            sz += (C)L::cz(i) * dp;
+          }
+          const C rho = rho_ref + R;
+          const C gp = -G * p0[c0];
+          const C ir = (C)1 / rho;
+          const C ux = (jx + tau * (gp * sx)) * ir, uy = (jy + tau * (gp * sy)) * ir,
+                  uz = (jz + tau * (gp * sz)) * ir;
+          const C m_uu = (C)-1.5 * (ux * ux + uy * uy + uz * uz);
+          const C dmc = site ? (C)dm : (C)0;
+          C moved = 0;
+#pragma unroll
+          for (int k2 = 0; k2 < L::NP; ++k2) {
+            const int i = L::rep(k2), o = L::opp(L::rep(k2));
+            const C w = (C)L::w(i);
+            const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
+            const C A = w * fmaf(rho, fmaf((C)4.5 * cu, cu, m_uu), R);
+            const C B = ((C)3 * w) * (rho * cu);
+            C gi = fmaf(omega, (A + B) - cur[i], cur[i]);
+            C go = fmaf(omega, (A - B) - cur[o], cur[o]);
+            moved += gi + go;
+            if (site) {
+              gi += w * dmc;
+              go += w * dmc;
+            }
+            *dst(i) = S::store(gi);
+            *dst(o) = S::store(go);
+          }
+          C g0 = R - moved;
+          if (site) g0 += (C)L::w(0) * dmc;
+          *dst(0) = S::store(g0);
         }
       }
     }
@@ -348,7 +399,9 @@ cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const FusedMap
   X(2, 32, 4, 4)             \
   X(3, 64, 4, 3)             \
   X(4, 64, 8, 2)             \
-  X(5, 128, 4, 2)
+  X(5, 128, 4, 2)            \
+  X(6, 32, 8, 2)             \
+  X(7, 64, 4, 2)
 #define SCLBM_D2Q9_TILES(X) \
   X(1, 256, 1, 4)           \
   X(2, 128, 1, 4)           \

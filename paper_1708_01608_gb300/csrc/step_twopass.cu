@@ -23,6 +23,19 @@ __device__ __forceinline__ Cell cell_of(int64_t k, int64_t NX, int64_t NY) {
 }
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// f_i in the arithmetic type from a stored value and back (offset storage
+// adds / removes w_i rho_ref)
+template <int ST>
+__device__ __forceinline__ typename Storage<ST>::C dec(typename Storage<ST>::T v,
+                                                       typename Storage<ST>::C wref) {
+  return Storage<ST>::OFFSET ? wref + Storage<ST>::load(v) : Storage<ST>::load(v);
+}
+template <int ST>
+__device__ __forceinline__ typename Storage<ST>::T enc(typename Storage<ST>::C f,
+                                                       typename Storage<ST>::C wref) {
+  return Storage<ST>::store(Storage<ST>::OFFSET ? f - wref : f);
+}
+
 template <int LAT, int ST>
 __global__ void tp_psi_kernel(const StepArgs a, typename Storage<ST>::C *psi) {
   using L = Lattice<LAT>;
@@ -39,7 +52,7 @@ __global__ void tp_psi_kernel(const StepArgs a, typename Storage<ST>::C *psi) {
     const int64_t o = (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
     C rho = 0;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) rho += S::load(f[i * pop + o], (C)(L::w(i) * a.rho_ref));
+    for (int i = 0; i < L::Q; ++i) rho += dec<ST>(f[i * pop + o], (C)(L::w(i) * a.rho_ref));
     psi[k] = psi_of(rho, rho0, inv_rho0);
   }
 }
@@ -64,7 +77,7 @@ __global__ void tp_collide_kernel(const StepArgs a, const typename Storage<ST>::
     const int64_t own = (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      fi[i] = S::load(f[i * pop + own], (C)(L::w(i) * a.rho_ref));
+      fi[i] = dec<ST>(f[i * pop + own], (C)(L::w(i) * a.rho_ref));
       rho += fi[i];
       jx += (C)L::cx(i) * fi[i];
       jy += (C)L::cy(i) * fi[i];
@@ -104,9 +117,9 @@ __global__ void tp_collide_kernel(const StepArgs a, const typename Storage<ST>::
       const int X = wrapi(c.x + L::cx(i), NX), Y = wrapi(c.y + L::cy(i), NY),
                 Z = wrapi(c.z + L::cz(i), NZ);
       g[i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X] =
-          S::store(fs, (C)(L::w(i) * a.rho_ref));
+          enc<ST>(fs, (C)(L::w(i) * a.rho_ref));
     }
-    if (sizeof(C) == 4) g[own] = S::store(rho - moved, (C)(L::w(0) * a.rho_ref));
+    if (sizeof(C) == 4) g[own] = enc<ST>(rho - moved, (C)(L::w(0) * a.rho_ref));
   }
 }
 
@@ -141,7 +154,7 @@ __global__ void tp_inject_kernel(const StepArgs a) {
               Z = wrapi(a.site_z[s0] + L::cz(i), (int)a.NZ);
     T *o = g + i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X;
     const C wref = (C)(L::w(i) * a.rho_ref);
-    *o = S::store(S::load(*o, wref) + (C)(L::w(i) * dm), wref);
+    *o = enc<ST>(dec<ST>(*o, wref) + (C)(L::w(i) * dm), wref);
   }
 }
 

@@ -27,6 +27,7 @@ D2Q9, D3Q19 = 0, 1
 F64, F32, F16_OFFSET, BF16_OFFSET = 0, 1, 2, 3
 RHO, PSI, P, U, F, LAPP = range(6)
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_TWO_PASS = 0, 1, 2
+DEBUG_WITHHOLD_TMA = 1
 
 STORAGE = {"f64": F64, "f32": F32, "f16": F16_OFFSET, "bf16": BF16_OFFSET}
 LATTICE = {"D2Q9": D2Q9, "D3Q19": D3Q19}
@@ -47,6 +48,7 @@ class Config(C.Structure):
         ("kernel", C.c_int32), ("tile", C.c_int32),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+        ("debug_flags", C.c_int32),
     ]
 
 
@@ -78,6 +80,8 @@ def _load():
         "lbm_read_budgets": (i32, [P_, P_, i32]),
         "lbm_step": (i32, [P_, i64]),
         "lbm_step_count": (i64, [P_]),
+        "lbm_autotune": (i32, [P_, i32, C.POINTER(i32), C.POINTER(d)]),
+        "lbm_plan_info": (i32, [P_, P_]),
         "lbm_sync": (i32, [P_]),
         "lbm_pressure_laplacian": (i32, [P_, P_, i64, P_]),
         "lbm_label_gas": (i32, [P_, P_, C.POINTER(i64)]),
@@ -100,6 +104,7 @@ _lib = _load()
 # every symbol the header declares (checked by the CPU tests)
 EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites",
            "lbm_seed_bubbles", "lbm_inject", "lbm_read_budgets", "lbm_step", "lbm_step_count",
+           "lbm_autotune", "lbm_plan_info",
            "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_site_labels",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_last_error", "lbm_version")
 
@@ -160,7 +165,7 @@ class Lattice:
 
     def __init__(self, lattice="D3Q19", nx=64, ny=64, nz=1, tau=1.0, G=-5.0, rho0=1.0,
                  storage="f32", rho_ref=1.0, gas_threshold=1.0, kernel="auto", tile=0,
-                 stream: Optional[int] = None, torch_memory: bool = True):
+                 stream: Optional[int] = None, torch_memory: bool = True, debug_flags: int = 0):
         cfg = Config()
         _lib.lbm_config_default(C.byref(cfg))
         cfg.lattice = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
@@ -170,6 +175,7 @@ class Lattice:
         cfg.rho_ref, cfg.gas_threshold = float(rho_ref), float(gas_threshold)
         cfg.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         cfg.tile = int(tile)
+        cfg.debug_flags = int(debug_flags)
         self._mem = None
         if torch_memory:
             try:
@@ -245,6 +251,20 @@ class Lattice:
 
     def sync(self):
         _check(_lib.lbm_sync(self._h))
+
+    def autotune(self, steps=10):
+        """Time every fitting fused tile on the current state (restored
+        afterwards) and keep the fastest: (tile id, ms per step)."""
+        t = C.c_int32(0)
+        ms = C.c_double(0)
+        _check(_lib.lbm_autotune(self._h, int(steps), C.byref(t), C.byref(ms)))
+        return int(t.value), float(ms.value)
+
+    def plan(self):
+        """(kernel, tile id, tile x, tile y, z chunks, CTAs per step)."""
+        out = np.zeros(6, dtype=np.int32)
+        _check(_lib.lbm_plan_info(self._h, _ptr(out)))
+        return tuple(int(v) for v in out)
 
     @property
     def steps(self):

@@ -4,8 +4,9 @@ The paper reports no grid sizes or run lengths; these recipes stand in for
 its two-bubble runs (Sec. 4, Fig. 2), its bubble-size sweep (Fig. 3) and its
 foam runs.  Each recipe lists the lattice, the physical parameters, how the
 bubbles are placed (explicit centres, or random nucleation sites drawn with
-the library's / the oracle's SplitMix64 sampler from the given seed) and the
-blowing-agent rates.  Both the CUDA path and the CPU oracle read these
+the library's / the oracle's SplitMix64 sampler from the given seed), the
+blowing-agent rates and the reference density of the offset storage (the
+liquid density, where most cells sit).  Both the CUDA path and the CPU oracle read these
 dictionaries; neither imports the other.
 """
 from __future__ import annotations
@@ -22,20 +23,20 @@ FOAM_128 = dict(
     name="d3q19_foam_128", lattice="D3Q19", nx=128, ny=128, nz=128, tau=1.0, G=-5.0,
     rho0=1.0, storage="f32", rho_l=2.0, rho_g=0.15, width=2.0, noise=1e-3, seed=1,
     sites=dict(n=64, r_min=3.0, r_max=3.0, min_spacing=12.0, min_gap=0.0),
-    rate=1e-4, budget=50.0, steps=20000, diag_every=100, threshold=1.0)
+    rate=1e-4, budget=50.0, steps=20000, diag_every=100, threshold=1.0, rho_ref=2.0)
 
 # 1000 bubbles r ~ U(4, 12) on 512^3, tau 0.8 (precision study)
 FOAM_512 = dict(
     name="d3q19_foam_512", lattice="D3Q19", nx=512, ny=512, nz=512, tau=0.8, G=-5.0,
     rho0=1.0, storage="f32", rho_l=2.0, rho_g=0.15, width=2.0, noise=1e-3, seed=2,
     sites=dict(n=1000, r_min=4.0, r_max=12.0, min_spacing=0.0, min_gap=4.0),
-    rate=0.0, budget=0.0, steps=2000, rho_ref=1.0, threshold=1.0)
+    rate=0.0, budget=0.0, steps=2000, rho_ref=2.0, threshold=1.0)
 
 # full foam, 4096 sites, FP16-offset storage (768^3)
 FOAM_768 = dict(
     name="d3q19_foam_768", lattice="D3Q19", nx=768, ny=768, nz=768, tau=0.9, G=-5.0,
     rho0=1.0, storage="f16", rho_l=2.0, rho_g=0.15, width=2.0, noise=1e-3, seed=4,
     sites=dict(n=4096, r_min=3.0, r_max=3.0, min_spacing=12.0, min_gap=0.0),
-    rate=5e-5, budget=(20.0, 80.0), steps=50000, diag_every=100, rho_ref=1.0, threshold=1.0)
+    rate=5e-5, budget=(20.0, 80.0), steps=50000, diag_every=100, rho_ref=2.0, threshold=1.0)
 
 WORKLOADS = {w["name"]: w for w in (TWO_DISKS_128, FOAM_128, FOAM_512, FOAM_768)}
