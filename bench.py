@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the fused kernel from an ncu capture of this
 # workload (dram__bytes_read.sum + dram__bytes_write.sum); None = not captured
 # for the current kernel.
-NCU_TRAFFIC_PER_LAUNCH = None
+NCU_TRAFFIC_PER_LAUNCH = {4: 276.7e6}  # tile id -> bytes (profiles/fused_step_d3q19_f32_128.md)
 
 
 def peak_hbm():
@@ -241,9 +241,8 @@ def run_ours(args, world, rank, local):
         L.step(INNER)
         if e_end is not None:
             e_end.record(stream)
-        L.totals()
-        L.label_gas(want_labels=False)
-        L.site_labels()
+        L.diagnose(want_labels=False)   # FP64 totals + gas labels in one pass
+        L.site_labels()                 # per-site labels, merge events
 
     for _ in range(args.warmup):
         bench_step()
@@ -282,9 +281,9 @@ def run_ours(args, world, rank, local):
     for _ in range(args.steps):
         L.inject(rate_h, budget_pin)                      # H2D: rates and budgets
         L.step(INNER)
-        lbm._check(lbm.lib().lbm_label_gas(L.handle, labels.ctypes.data_as(C.c_void_p),
-                                           C.byref(nc)))  # D2H: labels
-        tot = L.totals()                                  # D2H: totals
+        lbm._check(lbm.lib().lbm_diagnose(L.handle, tot.ctypes.data_as(C.c_void_p),
+                                          labels.ctypes.data_as(C.c_void_p),
+                                          C.byref(nc)))   # D2H: totals, labels
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
     h2d = rate_h.nbytes + budget_pin.nbytes
@@ -295,7 +294,7 @@ def run_ours(args, world, rank, local):
     e2e_val = units / e2e_s / 1e6
     peak, src = peak_hbm()
     achieved = B_ALG * CELLS / (step_kernel_ms / 1e3) / 1e9
-    launches_per_step = INNER + 2 + 1 + 3 + 1   # steps, totals, moments, labelling, site gather
+    launches_per_step = INNER + 2 + 2 + 1   # steps, scan + final, union + compress, site gather
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -318,13 +317,33 @@ def run_ours(args, world, rank, local):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src,
-                         "traffic": NCU_TRAFFIC_PER_LAUNCH,
+                         "traffic": NCU_TRAFFIC_PER_LAUNCH.get(plan[1]),
                          "kernel": "fused_step_kernel", "bytes_per_update": B_ALG,
                          "kernel_ms": step_kernel_ms},
             "cpu_baseline": cpu,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
+    L.close()
+
+
+def run_profile_case(args):
+    import torch
+    from paper_1708_01608_gb300 import build_lib
+    build_lib.build()
+    from paper_1708_01608_gb300 import lbm
+    torch.cuda.set_device(0)
+    s = W["sites"]
+    bub = lbm.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
+                           s["min_spacing"], s["min_gap"], W["seed"])
+    L = lbm.Lattice("D3Q19", W["nx"], W["ny"], W["nz"], tau=W["tau"], G=W["G"],
+                    rho0=W["rho0"], storage=W["storage"], rho_ref=W["rho_ref"],
+                    kernel="fused" if args.tile else args.kernel, tile=args.tile)
+    L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
+    L.inject(np.full(len(bub), W["rate"]), np.full(len(bub), W["budget"]))
+    L.step(args.profile_steps)
+    L.sync()
+    print(json.dumps({"profile_case": W["name"], "steps": args.profile_steps, "plan": L.plan()}))
     L.close()
 
 
@@ -337,7 +356,14 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "two_pass"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="no timing: build the workload lattice, run this many steps, exit "
+                         "(a short fixed case for ncu captures)")
+    ap.add_argument("--tile", type=int, default=0, help="fused tile id for --profile-steps")
     args = ap.parse_args()
+    if args.profile_steps > 0:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup(args.gpus)

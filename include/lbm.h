@@ -211,15 +211,26 @@ lbm_status lbm_pressure_laplacian(lbm_ctx *ctx, double *out, int64_t count,
  * number of components (may be NULL).  Synchronous. */
 lbm_status lbm_label_gas(lbm_ctx *ctx, int32_t *labels, int64_t *ncomp);
 
-/* Label of each injection site's cell after the last lbm_label_gas (-1 when
+/* The record of one diagnostic interval in a single pass over the
+ * populations: FP64 totals as lbm_totals (totals may be NULL), gas labels as
+ * lbm_label_gas (labels: host array of N int32 or NULL; *ncomp may be NULL),
+ * per-site labels and merge events updated as by lbm_label_gas.
+ * Synchronous. */
+lbm_status lbm_diagnose(lbm_ctx *ctx, double totals[4], int32_t *labels, int64_t *ncomp);
+
+/* Label of each injection site's cell after the last labelling (-1 when
  * the cell is liquid), and the number of merge events so far: a merge event
  * is a pair of sites whose labels differed at the previous labelling and
  * are equal now (both gas).  site_labels may be NULL. */
 lbm_status lbm_site_labels(lbm_ctx *ctx, int32_t *site_labels, int32_t n,
                            int64_t *merge_events);
 
-/* FP64 totals: out[0] = sum rho, out[1..3] = sum j (all cells, velocity
- * order within a cell, fixed-order block reduction).  Synchronous. */
+/* FP64 totals: out[0] = sum rho, out[1..3] = sum j over all cells, with a
+ * fixed-order block reduction (repeated calls give identical bits).  FP64
+ * storage sums every population in FP64; the FP32-arithmetic storages sum
+ * the offsets f_i - w_i rho_ref of a cell in FP32 and the cells in
+ * compensated FP32 / FP64 (mass = N rho_ref + sum of offsets).
+ * Synchronous. */
 lbm_status lbm_totals(lbm_ctx *ctx, double out[4]);
 
 /* Copy a field (doubles, see lbm_field) to host; bytes must be exactly the

@@ -183,7 +183,8 @@ lbm_status ensure_diag(lbm_ctx *c) {
   CKS(dalloc(c, c->d_rho, nd));
   CKS(dalloc(c, c->d_p, nd));
   CKS(dalloc(c, c->d_tmp, nd));
-  CKS(dalloc(c, c->d_part, 4 * sizeof(double) * diag_totals_blocks()));
+  CKS(dalloc(c, c->d_part,
+             4 * sizeof(double) * std::max(diag_totals_blocks(), diag_scan_blocks())));
   CKS(dalloc(c, c->d_tot, 4 * sizeof(double)));
   CKS(dalloc(c, c->d_ncomp, sizeof(unsigned long long)));
   return LBM_OK;
@@ -667,50 +668,89 @@ lbm_status lbm_pressure_laplacian(lbm_ctx *c, double *out, int64_t count, const 
   return sync_and_check(c);
 }
 
-lbm_status lbm_label_gas(lbm_ctx *c, int32_t *labels, int64_t *ncomp) {
-  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
-  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
-  CKS(set_device(c));
-  CKS(check_sticky(c));
-  CKS(compute_pressure(c));
+// Enqueue the labelling of gas cells (and, for FP32-arithmetic storages, the
+// totals in the same pass when want_totals), then the per-site label gather.
+static lbm_status enqueue_labels(lbm_ctx *c, bool want_totals) {
+  CKS(ensure_diag(c));
   CKS(dalloc(c, c->d_labels, sizeof(int32_t) * c->N));
-  CK(diag_label(c->v, static_cast<const double *>(c->d_rho.p), c->cfg.gas_threshold,
-                static_cast<int32_t *>(c->d_labels.p),
-                static_cast<unsigned long long *>(c->d_ncomp.p), c->s));
+  int32_t *lab = static_cast<int32_t *>(c->d_labels.p);
+  if (c->st != LBM_F64) {
+    CK(diag_scan(c->v, lattice_ptr(c, c->cur), c->cfg.gas_threshold, lab,
+                 want_totals ? static_cast<double *>(c->d_part.p) : nullptr,
+                 want_totals ? static_cast<double *>(c->d_tot.p) : nullptr,
+                 static_cast<int *>(c->d_err.p), c->s));
+    CK(diag_label_links(c->v, lab, static_cast<unsigned long long *>(c->d_ncomp.p), c->s));
+  } else {
+    CKS(compute_pressure(c));
+    CK(diag_label(c->v, static_cast<const double *>(c->d_rho.p), c->cfg.gas_threshold, lab,
+                  static_cast<unsigned long long *>(c->d_ncomp.p), c->s));
+    if (want_totals)
+      CK(diag_totals(c->v, lattice_ptr(c, c->cur), static_cast<double *>(c->d_part.p),
+                     static_cast<double *>(c->d_tot.p), c->s));
+  }
   const int32_t ns = (int32_t)c->sx.size();
   if (ns > 0) {
     CKS(dalloc(c, c->d_site_lab, sizeof(int32_t) * ns));
-    CK(diag_gather_labels(static_cast<const int32_t *>(c->d_labels.p),
-                          static_cast<const int32_t *>(c->d_cells.p), ns,
+    CK(diag_gather_labels(lab, static_cast<const int32_t *>(c->d_cells.p), ns,
                           static_cast<int32_t *>(c->d_site_lab.p), c->s));
     c->site_labels.resize(ns);
     CK(cudaMemcpyAsync(c->site_labels.data(), c->d_site_lab.p, sizeof(int32_t) * ns,
                        cudaMemcpyDeviceToHost, c->s));
   }
+  return LBM_OK;
+}
+
+// merge events: pairs of sites with different labels before, equal now
+static void count_merges(lbm_ctx *c) {
+  const int32_t ns = (int32_t)c->sx.size();
+  if (ns == 0) return;
+  if (c->have_prev) {
+    std::map<int32_t, std::map<int32_t, int64_t>> groups;  // now -> prev -> count
+    for (int32_t k = 0; k < ns; ++k)
+      if (c->site_labels[k] >= 0) groups[c->site_labels[k]][c->prev_site_labels[k]]++;
+    for (auto &g : groups) {
+      int64_t tot = 0, same = 0;
+      for (auto &p : g.second) {
+        tot += p.second;
+        same += p.second * (p.second - 1) / 2;
+      }
+      c->merge_events += tot * (tot - 1) / 2 - same;
+    }
+  }
+  c->prev_site_labels = c->site_labels;
+  c->have_prev = true;
+}
+
+lbm_status lbm_label_gas(lbm_ctx *c, int32_t *labels, int64_t *ncomp) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(enqueue_labels(c, false));
   unsigned long long nc = 0;
   CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
   if (labels)
     CK(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost, c->s));
   CKS(sync_and_check(c));
   if (ncomp) *ncomp = (int64_t)nc;
-  // merge events: pairs of sites with different labels before, equal now
-  if (ns > 0) {
-    if (c->have_prev) {
-      std::map<int32_t, std::map<int32_t, int64_t>> groups;  // now -> prev -> count
-      for (int32_t k = 0; k < ns; ++k)
-        if (c->site_labels[k] >= 0) groups[c->site_labels[k]][c->prev_site_labels[k]]++;
-      for (auto &g : groups) {
-        int64_t tot = 0, same = 0;
-        for (auto &p : g.second) {
-          tot += p.second;
-          same += p.second * (p.second - 1) / 2;
-        }
-        c->merge_events += tot * (tot - 1) / 2 - same;
-      }
-    }
-    c->prev_site_labels = c->site_labels;
-    c->have_prev = true;
-  }
+  count_merges(c);
+  return LBM_OK;
+}
+
+lbm_status lbm_diagnose(lbm_ctx *c, double totals[4], int32_t *labels, int64_t *ncomp) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(enqueue_labels(c, totals != nullptr));
+  unsigned long long nc = 0;
+  CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
+  if (totals) CK(cudaMemcpyAsync(totals, c->d_tot.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  if (labels)
+    CK(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost, c->s));
+  CKS(sync_and_check(c));
+  if (ncomp) *ncomp = (int64_t)nc;
+  count_merges(c);
   return LBM_OK;
 }
 
@@ -730,8 +770,13 @@ lbm_status lbm_totals(lbm_ctx *c, double out[4]) {
   CKS(set_device(c));
   CKS(check_sticky(c));
   CKS(ensure_diag(c));
-  CK(diag_totals(c->v, lattice_ptr(c, c->cur), static_cast<double *>(c->d_part.p),
-                 static_cast<double *>(c->d_tot.p), c->s));
+  if (c->st != LBM_F64)
+    CK(diag_scan(c->v, lattice_ptr(c, c->cur), c->cfg.gas_threshold, nullptr,
+                 static_cast<double *>(c->d_part.p), static_cast<double *>(c->d_tot.p),
+                 static_cast<int *>(c->d_err.p), c->s));
+  else
+    CK(diag_totals(c->v, lattice_ptr(c, c->cur), static_cast<double *>(c->d_part.p),
+                   static_cast<double *>(c->d_tot.p), c->s));
   CK(cudaMemcpyAsync(out, c->d_tot.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
   return sync_and_check(c);
 }

@@ -69,19 +69,44 @@ __device__ __forceinline__ double min_image(double d, double n) {
   return d;
 }
 
+// Initial density.  The nearest bubble (smallest distance minus radius) is
+// found with FP32 distances, then every bubble within 1e-3 of that FP32
+// minimum is re-evaluated in FP64 with the exact formula, so the result
+// equals the all-FP64 minimum (FP32 distance errors are < 1e-4 here).
+__device__ __forceinline__ float min_image_f(float d, float n) {
+  d = fmodf(d, n);
+  if (d < 0) d += n;
+  if (d > 0.5f * n) d -= n;
+  return d;
+}
 __global__ void k_init_rho(const View v, const double *bub, int32_t nb, double rho_l,
                            double rho_g, double width, double amp, uint64_t key, double *rho) {
   const int64_t N = v.NX * v.NY * v.NZ;
+  const float nxf = (float)v.NX, nyf = (float)v.NY, nzf = (float)v.NZ;
   GRID_LOOP(k, N) {
     const Idx c = idx_of(k, v);
     double r = rho_l;
     if (nb > 0) {
+      float s32 = INFINITY;
+      for (int b = 0; b < nb; ++b) {
+        const float dx = min_image_f((float)c.x - (float)bub[4 * b + 0], nxf);
+        const float dy = min_image_f((float)c.y - (float)bub[4 * b + 1], nyf);
+        const float dz = min_image_f((float)c.z - (float)bub[4 * b + 2], nzf);
+        const float d = sqrtf(dx * dx + dy * dy + dz * dz) - (float)bub[4 * b + 3];
+        s32 = fminf(s32, d);
+      }
       double s = INFINITY;
       for (int b = 0; b < nb; ++b) {
+        const float dxf = min_image_f((float)c.x - (float)bub[4 * b + 0], nxf);
+        const float dyf = min_image_f((float)c.y - (float)bub[4 * b + 1], nyf);
+        const float dzf = min_image_f((float)c.z - (float)bub[4 * b + 2], nzf);
+        if (sqrtf(dxf * dxf + dyf * dyf + dzf * dzf) - (float)bub[4 * b + 3] > s32 + 1e-3f) continue;
         const double dx = min_image((double)c.x - bub[4 * b + 0], (double)v.NX);
         const double dy = min_image((double)c.y - bub[4 * b + 1], (double)v.NY);
         const double dz = min_image((double)c.z - bub[4 * b + 2], (double)v.NZ);
-        const double d = sqrt(dx * dx + dy * dy + dz * dz) - bub[4 * b + 3];
+        const double d =
+            __dadd_rn(sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz))),
+                      -bub[4 * b + 3]);
         s = d < s ? d : s;
       }
       r = rho_g + 0.5 * (rho_l - rho_g) * (1.0 + tanh(2.0 * s / width));
@@ -315,6 +340,109 @@ __global__ void __launch_bounds__(TPB) k_totals_final(const double *part, double
   }
 }
 
+// ---- one pass for the diagnostic interval (FP32-arithmetic storages) -------
+// Per cell, the offsets g_i are summed with an error-free FP32 transformation
+// (TwoSum, Knuth TAOCP vol. 2, 4.2.2): the pair (hi, lo) holds sum g exactly
+// up to FP32 underflow, and hi + lo is added to a per-thread FP64
+// accumulator; threads and blocks are combined in FP64 in a fixed order, so
+// the mass (N rho_ref + sum of offsets) is an FP64 reduction that repeated
+// calls reproduce bit for bit.  Momentum (sum g c_i; the w_i rho_ref part
+// cancels) is reduced the same way.
+// The gas decision rho < threshold is taken in FP64, exactly as the FP64
+// moments of the decoded populations would take it, whenever the FP32
+// density is within 1e-5 of the threshold; elsewhere hi decides.
+constexpr int SCAN_BLOCKS = 1024;
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += err;
+}
+template <int LAT, int ST>
+__global__ void __launch_bounds__(TPB) k_scan(const View v, const void *stored, double thr,
+                                              int32_t *labels, double *part, int *err) {
+  using L = Lattice<LAT>;
+  using S = Storage<ST>;
+  using T = typename S::T;
+  __shared__ double sh[4][TPB];
+  const int64_t N = v.NX * v.NY * v.NZ;
+  const int64_t pop = v.px * v.NY * v.NZ;
+  const T *f = static_cast<const T *>(stored);
+  const float rho_ref = (float)v.rho_ref, thr_f = (float)thr;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  bool bad = false;
+  for (int64_t k = blockIdx.x * (int64_t)TPB + threadIdx.x; k < N;
+       k += (int64_t)SCAN_BLOCKS * TPB) {
+    const Idx c = idx_of(k, v);
+    const int64_t o = ((int64_t)c.z * v.NY + c.y) * v.px + c.x;
+    float g[L::Q];
+    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      g[i] = S::load(f[i * pop + o]);
+      two_sum(hi[0], lo[0], g[i]);
+      if (L::cx(i) != 0) two_sum(hi[1], lo[1], L::cx(i) > 0 ? g[i] : -g[i]);
+      if (L::cy(i) != 0) two_sum(hi[2], lo[2], L::cy(i) > 0 ? g[i] : -g[i]);
+      if (L::cz(i) != 0) two_sum(hi[3], lo[3], L::cz(i) > 0 ? g[i] : -g[i]);
+    }
+    if (!isfinite(hi[0])) bad = true;
+    if (labels) {
+      const float r32 = rho_ref + hi[0];
+      bool gas;
+      if (fabsf(r32 - thr_f) > 1e-5f) {
+        gas = r32 < thr_f;
+      } else {
+        double r64 = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) r64 += __dadd_rn(__dmul_rn(L::w(i), v.rho_ref), (double)g[i]);
+        gas = r64 < thr;
+      }
+      labels[k] = gas ? (int32_t)k : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += (double)hi[q] + (double)lo[q];
+  }
+  if (bad && err) atomicOr(err, ERR_NONFINITE);
+  if (!part) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = TPB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 4; ++q) part[4 * blockIdx.x + q] = sh[q][0];
+}
+
+template <int LAT>
+__global__ void __launch_bounds__(TPB) k_scan_final(const double *part, double mass0, double *out) {
+  __shared__ double sh[4][TPB];
+  double a[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < SCAN_BLOCKS; b += TPB)
+    for (int q = 0; q < 4; ++q) a[q] += part[4 * b + q];
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int w = TPB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = mass0 + sh[0][0];
+    out[1] = sh[1][0];
+    if (LAT == D2Q9) {  // view (x, 1, y) -> user (x, y)
+      out[2] = sh[3][0];
+      out[3] = 0.0;
+    } else {
+      out[2] = sh[2][0];
+      out[3] = sh[3][0];
+    }
+  }
+}
+
 // ---- connected components (union-find, links always from the larger root
 // to the smaller, so every root is its component's minimum index) ---------
 __device__ __forceinline__ int32_t uf_find(const int32_t *L, int32_t x) {
@@ -497,6 +625,31 @@ cudaError_t diag_totals(const View &v, const void *stored, double *partials, dou
     k_totals_final<D3Q19><<<1, TPB, 0, s>>>(partials, out4);
   else
     k_totals_final<D2Q9><<<1, TPB, 0, s>>>(partials, out4);
+  return cudaGetLastError();
+}
+
+int diag_scan_blocks() { return SCAN_BLOCKS; }
+
+cudaError_t diag_scan(const View &v, const void *stored, double thr, int32_t *labels,
+                      double *partials, double *out4, int *err, cudaStream_t s) {
+  dispatch(v, [&](auto L, auto S) {
+    constexpr int lat = decltype(L)::value, st = decltype(S)::value;
+    if constexpr (st != ST_F64) {
+      k_scan<lat, st><<<SCAN_BLOCKS, TPB, 0, s>>>(v, stored, thr, labels, partials, err);
+      if (out4)
+        k_scan_final<lat><<<1, TPB, 0, s>>>(partials, (double)ncells(v) * v.rho_ref, out4);
+    }
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t diag_label_links(const View &v, int32_t *labels, unsigned long long *ncomp_dev,
+                             cudaStream_t s) {
+  const int64_t N = ncells(v);
+  cudaError_t e = cudaMemsetAsync(ncomp_dev, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_ccl_union<<<nblocks(N), TPB, 0, s>>>(v, labels);
+  k_ccl_compress<<<nblocks(N), TPB, 0, s>>>(N, labels, ncomp_dev);
   return cudaGetLastError();
 }
 

@@ -120,6 +120,15 @@ cudaError_t diag_line_d2(const View &v, const double *p, int64_t x0, int64_t y0,
 int diag_totals_blocks();
 cudaError_t diag_totals(const View &v, const void *stored, double *partials, double *out4,
                         cudaStream_t s);
+// One pass over the populations of an FP32-arithmetic storage: gas labels
+// initialised from rho < thr (labels may be null) and the totals (partials:
+// 4*diag_scan_blocks() doubles; out4 may be null).  Not for LBM_F64.
+int diag_scan_blocks();
+cudaError_t diag_scan(const View &v, const void *stored, double thr, int32_t *labels,
+                      double *partials, double *out4, int *err, cudaStream_t s);
+// union-find linking and compression of initialised labels
+cudaError_t diag_label_links(const View &v, int32_t *labels, unsigned long long *ncomp_dev,
+                             cudaStream_t s);
 // connected components of rho < thr; labels N int32; count -> *ncomp_dev (int64)
 cudaError_t diag_label(const View &v, const double *rho, double thr, int32_t *labels,
                        unsigned long long *ncomp_dev, cudaStream_t s);

@@ -119,9 +119,12 @@ struct Storage<ST_BF16> {
 };
 
 // f_i from a stored value and back, in double (diagnostics, state I/O)
+// (no FMA contraction: every path that decodes a stored value gets the same
+// double, which the host-side checks rely on)
 template <int ST>
 __device__ __forceinline__ double decode_f(typename Storage<ST>::T v, double wref) {
-  return Storage<ST>::OFFSET ? wref + (double)Storage<ST>::load(v) : (double)Storage<ST>::load(v);
+  return Storage<ST>::OFFSET ? __dadd_rn(wref, (double)Storage<ST>::load(v))
+                             : (double)Storage<ST>::load(v);
 }
 template <int ST>
 __device__ __forceinline__ typename Storage<ST>::T encode_f(double f, double wref) {

@@ -85,6 +85,7 @@ def _load():
         "lbm_sync": (i32, [P_]),
         "lbm_pressure_laplacian": (i32, [P_, P_, i64, P_]),
         "lbm_label_gas": (i32, [P_, P_, C.POINTER(i64)]),
+        "lbm_diagnose": (i32, [P_, P_, P_, C.POINTER(i64)]),
         "lbm_site_labels": (i32, [P_, P_, i32, C.POINTER(i64)]),
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
@@ -105,7 +106,8 @@ _lib = _load()
 EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites",
            "lbm_seed_bubbles", "lbm_inject", "lbm_read_budgets", "lbm_step", "lbm_step_count",
            "lbm_autotune", "lbm_plan_info",
-           "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_site_labels",
+           "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose",
+           "lbm_site_labels",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_last_error", "lbm_version")
 
 
@@ -296,6 +298,15 @@ class Lattice:
         nc = C.c_int64(0)
         _check(_lib.lbm_label_gas(self._h, _ptr(lab) if want_labels else None, C.byref(nc)))
         return lab, int(nc.value)
+
+    def diagnose(self, want_labels=False):
+        """One diagnostic interval: (totals[4], labels or None, components)."""
+        tot = np.zeros(4)
+        lab = np.empty(self.shape, dtype=np.int32) if want_labels else None
+        nc = C.c_int64(0)
+        _check(_lib.lbm_diagnose(self._h, _ptr(tot), _ptr(lab) if want_labels else None,
+                                 C.byref(nc)))
+        return tot, lab, int(nc.value)
 
     def site_labels(self):
         out = np.empty(self.nsites, dtype=np.int32)

@@ -330,3 +330,32 @@ def test_autotune_preserves_state_and_results(lbm):
     assert rel_err(f_tuned, R.read("f")) < 1e-6
     L.close()
     R.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "f64"])
+def test_diagnose_one_pass_and_threshold_guard(lbm, storage):
+    """lbm_diagnose gives the labels of the FP64 moments of the stored state
+    bit for bit, also for cells whose density lies within 1e-7 of the
+    threshold (where the FP32 sum must defer to FP64), and the totals of
+    lbm_totals."""
+    nx, ny, nz = 24, 20, 12
+    c, w = O.velocities(O.D3Q19)
+    rng = np.random.default_rng(5)
+    rho = rng.uniform(0.2, 1.9, size=(nz, ny, nx))
+    near = rng.random((nz, ny, nx)) < 0.3
+    rho[near] = 1.0 + rng.choice([-1, 1], near.sum()) * rng.uniform(0, 1e-7, near.sum())
+    f0 = w[:, None, None, None] * rho[None] * rng.uniform(0.97, 1.03, size=(19, nz, ny, nx))
+    L = lbm.Lattice("D3Q19", nx, ny, nz, storage=storage, rho_ref=2.0, gas_threshold=1.0)
+    L.write_f(f0)
+    f = L.read("f")
+    rho_o = O.moments(O.D3Q19, f)[0]
+    lab_o, n_o = O.label_gas(O.D3Q19, rho_o, 1.0)
+    tot, lab, n = L.diagnose(want_labels=True)
+    assert n == n_o and (lab == lab_o).all()
+    lab2, n2 = L.label_gas()
+    assert n2 == n_o and (lab2 == lab_o).all()
+    t2 = L.totals()
+    assert (tot == t2).all()
+    to = O.totals(O.D3Q19, f)
+    assert abs(tot[0] - to[0]) < 1e-10 * to[0] and np.abs(tot[1:] - to[1:]).max() < 1e-9
+    L.close()
