@@ -241,6 +241,27 @@ lbm_status lbm_read(lbm_ctx *ctx, int32_t field, double *host_dst, size_t bytes)
  * to the storage precision); marks the context seeded.  bytes = Q*N*8. */
 lbm_status lbm_write_f(lbm_ctx *ctx, const double *host_src, size_t bytes);
 
+/* Allocation-free time step.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate device memory - code that runs while
+ * a CUDA graph is being captured, hosts that forbid cudaMalloc inside their
+ * time loop, programs with a fixed device-memory budget.  It advances FP32
+ * populations f_in -> f_out by one step of the two-pass kernels (no
+ * injection).  Layout: Q fields of nx*ny*nz floats, f[i*N + cell], cell =
+ * x + nx*(y + ny*z), the post-streaming form lbm_read(LBM_F) returns, plain
+ * values (no offset).  The psi field passed between the two kernels lives
+ * in a file-scope device array of 2,097,152 floats (8 MB) that every GPU
+ * loading the library holds until the process exits; larger lattices are
+ * rejected with LBM_EINVAL.  The first call on a device looks up that
+ * array's device address and caches it; make that first call before any
+ * stream capture.  Every call uses the same array: calls that overlap on
+ * the GPU (other streams or threads without ordering) race on it.  f_in and
+ * f_out are distinct device buffers owned by the caller; stream may be
+ * NULL.  Asynchronous; no memory is allocated or freed.  Errors: EINVAL,
+ * ECUDA. */
+lbm_status lbm_step_static_f32(int32_t lattice, int64_t nx, int64_t ny, int64_t nz, double tau,
+                               double G, double rho0, const float *f_in, float *f_out,
+                               void *stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *lbm_last_error(void);
 

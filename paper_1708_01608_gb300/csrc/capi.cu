@@ -199,6 +199,9 @@ lbm_status set_device(lbm_ctx *c) {
 
 }  // namespace
 
+// record a failure for lbm_last_error() from another translation unit
+lbm_status sclbm::set_error(lbm_status st, const char *msg) { return fail(st, msg); }
+
 // ---- gather/scatter of one population (diag.cu) ----------------------------
 namespace sclbm {
 cudaError_t diag_gather_pop(const View &v, const void *stored, int i, double *out, cudaStream_t s);

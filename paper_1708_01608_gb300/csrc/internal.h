@@ -5,7 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm.h"
+
 namespace sclbm {
+
+// store a message for lbm_last_error() and return st
+lbm_status set_error(lbm_status st, const char *msg);
 
 // Everything a step kernel needs.  Cells are addressed in the kernels'
 // three-dimensional view (D2Q9 on (nx, 1, ny)); the population arrays are

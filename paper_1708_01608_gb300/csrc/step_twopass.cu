@@ -4,6 +4,8 @@
 // injection runs as a third, one-thread-per-site kernel.  This path moves
 // 3*Q*S + 2*sizeof(psi) bytes per update instead of the fused kernel's
 // 2*Q*S; it is kept as a simple, independently written comparison path.
+#include <mutex>
+
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -189,3 +191,86 @@ cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi, cudaSt
 }
 
 }  // namespace sclbm
+
+// ---- allocation-free time step ---------------------------------------------
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+// being captured, hosts that forbid device allocation inside their time
+// loop, or programs that hand the library a fixed memory budget.  The
+// two-pass step needs a psi field between its two kernels; this entry point
+// keeps that field in a file-scope device array of fixed size, so it
+// allocates nothing.  Its device address is looked up once per device (the
+// array's name is only a host-side stand-in in host code).
+namespace sclbm {
+namespace {
+
+constexpr int64_t kStaticPsiCells = 2097152;  // 8 MB of FP32: up to 128^3 cells
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) float g_static_psi[kStaticPsiCells];
+
+std::mutex g_static_mu;
+float *g_static_psi_ptr[kMaxDevices] = {};
+
+// device address of g_static_psi on the current device (looked up once)
+cudaError_t static_psi_address(float **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_psi_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_psi);
+    if (e != cudaSuccess) return e;
+    g_static_psi_ptr[dev] = static_cast<float *>(p);
+  }
+  *out = g_static_psi_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace sclbm
+
+extern "C" lbm_status lbm_step_static_f32(int32_t lattice, int64_t nx, int64_t ny, int64_t nz,
+                                          double tau, double G, double rho0, const float *f_in,
+                                          float *f_out, void *stream) {
+  using namespace sclbm;
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19)
+    return set_error(LBM_EINVAL, "lbm_step_static_f32: unknown lattice");
+  if (nx < 1 || ny < 1 || nz < 1 || (lattice == LBM_D2Q9 && nz != 1))
+    return set_error(LBM_EINVAL, "lbm_step_static_f32: extents must be >= 1 (nz = 1 for D2Q9)");
+  if (nx > kStaticPsiCells || ny > kStaticPsiCells || nz > kStaticPsiCells ||
+      nx * ny * nz > kStaticPsiCells)
+    return set_error(LBM_EINVAL,
+                     "lbm_step_static_f32: more than 2097152 cells, the size of the static "
+                     "scratch array (use lbm_create/lbm_step for larger lattices)");
+  if (!(tau > 0.5) || !(rho0 > 0) || !(G == G))
+    return set_error(LBM_EINVAL, "lbm_step_static_f32: tau must be > 0.5, rho0 > 0");
+  if (!f_in || !f_out || static_cast<const void *>(f_in) == static_cast<const void *>(f_out))
+    return set_error(LBM_EINVAL, "lbm_step_static_f32: f_in and f_out must be distinct buffers");
+  float *psi = nullptr;
+  cudaError_t e = static_psi_address(&psi);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LBM_ECUDA, cudaGetErrorString(e));
+  }
+  StepArgs a{};
+  a.fin = f_in;
+  a.fout = f_out;
+  a.NX = nx;
+  a.NY = lattice == LBM_D2Q9 ? 1 : ny;  // D2Q9 runs on the view (nx, 1, ny)
+  a.NZ = lattice == LBM_D2Q9 ? ny : nz;
+  a.px = nx;
+  a.tau = tau;
+  a.G = G;
+  a.rho0 = rho0;
+  a.rho_ref = 0.0;  // plain f_i, no offset
+  a.nsites = 0;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  e = lattice == LBM_D2Q9 ? tp_launch_t<D2Q9, ST_F32>(a, psi, s) : tp_launch_t<D3Q19, ST_F32>(a, psi, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LBM_ECUDA, cudaGetErrorString(e));
+  }
+  return LBM_OK;
+}

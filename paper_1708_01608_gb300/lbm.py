@@ -90,6 +90,7 @@ def _load():
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
         "lbm_write_f": (i32, [P_, P_, sz]),
+        "lbm_step_static_f32": (i32, [i32, i64, i64, i64, d, d, d, P_, P_, P_]),
         "lbm_last_error": (C.c_char_p, []),
         "lbm_version": (C.c_char_p, []),
     }
@@ -108,7 +109,8 @@ EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites"
            "lbm_autotune", "lbm_plan_info",
            "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose",
            "lbm_site_labels",
-           "lbm_totals", "lbm_read", "lbm_write_f", "lbm_last_error", "lbm_version")
+           "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_last_error",
+           "lbm_version")
 
 
 def lib():
@@ -319,3 +321,11 @@ class Lattice:
         out = np.zeros(4)
         _check(_lib.lbm_totals(self._h, _ptr(out)))
         return out
+
+
+def step_static_f32(lattice, nx, ny, nz, tau, G, rho0, f_in_ptr, f_out_ptr, stream=None):
+    """One allocation-free step on caller-owned device buffers (see
+    lbm_step_static_f32 in include/lbm.h): pointers are device addresses."""
+    lat = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
+    _check(_lib.lbm_step_static_f32(lat, nx, ny, nz, tau, G, rho0, C.c_void_p(f_in_ptr),
+                                    C.c_void_p(f_out_ptr), C.c_void_p(stream) if stream else None))
