@@ -582,13 +582,23 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best_tile, double *b
     CK(cudaEventCreate(&e1));
     FusedPlan best{};
     float best_t = 1e30f;
-    for (int tile = 1; tile < 64; ++tile) {
+    for (int cand = 0; cand < 64 * 3; ++cand) {
+      // every tile, with the one-wave number of z chunks, half and double it
+      const int tile = 1 + cand / 3, variant = cand % 3;
       int bx, by, ns;
       if (!fused_tile_shape(c->lat, c->st, tile, &bx, &by, &ns)) continue;
       FusedPlan p;
       if (fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, 0, &p) != cudaSuccess) {
         cudaGetLastError();
         continue;
+      }
+      if (variant > 0) {
+        const int nzc = variant == 1 ? std::max(1, p.nzc / 2) : p.nzc * 2;
+        if (nzc == p.nzc || nzc > c->v.NZ) continue;
+        if (fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, nzc, &p) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
       }
       CKS(use_plan(c, p));
       CKS(lbm_step(c, 2));

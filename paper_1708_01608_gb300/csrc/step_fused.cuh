@@ -24,6 +24,8 @@
 // and returns without writing further planes.
 #pragma once
 
+#include <climits>
+
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(BX *BY)
     sp = a.bucket_off[item];
     send = a.bucket_off[item + 1];
   }
+  int next_z = sp < send ? a.site_z[a.bucket_site[sp]] : INT_MAX;  // plane of the next site
 
   // destination coordinates of the push, fixed per thread (periodic)
   const int x = x0 + tx, y = y0 + ty;
@@ -261,10 +264,9 @@ __global__ void __launch_bounds__(BX *BY)
       const int Pc = P - 1;
       double dm = 0.0;  // blowing-agent mass deposited in this cell this step
       bool site = false;
-      if (a.nsites > 0) {
-        while (sp < send && a.site_z[a.bucket_site[sp]] < Pc) ++sp;
-        for (int q = sp; q < send; ++q) {
-          const int sidx = a.bucket_site[q];
+      if (Pc == next_z) {  // sites of this CTA in this plane (rare)
+        for (; sp < send; ++sp) {
+          const int sidx = a.bucket_site[sp];
           if (a.site_z[sidx] != Pc) break;
           if (active && a.site_x[sidx] == x && a.site_y[sidx] == y) {
             const double b = a.budget[sidx];
@@ -276,6 +278,7 @@ __global__ void __launch_bounds__(BX *BY)
             }
           }
         }
+        next_z = sp < send ? a.site_z[a.bucket_site[sp]] : INT_MAX;
       }
       if (active) {
         const C *pm = ring + ((k - 2) & 3) * PW * PH;
