@@ -204,6 +204,45 @@ lbm_status lbm_sync(lbm_ctx *ctx);
 lbm_status lbm_pressure_laplacian(lbm_ctx *ctx, double *out, int64_t count,
                                   const int64_t *line);
 
+/* Film between two bubbles (Sec. 3.1 / Sec. 4: the second derivative of the
+ * pressure across the film is the rupture criterion).  line = {x, y, z,
+ * axis, len}: len cells from (x,y,z) along the axis, starting inside bubble
+ * A and ending inside bubble B.  With rho_mid the density separating gas
+ * from liquid: x1 = first upward crossing of rho_mid along the line, x2 =
+ * the next downward crossing (linear interpolation between cells, in cells
+ * from the start), h = x2 - x1 the film thickness, d2p_mid = p(c+e) - 2p(c)
+ * + p(c-e) at the line cell c nearest to (x1+x2)/2 (FP64 EOS pressure; the
+ * mean of the two cells when the midpoint is exactly half-way), r_d = half
+ * the number of rows along the next axis ((axis+1) mod dims), contiguous
+ * with the midpoint row, whose liquid run along the axis through the
+ * midpoint column is no thicker than h + 2 (the film disc radius of Sec. 3).
+ * found = 0 when no such film exists (the bubbles have merged).
+ * Synchronous. */
+typedef struct {
+  int32_t found;
+  double x1, x2, h, d2p_mid, r_d;
+} lbm_film;
+lbm_status lbm_film_probe(lbm_ctx *ctx, const int64_t *line, double rho_mid, lbm_film *out);
+
+/* Rupture criterion of Sec. 3.1 (eta_m switches when d2p/dn2 = 0 across the
+ * film; Sec. 4: rupture starts at that point).  Advance in chunks of
+ * diag_every steps, probing the film after each chunk (lbm_film_probe).
+ * Exact zeros do not occur in floating point and a thick film's liquid
+ * plateau has d2p/dn2 ~ 0 trivially, so the criterion is armed once the
+ * midpoint value has been below -eps_arm and fires at the first later probe
+ * where it is >= 0.  Stops when it fires (fired = 1, h_c = h and r_d of that
+ * probe), when a probe finds no film (merged = 1: the bubbles joined before
+ * the criterion), or after max_steps.  out->steps = steps taken by this
+ * call.  Synchronous. */
+typedef struct {
+  int32_t fired, merged;
+  int64_t steps;
+  double h_c, r_d;
+} lbm_rupture;
+lbm_status lbm_run_until_rupture(lbm_ctx *ctx, const int64_t *line, double rho_mid,
+                                  double eps_arm, int64_t diag_every, int64_t max_steps,
+                                  lbm_rupture *out);
+
 /* Gas connected-component labelling: gas cells are rho < gas_threshold
  * (FP64 density), face-connected (4 in 2-D, 6 in 3-D) with periodic wrap;
  * each gas cell gets the smallest linear index of its component, liquid

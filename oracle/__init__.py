@@ -67,6 +67,8 @@ def _L():
         _lib.orc_label_gas.argtypes = [C.c_int, i64, i64, i64, P, d, P]
         _lib.orc_label_gas.restype = i64
         _lib.orc_totals.argtypes = [C.c_int, i64, i64, i64, P, P]
+        _lib.orc_film_probe.argtypes = [C.c_int, i64, i64, i64, P, P, i64, i64, i64, C.c_int, i64,
+                                        d, P]
     return _lib
 
 
@@ -209,3 +211,40 @@ def totals(lat, f):
     out = np.zeros(4)
     _L().orc_totals(lat, nx, ny, nz, _p(f), _p(out))
     return out
+
+
+def film_probe(lat, rho, p, start, axis, length, rho_mid):
+    """Film between two bubbles along a line from inside bubble A (Sec. 3.1,
+    Sec. 4): dict(found, x1, x2, h, d2p_mid, r_d); see sc_oracle.c."""
+    rho = _f64(rho)
+    p = _f64(p)
+    nz, ny, nx = rho.shape
+    out = np.zeros(6)
+    _L().orc_film_probe(lat, nx, ny, nz, _p(rho), _p(p), int(start[0]), int(start[1]),
+                        int(start[2]), int(axis), int(length), float(rho_mid), _p(out))
+    return dict(found=bool(out[0]), x1=out[1], x2=out[2], h=out[3], d2p_mid=out[4], r_d=out[5])
+
+
+def run_until_rupture(lat, f, tau, G, start, axis, length, rho_mid, eps_arm, max_steps,
+                      diag_every, rho0=1.0):
+    """The rupture criterion of Sec. 3.1 / Sec. 4 as a plain loop: advance f,
+    probe the film every diag_every steps; the criterion is armed once the
+    film-midpoint d2p/dn2 has been below -eps_arm and fires at the first
+    probe where it is >= 0.  A probe that finds no film ends the run as a
+    merge before the criterion.  Returns dict(fired, merged, step, h_c, r_d,
+    f)."""
+    armed = False
+    t = 0
+    while t < max_steps:
+        f = run(lat, f, diag_every, tau, G, rho0)
+        t += diag_every
+        rho = moments(lat, f)[0]
+        _, p = eos(rho, G, rho0)
+        pr = film_probe(lat, rho, p, start, axis, length, rho_mid)
+        if not pr["found"]:
+            return dict(fired=False, merged=True, step=t, h_c=0.0, r_d=0.0, f=f)
+        if pr["d2p_mid"] < -eps_arm:
+            armed = True
+        elif armed and pr["d2p_mid"] >= 0.0:
+            return dict(fired=True, merged=False, step=t, h_c=pr["h"], r_d=pr["r_d"], f=f)
+    return dict(fired=False, merged=False, step=t, h_c=0.0, r_d=0.0, f=f)

@@ -481,3 +481,119 @@ void orc_totals(int lat, int64_t nx, int64_t ny, int64_t nz, const double *f,
   out[2] = b;
   out[3] = c;
 }
+
+/* ---- film probe (Sec. 3.1 / Sec. 4: pressure second derivative across the
+ * film between two bubbles) ----------------------------------------------------
+ * Along `len` cells from (x0,y0,z0) in direction e_axis (from inside bubble A
+ * towards bubble B), with rho_mid the density separating gas from liquid:
+ *   x1 = first upward crossing of rho_mid (linear interpolation between the
+ *        two cells), x2 = the next downward crossing; h = x2 - x1 is the film
+ *        thickness.
+ *   d2p/dn2 at the film midpoint xm = (x1+x2)/2: p(c+e)-2p(c)+p(c-e) at the
+ *        nearest line cell c (mean of the two cells when xm is exactly half-way).
+ *   R_d: through the midpoint cell, walk along e_perp (axis+1, modulo the
+ *        lattice dimension); in every row whose midpoint cell is liquid the
+ *        local thickness is the length of the liquid run along e_axis through
+ *        it (interpolated crossings on both sides).  The rows contiguous with
+ *        the centre row whose thickness is <= h + 2 form the film disc, and
+ *        R_d is half its extent in cells.
+ * out = {found, x1, x2, h, d2p_mid, R_d}; found = 0 when no film exists. */
+static double lerp_cross(double ra, double rb, double mid) { return (mid - ra) / (rb - ra); }
+
+static int64_t cell_at(int64_t nx, int64_t ny, int64_t nz, int64_t x, int64_t y, int64_t z) {
+  return wrap(x, nx) + nx * (wrap(y, ny) + ny * wrap(z, nz));
+}
+
+/* thickness of the liquid run along e through cell (x,y,z); -1 if gas */
+static double run_thickness(int64_t nx, int64_t ny, int64_t nz, const double *rho, int64_t x,
+                            int64_t y, int64_t z, const int e[3], double mid, int64_t maxlen) {
+  if (rho[cell_at(nx, ny, nz, x, y, z)] < mid) return -1.0;
+  double lo = 0, hi = 0;
+  int64_t m;
+  for (m = 1; m <= maxlen; ++m) { /* backwards */
+    double ra = rho[cell_at(nx, ny, nz, x - (m - 1) * e[0], y - (m - 1) * e[1], z - (m - 1) * e[2])];
+    double rb = rho[cell_at(nx, ny, nz, x - m * e[0], y - m * e[1], z - m * e[2])];
+    if (rb < mid) {
+      lo = -((double)(m - 1) + lerp_cross(ra, rb, mid));
+      break;
+    }
+  }
+  if (m > maxlen) return -1.0;
+  for (m = 1; m <= maxlen; ++m) { /* forwards */
+    double ra = rho[cell_at(nx, ny, nz, x + (m - 1) * e[0], y + (m - 1) * e[1], z + (m - 1) * e[2])];
+    double rb = rho[cell_at(nx, ny, nz, x + m * e[0], y + m * e[1], z + m * e[2])];
+    if (rb < mid) {
+      hi = (double)(m - 1) + lerp_cross(ra, rb, mid);
+      break;
+    }
+  }
+  if (m > maxlen) return -1.0;
+  return hi - lo;
+}
+
+void orc_film_probe(int lat, int64_t nx, int64_t ny, int64_t nz, const double *rho,
+                    const double *p, int64_t x0, int64_t y0, int64_t z0, int axis, int64_t len,
+                    double mid, double *out) {
+  int e[3] = {0, 0, 0}, ep[3] = {0, 0, 0};
+  int dims = lat == ORC_D2Q9 ? 2 : 3;
+  e[axis] = 1;
+  ep[(axis + 1) % dims] = 1;
+  for (int q = 0; q < 6; ++q) out[q] = 0.0;
+  double x1 = -1, x2 = -1;
+  int64_t m;
+  for (m = 1; m < len; ++m) {
+    double ra = rho[cell_at(nx, ny, nz, x0 + (m - 1) * e[0], y0 + (m - 1) * e[1], z0 + (m - 1) * e[2])];
+    double rb = rho[cell_at(nx, ny, nz, x0 + m * e[0], y0 + m * e[1], z0 + m * e[2])];
+    if (ra < mid && rb >= mid) {
+      x1 = (double)(m - 1) + lerp_cross(ra, rb, mid);
+      break;
+    }
+  }
+  if (x1 < 0) return;
+  for (++m; m < len; ++m) {
+    double ra = rho[cell_at(nx, ny, nz, x0 + (m - 1) * e[0], y0 + (m - 1) * e[1], z0 + (m - 1) * e[2])];
+    double rb = rho[cell_at(nx, ny, nz, x0 + m * e[0], y0 + m * e[1], z0 + m * e[2])];
+    if (ra >= mid && rb < mid) {
+      x2 = (double)(m - 1) + lerp_cross(ra, rb, mid);
+      break;
+    }
+  }
+  if (x2 < 0) return;
+  double h = x2 - x1, xm = 0.5 * (x1 + x2);
+  double fl = floor(xm);
+  int64_t c = (int64_t)fl;
+  double d2;
+  if (xm - fl == 0.5) {
+    double dd[2];
+    for (int k = 0; k < 2; ++k) {
+      int64_t cc = c + k;
+      dd[k] = p[cell_at(nx, ny, nz, x0 + (cc + 1) * e[0], y0 + (cc + 1) * e[1], z0 + (cc + 1) * e[2])] -
+              2.0 * p[cell_at(nx, ny, nz, x0 + cc * e[0], y0 + cc * e[1], z0 + cc * e[2])] +
+              p[cell_at(nx, ny, nz, x0 + (cc - 1) * e[0], y0 + (cc - 1) * e[1], z0 + (cc - 1) * e[2])];
+    }
+    d2 = 0.5 * (dd[0] + dd[1]);
+  } else {
+    int64_t cc = xm - fl < 0.5 ? c : c + 1;
+    d2 = p[cell_at(nx, ny, nz, x0 + (cc + 1) * e[0], y0 + (cc + 1) * e[1], z0 + (cc + 1) * e[2])] -
+         2.0 * p[cell_at(nx, ny, nz, x0 + cc * e[0], y0 + cc * e[1], z0 + cc * e[2])] +
+         p[cell_at(nx, ny, nz, x0 + (cc - 1) * e[0], y0 + (cc - 1) * e[1], z0 + (cc - 1) * e[2])];
+  }
+  /* film disc along e_perp through the midpoint cell */
+  int64_t cm = (int64_t)floor(xm + 0.5);
+  int64_t xc = x0 + cm * e[0], yc = y0 + cm * e[1], zc = z0 + cm * e[2];
+  int64_t extent = 0;
+  for (int sg = -1; sg <= 1; sg += 2) {
+    for (int64_t j = (sg < 0 ? 1 : 0); j <= len; ++j) {
+      double t = run_thickness(nx, ny, nz, rho, xc + sg * j * ep[0], yc + sg * j * ep[1],
+                               zc + sg * j * ep[2], e, mid, len);
+      if (t < 0 || t > h + 2.0) break;
+      ++extent;
+    }
+  }
+  out[0] = 1.0;
+  out[1] = x1;
+  out[2] = x2;
+  out[3] = h;
+  out[4] = d2;
+  out[5] = 0.5 * (double)extent;
+}

@@ -734,6 +734,73 @@ static void count_merges(lbm_ctx *c) {
   c->have_prev = true;
 }
 
+lbm_status lbm_film_probe(lbm_ctx *c, const int64_t *line, double rho_mid, lbm_film *out) {
+  if (!c || !line || !out) return fail(LBM_EINVAL, "NULL argument");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  const int dims = c->lat == D2Q9 ? 2 : 3;
+  if (line[3] < 0 || line[3] >= dims || line[4] < 2)
+    return fail(LBM_EINVAL, "line = {x, y, z, axis (< dims), len >= 2}");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(compute_pressure(c));
+  // user axes -> view axes (D2Q9: x -> x, y -> z)
+  auto vaxis = [&](int a) { return c->lat == D2Q9 ? (a == 0 ? 0 : 2) : a; };
+  int e[3] = {0, 0, 0}, ep[3] = {0, 0, 0};
+  e[vaxis((int)line[3])] = 1;
+  ep[vaxis(((int)line[3] + 1) % dims)] = 1;
+  int64_t x0 = line[0], y0 = line[1], z0 = line[2];
+  if (c->lat == D2Q9) {
+    z0 = y0;
+    y0 = 0;
+  }
+  double *tmp = static_cast<double *>(c->d_tmp.p);
+  CK(diag_film_probe(c->v, static_cast<const double *>(c->d_rho.p),
+                     static_cast<const double *>(c->d_p.p), wrap64(x0, c->v.NX), wrap64(y0, c->v.NY),
+                     wrap64(z0, c->v.NZ), e, ep, line[4], rho_mid, tmp, c->s));
+  double h[6];
+  CK(cudaMemcpyAsync(h, tmp, sizeof(h), cudaMemcpyDeviceToHost, c->s));
+  CKS(sync_and_check(c));
+  out->found = h[0] != 0.0;
+  out->x1 = h[1];
+  out->x2 = h[2];
+  out->h = h[3];
+  out->d2p_mid = h[4];
+  out->r_d = h[5];
+  return LBM_OK;
+}
+
+lbm_status lbm_run_until_rupture(lbm_ctx *c, const int64_t *line, double rho_mid,
+                                  double eps_arm, int64_t diag_every, int64_t max_steps,
+                                  lbm_rupture *out) {
+  if (!c || !line || !out) return fail(LBM_EINVAL, "NULL argument");
+  if (diag_every < 1 || max_steps < 0 || !(eps_arm >= 0))
+    return fail(LBM_EINVAL, "diag_every >= 1, max_steps >= 0, eps_arm >= 0");
+  std::memset(out, 0, sizeof(*out));
+  bool armed = false;
+  int64_t t = 0;
+  while (t < max_steps) {
+    const int64_t n = std::min(diag_every, max_steps - t);
+    CKS(lbm_step(c, n));
+    t += n;
+    lbm_film pr;
+    CKS(lbm_film_probe(c, line, rho_mid, &pr));
+    out->steps = t;
+    if (!pr.found) {  // the film is gone: merged before the criterion fired
+      out->merged = 1;
+      return LBM_OK;
+    }
+    if (pr.d2p_mid < -eps_arm) {
+      armed = true;
+    } else if (armed && pr.d2p_mid >= 0.0) {
+      out->fired = 1;
+      out->h_c = pr.h;
+      out->r_d = pr.r_d;
+      return LBM_OK;
+    }
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_label_gas(lbm_ctx *c, int32_t *labels, int64_t *ncomp) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");

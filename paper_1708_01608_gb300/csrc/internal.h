@@ -137,6 +137,10 @@ cudaError_t diag_label_links(const View &v, int32_t *labels, unsigned long long 
 // connected components of rho < thr; labels N int32; count -> *ncomp_dev (int64)
 cudaError_t diag_label(const View &v, const double *rho, double thr, int32_t *labels,
                        unsigned long long *ncomp_dev, cudaStream_t s);
+// film probe along a line (view coordinates, directions e and ep); out: 6 doubles
+cudaError_t diag_film_probe(const View &v, const double *rho, const double *p, int64_t x0,
+                            int64_t y0, int64_t z0, const int e[3], const int ep[3], int64_t len,
+                            double mid, double *out, cudaStream_t s);
 cudaError_t diag_gather_labels(const int32_t *labels, const int32_t *cells, int32_t n,
                                int32_t *out, cudaStream_t s);
 

@@ -56,6 +56,16 @@ class Bubble(C.Structure):
     _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("r", C.c_double)]
 
 
+class Film(C.Structure):
+    _fields_ = [("found", C.c_int32), ("x1", C.c_double), ("x2", C.c_double), ("h", C.c_double),
+                ("d2p_mid", C.c_double), ("r_d", C.c_double)]
+
+
+class Rupture(C.Structure):
+    _fields_ = [("fired", C.c_int32), ("merged", C.c_int32), ("steps", C.c_int64),
+                ("h_c", C.c_double), ("r_d", C.c_double)]
+
+
 class LBMError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -86,6 +96,8 @@ def _load():
         "lbm_pressure_laplacian": (i32, [P_, P_, i64, P_]),
         "lbm_label_gas": (i32, [P_, P_, C.POINTER(i64)]),
         "lbm_diagnose": (i32, [P_, P_, P_, C.POINTER(i64)]),
+        "lbm_film_probe": (i32, [P_, P_, d, C.POINTER(Film)]),
+        "lbm_run_until_rupture": (i32, [P_, P_, d, d, i64, i64, C.POINTER(Rupture)]),
         "lbm_site_labels": (i32, [P_, P_, i32, C.POINTER(i64)]),
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
@@ -107,7 +119,8 @@ _lib = _load()
 EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites",
            "lbm_seed_bubbles", "lbm_inject", "lbm_read_budgets", "lbm_step", "lbm_step_count",
            "lbm_autotune", "lbm_plan_info",
-           "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose",
+           "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose", "lbm_film_probe",
+           "lbm_run_until_rupture",
            "lbm_site_labels",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_last_error",
            "lbm_version")
@@ -300,6 +313,25 @@ class Lattice:
         nc = C.c_int64(0)
         _check(_lib.lbm_label_gas(self._h, _ptr(lab) if want_labels else None, C.byref(nc)))
         return lab, int(nc.value)
+
+    def film_probe(self, line, rho_mid):
+        """Film between two bubbles along line = (x, y, z, axis, len):
+        dict(found, x1, x2, h, d2p_mid, r_d)."""
+        ln = np.ascontiguousarray(line, dtype=np.int64)
+        out = Film()
+        _check(_lib.lbm_film_probe(self._h, _ptr(ln), float(rho_mid), C.byref(out)))
+        return dict(found=bool(out.found), x1=out.x1, x2=out.x2, h=out.h, d2p_mid=out.d2p_mid,
+                    r_d=out.r_d)
+
+    def run_until_rupture(self, line, rho_mid, eps_arm, diag_every, max_steps):
+        """Rupture criterion (lbm_run_until_rupture): dict(fired, merged, steps,
+        h_c, r_d)."""
+        ln = np.ascontiguousarray(line, dtype=np.int64)
+        out = Rupture()
+        _check(_lib.lbm_run_until_rupture(self._h, _ptr(ln), float(rho_mid), float(eps_arm),
+                                          int(diag_every), int(max_steps), C.byref(out)))
+        return dict(fired=bool(out.fired), merged=bool(out.merged), steps=int(out.steps),
+                    h_c=out.h_c, r_d=out.r_d)
 
     def diagnose(self, want_labels=False):
         """One diagnostic interval: (totals[4], labels or None, components)."""

@@ -359,3 +359,54 @@ def test_diagnose_one_pass_and_threshold_guard(lbm, storage):
     to = O.totals(O.D3Q19, f)
     assert abs(tot[0] - to[0]) < 1e-10 * to[0] and np.abs(tot[1:] - to[1:]).max() < 1e-9
     L.close()
+
+
+def _two_disks(lbm):
+    from paper_1708_01608_gb300.workloads import TWO_DISKS_128 as W
+    L = lbm.Lattice("D2Q9", 128, 128, 1, tau=W["tau"], G=W["G"], storage="f64")
+    L.seed_bubbles(np.array(W["bubbles"]), W["rho_l"], W["rho_g"], W["width"], W["noise"],
+                   W["seed"])
+    return L, W
+
+
+def test_film_probe_same_state(lbm):
+    L, W = _two_disks(lbm)
+    L.step(2800)
+    f = L.read("f")
+    rho = O.moments(O.D2Q9, f)[0]
+    _, p = O.eos(rho, W["G"])
+    for line in [(42, 64, 0, 0, 45), (20, 60, 0, 0, 80)]:
+        ref = O.film_probe(O.D2Q9, rho, p, line[:3], line[3], line[4], 1.075)
+        got = L.film_probe(line, 1.075)
+        assert got["found"] == ref["found"]
+        for k in ("x1", "x2", "h", "d2p_mid", "r_d"):
+            assert abs(got[k] - ref[k]) < 1e-12, (k, got[k], ref[k])
+    L.close()
+
+
+def test_two_disks_rupture_criterion_matches_oracle(lbm):
+    """The criterion fires at the same probe on both sides and h_c agrees
+    within 1 %; both runs start from the same FP64 state."""
+    L, W = _two_disks(lbm)
+    f0 = L.read("f")
+    line = (42, 64, 0, 0, 45)
+    got = L.run_until_rupture(line, 1.075, 1e-3, 100, 5000)
+    ref = O.run_until_rupture(O.D2Q9, f0, W["tau"], W["G"], line[:3], line[3], line[4],
+                              1.075, 1e-3, 5000, 100)
+    assert got["fired"] and ref["fired"]
+    assert got["steps"] == ref["step"]
+    assert abs(got["h_c"] / ref["h_c"] - 1) < 0.01 and got["r_d"] == ref["r_d"]
+    L.close()
+
+
+def test_two_disks_128_fp64_5000_steps(lbm):
+    """The full two-disk run (5000 steps, through the film rupture and the
+    merge): FP64 populations against the oracle."""
+    L, W = _two_disks(lbm)
+    f0 = L.read("f")
+    L.step(5000)
+    fo = O.run(O.D2Q9, f0, 5000, W["tau"], W["G"])
+    err = rel_err(L.read("f"), fo)
+    print("5000-step FP64 relative error", err)
+    assert err < 1e-12
+    L.close()

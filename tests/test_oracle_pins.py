@@ -434,3 +434,52 @@ def test_step_cells_matches_full_step():
     out = O.step_cells(lat, f0, cells, 0.8, -5.0)
     ref = f1.reshape(19, -1)[:, cells].T
     assert np.abs(out - ref).max() < 1e-15
+
+
+# ---------------------------------------------------------------- film probe
+
+def test_film_probe_constructed_slab_and_parabola():
+    """Two gas blocks separated by a liquid slab whose width is exact under
+    linear interpolation; p a parabola with known second difference; the
+    film disc of a slab that widens beyond |dy| = J has R_d = (2J + 1)/2."""
+    nx, ny = 40, 30
+    rho = np.full((1, ny, nx), 2.0)
+    rg, rl, mid = 0.2, 2.0, 1.1
+    J = 4
+    for y in range(ny):
+        dy = abs(y - 15)
+        gap = 6 if dy <= J else 12          # liquid cells between the blocks
+        a_end = 20 - gap // 2               # gas block A: x in [5, a_end)
+        rho[0, y, 5:a_end] = rg
+        rho[0, y, a_end + gap:35] = rg
+    p = 0.05 * (np.arange(nx) - 17.25) ** 2 * np.ones((1, ny, 1))
+    r = O.film_probe(O.D2Q9, rho, p, (8, 15, 0), 0, 25, mid)
+    # crossings: between gas cell a_end-1 and liquid a_end at fraction 0.5
+    a_end = 17
+    assert r["found"]
+    assert abs(r["x1"] - (a_end - 1 - 8 + 0.5)) < 1e-12
+    assert abs(r["h"] - 6.0) < 1e-12
+    assert abs(r["d2p_mid"] - 0.1) < 1e-12          # 2 * 0.05
+    assert r["r_d"] == (2 * J + 1) / 2
+    # no film once the blocks touch
+    rho2 = rho.copy()
+    rho2[0, 15, :] = rg
+    r2 = O.film_probe(O.D2Q9, rho2, p, (8, 15, 0), 0, 25, mid)
+    assert not r2["found"]
+
+
+def test_film_probe_midpoint_tie_averages():
+    nx = 32
+    rho = np.full((1, 1, nx), 2.0)
+    rho[0, 0, :10] = 0.2
+    rho[0, 0, 15:] = 0.2                   # liquid cells 10..14, crossings 9.5 and 14.5
+    p = np.zeros((1, 1, nx))
+    p[0, 0, 12] = 1.0                      # d2(12) = -2, d2(11) = d2(13) = 1
+    r = O.film_probe(O.D2Q9, rho, p, (0, 0, 0), 0, 30, 1.1)
+    assert abs(r["x1"] - 9.5) < 1e-12 and abs(r["x2"] - 14.5) < 1e-12
+    assert r["d2p_mid"] == -2.0            # midpoint 12.0: nearest cell
+    p2 = np.zeros((1, 1, nx))
+    rho[0, 0, 14] = 0.2                    # liquid 10..13: midpoint 11.5 -> tie
+    p2[0, 0, 11] = 1.0
+    r2 = O.film_probe(O.D2Q9, rho, p2, (0, 0, 0), 0, 30, 1.1)
+    assert abs(r2["d2p_mid"] - 0.5 * (-2.0 + 1.0)) < 1e-15
