@@ -227,9 +227,11 @@ lbm_status lbm_film_probe(lbm_ctx *ctx, const int64_t *line, double rho_mid, lbm
 /* Rupture criterion of Sec. 3.1 (eta_m switches when d2p/dn2 = 0 across the
  * film; Sec. 4: rupture starts at that point).  Advance in chunks of
  * diag_every steps, probing the film after each chunk (lbm_film_probe).
- * Exact zeros do not occur in floating point and a thick film's liquid
- * plateau has d2p/dn2 ~ 0 trivially, so the criterion is armed once the
- * midpoint value has been below -eps_arm and fires at the first later probe
+ * Exact zeros do not occur in floating point, and a thick film's liquid
+ * plateau has d2p/dn2 ~ 0 trivially (acoustic transients swing it either
+ * way), so the criterion applies to a thin film, h <= h_max: it is armed
+ * once the midpoint value has been below -eps_arm, disarmed whenever the
+ * film is thicker than h_max, and fires at the first probe of a thin film
  * where it is >= 0.  Stops when it fires (fired = 1, h_c = h and r_d of that
  * probe), when a probe finds no film (merged = 1: the bubbles joined before
  * the criterion), or after max_steps.  out->steps = steps taken by this
@@ -240,8 +242,8 @@ typedef struct {
   double h_c, r_d;
 } lbm_rupture;
 lbm_status lbm_run_until_rupture(lbm_ctx *ctx, const int64_t *line, double rho_mid,
-                                  double eps_arm, int64_t diag_every, int64_t max_steps,
-                                  lbm_rupture *out);
+                                  double eps_arm, double h_max, int64_t diag_every,
+                                  int64_t max_steps, lbm_rupture *out);
 
 /* Gas connected-component labelling: gas cells are rho < gas_threshold
  * (FP64 density), face-connected (4 in 2-D, 6 in 3-D) with periodic wrap;
@@ -279,6 +281,51 @@ lbm_status lbm_read(lbm_ctx *ctx, int32_t field, double *host_dst, size_t bytes)
 /* Overwrite the populations with host data f[i*N + cell] (doubles, rounded
  * to the storage precision); marks the context seeded.  bytes = Q*N*8. */
 lbm_status lbm_write_f(lbm_ctx *ctx, const double *host_src, size_t bytes);
+
+/* ---- batched ensemble of independent two-bubble D2Q9 domains ------------
+ * The bubble-size sweep of Sec. 4 (Fig. 3: critical film thickness h_c
+ * against the film-disc radius R_d) runs many uneven lattices at once: one
+ * launch per time step and tile class covers every active domain, and every
+ * diag_every steps a probe measures each domain's film (lbm_film_probe) and
+ * advances its rupture state machine (lbm_run_until_rupture) on the device.
+ * Domains whose criterion fired, or whose film is gone, stop.  Storage is
+ * FP32 offset form (f_i - w_i rho_ref), arithmetic FP32, probes FP64. */
+typedef struct {
+  int64_t nx, ny;          /* extents: 8..4096, nx a multiple of 4 */
+  double tau, G, rho0, rho_ref;
+  double rho_l, rho_g, width, noise_amp; /* initial state as lbm_seed_bubbles */
+  uint64_t seed;
+  int32_t nbubbles;        /* 0..4 */
+  lbm_bubble bubbles[4];   /* centres (x, y, 0) and radii */
+  int64_t line[5];         /* film probe line {x, y, 0, axis 0/1, len} */
+  double rho_mid;          /* gas / liquid separating density of the probe */
+} lbm_domain;
+
+typedef struct lbm_ensemble lbm_ensemble; /* opaque */
+
+/* Create an ensemble of n domains on the current device (one arena; the
+ * allocator callbacks as in lbm_config, NULL for cudaMalloc) and seed every
+ * domain.  diag_every must be even.  Errors: EINVAL, ENOMEM, ECUDA. */
+lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
+                               double h_max, int32_t diag_every, lbm_alloc_fn alloc,
+                               lbm_free_fn free, void *alloc_user, lbm_ensemble **out);
+void lbm_ensemble_destroy(lbm_ensemble *ens);
+
+/* Run until every domain has stopped or max_steps more steps were taken
+ * (whole diagnostic intervals).  *steps_done (may be NULL) receives the
+ * steps taken.  Synchronous. */
+lbm_status lbm_ensemble_run(lbm_ensemble *ens, int64_t max_steps, int64_t *steps_done);
+
+/* Per domain: fired / merged flags, the step at which it stopped (or the
+ * steps so far), h_c and r_d at firing. */
+lbm_status lbm_ensemble_results(const lbm_ensemble *ens, lbm_rupture *out, int32_t n);
+
+/* out = {steps taken, lattice updates performed (sum over domains of cells x
+ * steps while active), active domains, kernel launches}. */
+lbm_status lbm_ensemble_stats(const lbm_ensemble *ens, double out[4]);
+
+/* Current populations of one domain as doubles f[i*N + x + nx*y]. */
+lbm_status lbm_ensemble_read_f(lbm_ensemble *ens, int32_t domain, double *host, size_t bytes);
 
 /* Allocation-free time step.  The paper has no counterpart: this entry point
  * serves callers that cannot allocate device memory - code that runs while

@@ -226,13 +226,14 @@ def film_probe(lat, rho, p, start, axis, length, rho_mid):
 
 
 def run_until_rupture(lat, f, tau, G, start, axis, length, rho_mid, eps_arm, max_steps,
-                      diag_every, rho0=1.0):
+                      diag_every, rho0=1.0, h_max=8.0):
     """The rupture criterion of Sec. 3.1 / Sec. 4 as a plain loop: advance f,
-    probe the film every diag_every steps; the criterion is armed once the
-    film-midpoint d2p/dn2 has been below -eps_arm and fires at the first
-    probe where it is >= 0.  A probe that finds no film ends the run as a
-    merge before the criterion.  Returns dict(fired, merged, step, h_c, r_d,
-    f)."""
+    probe the film every diag_every steps.  The criterion concerns a thin
+    film (h <= h_max): it is armed once the film-midpoint d2p/dn2 has been
+    below -eps_arm, disarmed whenever the film is thicker than h_max, and
+    fires at the first probe of a thin film where d2p/dn2 >= 0.  A probe
+    that finds no film ends the run as a merge before the criterion.
+    Returns dict(fired, merged, step, h_c, r_d, f)."""
     armed = False
     t = 0
     while t < max_steps:
@@ -243,7 +244,9 @@ def run_until_rupture(lat, f, tau, G, start, axis, length, rho_mid, eps_arm, max
         pr = film_probe(lat, rho, p, start, axis, length, rho_mid)
         if not pr["found"]:
             return dict(fired=False, merged=True, step=t, h_c=0.0, r_d=0.0, f=f)
-        if pr["d2p_mid"] < -eps_arm:
+        if pr["h"] > h_max:
+            armed = False
+        elif pr["d2p_mid"] < -eps_arm:
             armed = True
         elif armed and pr["d2p_mid"] >= 0.0:
             return dict(fired=True, merged=False, step=t, h_c=pr["h"], r_d=pr["r_d"], f=f)

@@ -202,11 +202,6 @@ lbm_status set_device(lbm_ctx *c) {
 // record a failure for lbm_last_error() from another translation unit
 lbm_status sclbm::set_error(lbm_status st, const char *msg) { return fail(st, msg); }
 
-// ---- gather/scatter of one population (diag.cu) ----------------------------
-namespace sclbm {
-cudaError_t diag_gather_pop(const View &v, const void *stored, int i, double *out, cudaStream_t s);
-cudaError_t diag_store_pop(const View &v, const double *f, int i, void *stored, cudaStream_t s);
-}  // namespace sclbm
 
 extern "C" {
 
@@ -770,11 +765,11 @@ lbm_status lbm_film_probe(lbm_ctx *c, const int64_t *line, double rho_mid, lbm_f
 }
 
 lbm_status lbm_run_until_rupture(lbm_ctx *c, const int64_t *line, double rho_mid,
-                                  double eps_arm, int64_t diag_every, int64_t max_steps,
-                                  lbm_rupture *out) {
+                                  double eps_arm, double h_max, int64_t diag_every,
+                                  int64_t max_steps, lbm_rupture *out) {
   if (!c || !line || !out) return fail(LBM_EINVAL, "NULL argument");
-  if (diag_every < 1 || max_steps < 0 || !(eps_arm >= 0))
-    return fail(LBM_EINVAL, "diag_every >= 1, max_steps >= 0, eps_arm >= 0");
+  if (diag_every < 1 || max_steps < 0 || !(eps_arm >= 0) || !(h_max > 0))
+    return fail(LBM_EINVAL, "diag_every >= 1, max_steps >= 0, eps_arm >= 0, h_max > 0");
   std::memset(out, 0, sizeof(*out));
   bool armed = false;
   int64_t t = 0;
@@ -789,7 +784,9 @@ lbm_status lbm_run_until_rupture(lbm_ctx *c, const int64_t *line, double rho_mid
       out->merged = 1;
       return LBM_OK;
     }
-    if (pr.d2p_mid < -eps_arm) {
+    if (pr.h > h_max) {
+      armed = false;  // thick film: the criterion does not apply
+    } else if (pr.d2p_mid < -eps_arm) {
       armed = true;
     } else if (armed && pr.d2p_mid >= 0.0) {
       out->fired = 1;

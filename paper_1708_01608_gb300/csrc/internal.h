@@ -108,6 +108,9 @@ cudaError_t diag_init_rho(const View &v, const double *bub, int32_t nb, double r
 // stored populations from canonical f_i(x) (doubles, Q*N), or from rho at rest
 cudaError_t diag_store_from_f(const View &v, const double *f, void *stored, cudaStream_t s);
 cudaError_t diag_store_from_rho(const View &v, const double *rho, void *stored, cudaStream_t s);
+// one population f_i (N doubles) from / into stored populations
+cudaError_t diag_gather_pop(const View &v, const void *stored, int i, double *out, cudaStream_t s);
+cudaError_t diag_store_pop(const View &v, const double *f, int i, void *stored, cudaStream_t s);
 // canonical f_i(x) (doubles, Q*N) from stored populations
 cudaError_t diag_gather_f(const View &v, const void *stored, double *f, cudaStream_t s);
 // FP64 moments: any output may be null; sets ERR_NONFINITE in err

@@ -69,10 +69,29 @@ struct FusedK {
   static_assert(STAGE_BYTES % 128 == 0, "TMA destinations must be 128-byte aligned");
 };
 
-template <int LAT, int ST, int BX, int BY, int NS>
-__global__ void __launch_bounds__(BX *BY)
-    fused_step_kernel(const __grid_constant__ FusedMaps tm, const StepArgs a, const int tiles_x,
-                      const int tiles_y, const int zlen) {
+// What one CTA's march needs: lattice extents, constants, the TMA
+// descriptors of the input lattice, its column and z chunk, its injection
+// sites (sorted by z), and the status word.
+struct MarchArgs {
+  int NX, NY, NZ;
+  int64_t px;
+  double tau, G, rho0;  // FP64 arithmetic
+  float tau_f, omega_f, G_f, rho0_f, inv_rho0_f, rho_ref_f;
+  const FusedMaps *tm;
+  int x0, y0, zs, ze;
+  int32_t nsites;
+  int sp, send;
+  const int32_t *site_x, *site_y, *site_z, *bucket_site;
+  const double *rate;
+  double *budget;
+  int *err;
+  int debug_flags;
+};
+
+// The march of one CTA over its column: TMA staging, psi ring, collision,
+// push.  out_pop(i) returns the base of population i of the output lattice.
+template <int LAT, int ST, int BX, int BY, int NS, class OutPop>
+__device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) {
   using K = FusedK<LAT, ST, BX, BY, NS>;
   using L = typename K::L;
   using S = typename K::S;
@@ -88,13 +107,9 @@ __global__ void __launch_bounds__(BX *BY)
 
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
-  const int item = blockIdx.x;
-  const int ntiles = tiles_x * tiles_y;
-  const int zc = item / ntiles, tt = item % ntiles;
-  const int NX = (int)a.NX, NY = (int)a.NY, NZ = (int)a.NZ;
-  const int x0 = (tt % tiles_x) * BX, y0 = (tt / tiles_x) * BY;
+  const int NX = m.NX, NY = m.NY, NZ = m.NZ;
+  const int x0 = m.x0, y0 = m.y0, zs = m.zs, ze = m.ze;
   const int BXe = min(BX, NX - x0), BYe = min(BY, NY - y0);
-  const int zs = zc * zlen, ze = min(NZ, zs + zlen);
   if (zs >= ze) return;
   const int NPL = ze - zs + 2;  // staged planes zs-1 .. ze
   const bool active = tx < BXe && ty < BYe;
@@ -104,58 +119,53 @@ __global__ void __launch_bounds__(BX *BY)
   const int yt = y0 == 0 ? NY - 1 : y0 - 1;
   const int yb = y0 + BYe == NY ? 0 : y0 + BYe;
 
-  const int64_t plane = a.px * a.NY;
-  const int64_t popstride = plane * a.NZ;
-  T *fout = static_cast<T *>(a.fout);
+  const int64_t plane = m.px * NY;
 
   // constants in the arithmetic type (FP32 kernels execute no FP64 at all)
-  const C G = F64 ? (C)a.G : (C)a.G_f, tau = F64 ? (C)a.tau : (C)a.tau_f,
-          omega = F64 ? (C)(1.0 / a.tau) : (C)a.omega_f, rho0 = F64 ? (C)a.rho0 : (C)a.rho0_f,
-          inv_rho0 = F64 ? (C)(1.0 / a.rho0) : (C)a.inv_rho0_f;
+  const C G = F64 ? (C)m.G : (C)m.G_f, tau = F64 ? (C)m.tau : (C)m.tau_f,
+          omega = F64 ? (C)(1.0 / m.tau) : (C)m.omega_f, rho0 = F64 ? (C)m.rho0 : (C)m.rho0_f,
+          inv_rho0 = F64 ? (C)(1.0 / m.rho0) : (C)m.inv_rho0_f;
   // offset storage: the staged values are g_i = f_i - w_i rho_ref
-  const C rho_ref = S::OFFSET ? (C)a.rho_ref_f : (C)0;
+  const C rho_ref = S::OFFSET ? (C)m.rho_ref_f : (C)0;
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
     fence_proxy_async_smem();
-    prefetch_tmap(&tm.main);
-    prefetch_tmap(&tm.col);
+    prefetch_tmap(&m.tm->main);
+    prefetch_tmap(&m.tm->col);
     if (HY) {
-      prefetch_tmap(&tm.row);
-      prefetch_tmap(&tm.crn);
+      prefetch_tmap(&m.tm->row);
+      prefetch_tmap(&m.tm->crn);
     }
   }
   __syncthreads();
 
   auto issue = [&](int k) {
-    if ((a.debug_flags & 1) && k == 1) return;  // test hook: let the wait expire
+    if ((m.debug_flags & 1) && k == 1) return;  // test hook: let the wait expire
     const int P = zs - 1 + k, s = k % NS;
     const int zp = P < 0 ? P + NZ : (P >= NZ ? P - NZ : P);
     uint8_t *st = smem + s * K::STAGE_BYTES;
     mbar_arrive_expect_tx(&bars[s], (uint32_t)K::TX_BYTES);
-    tma_load_4d(st, &tm.main, x0, y0, zp, 0, &bars[s]);
-    tma_load_4d(st + K::OFF_L, &tm.col, xl, y0, zp, 0, &bars[s]);
-    tma_load_4d(st + K::OFF_R, &tm.col, xr, y0, zp, 0, &bars[s]);
+    tma_load_4d(st, &m.tm->main, x0, y0, zp, 0, &bars[s]);
+    tma_load_4d(st + K::OFF_L, &m.tm->col, xl, y0, zp, 0, &bars[s]);
+    tma_load_4d(st + K::OFF_R, &m.tm->col, xr, y0, zp, 0, &bars[s]);
     if (HY) {
-      tma_load_4d(st + K::OFF_T, &tm.row, x0, yt, zp, 0, &bars[s]);
-      tma_load_4d(st + K::OFF_B, &tm.row, x0, yb, zp, 0, &bars[s]);
-      tma_load_4d(st + K::OFF_TL, &tm.crn, xl, yt, zp, 0, &bars[s]);
-      tma_load_4d(st + K::OFF_TR, &tm.crn, xr, yt, zp, 0, &bars[s]);
-      tma_load_4d(st + K::OFF_BL, &tm.crn, xl, yb, zp, 0, &bars[s]);
-      tma_load_4d(st + K::OFF_BR, &tm.crn, xr, yb, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_T, &m.tm->row, x0, yt, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_B, &m.tm->row, x0, yb, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_TL, &m.tm->crn, xl, yt, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_TR, &m.tm->crn, xr, yt, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_BL, &m.tm->crn, xl, yb, zp, 0, &bars[s]);
+      tma_load_4d(st + K::OFF_BR, &m.tm->crn, xr, yb, zp, 0, &bars[s]);
     }
   };
   if (tid == 0) {
     for (int k = 0; k < NS && k < NPL; ++k) issue(k);
   }
 
-  int sp = 0, send = 0;  // this CTA's injection sites, sorted by z
-  if (a.nsites > 0) {
-    sp = a.bucket_off[item];
-    send = a.bucket_off[item + 1];
-  }
-  int next_z = sp < send ? a.site_z[a.bucket_site[sp]] : INT_MAX;  // plane of the next site
+  int sp = m.sp;  // this CTA's injection sites [sp, send), sorted by z
+  const int send = m.send;
+  int next_z = sp < send ? m.site_z[m.bucket_site[sp]] : INT_MAX;  // plane of the next site
 
   // destination coordinates of the push, fixed per thread (periodic)
   const int x = x0 + tx, y = y0 + ty;
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(BX *BY)
 
   // 32-bit offsets of the push destinations inside a population block
   const int32_t ox[3] = {xm, x, xp};
-  const int32_t oy[3] = {(int32_t)(ym * a.px), (int32_t)(y * a.px), (int32_t)(yp * a.px)};
+  const int32_t oy[3] = {(int32_t)(ym * m.px), (int32_t)(y * m.px), (int32_t)(yp * m.px)};
 
   C cur[Q], nxt[Q];
 #pragma unroll
@@ -250,7 +260,7 @@ __global__ void __launch_bounds__(BX *BY)
 
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
-        atomicOr(a.err, ERR_TMA_TIMEOUT);
+        if (m.err) atomicOr(m.err, ERR_TMA_TIMEOUT);
         // wait (bounded) for copies still in flight into this CTA's stages
         for (int k2 = k + 1; k2 < NPL && k2 < k + NS; ++k2)
           mbar_wait_bounded(&bars[k2 % NS], (uint32_t)((k2 / NS) & 1), 100000000ull);
@@ -266,19 +276,19 @@ __global__ void __launch_bounds__(BX *BY)
       bool site = false;
       if (Pc == next_z) {  // sites of this CTA in this plane (rare)
         for (; sp < send; ++sp) {
-          const int sidx = a.bucket_site[sp];
-          if (a.site_z[sidx] != Pc) break;
-          if (active && a.site_x[sidx] == x && a.site_y[sidx] == y) {
-            const double b = a.budget[sidx];
+          const int sidx = m.bucket_site[sp];
+          if (m.site_z[sidx] != Pc) break;
+          if (active && m.site_x[sidx] == x && m.site_y[sidx] == y) {
+            const double b = m.budget[sidx];
             if (b > 0.0) {
-              const double d = fmin(a.rate[sidx], b);
-              a.budget[sidx] = b - d;
+              const double d = fmin(m.rate[sidx], b);
+              m.budget[sidx] = b - d;
               dm += d;
               site = true;
             }
           }
         }
-        next_z = sp < send ? a.site_z[a.bucket_site[sp]] : INT_MAX;
+        next_z = sp < send ? m.site_z[m.bucket_site[sp]] : INT_MAX;
       }
       if (active) {
         const C *pm = ring + ((k - 2) & 3) * PW * PH;
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(BX *BY)
         const int zm = Pc == 0 ? NZ - 1 : Pc - 1, zp = Pc + 1 >= NZ ? 0 : Pc + 1;
         const int32_t oz[3] = {(int32_t)(zm * plane), (int32_t)(Pc * plane), (int32_t)(zp * plane)};
         auto dst = [&](int i) -> T * {
-          return static_cast<T *>(a.out_pop[i]) + (oz[L::cz(i) + 1] + oy[L::cy(i) + 1] + ox[L::cx(i) + 1]);
+          return out_pop(i) + (oz[L::cz(i) + 1] + oy[L::cy(i) + 1] + ox[L::cx(i) + 1]);
         };
         auto psi_at = [&](int i) -> C {
           const C *pl = L::cz(i) < 0 ? pm : (L::cz(i) > 0 ? pp : p0);
@@ -378,6 +388,47 @@ __global__ void __launch_bounds__(BX *BY)
 #pragma unroll
     for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
   }
+}
+
+template <int LAT, int ST, int BX, int BY, int NS>
+__global__ void __launch_bounds__(BX *BY)
+    fused_step_kernel(const __grid_constant__ FusedMaps tm, const StepArgs a, const int tiles_x,
+                      const int tiles_y, const int zlen) {
+  using T = typename Storage<ST>::T;
+  const int item = blockIdx.x;
+  const int ntiles = tiles_x * tiles_y;
+  const int zc = item / ntiles, tt = item % ntiles;
+  MarchArgs m;
+  m.NX = (int)a.NX;
+  m.NY = (int)a.NY;
+  m.NZ = (int)a.NZ;
+  m.px = a.px;
+  m.tau = a.tau;
+  m.G = a.G;
+  m.rho0 = a.rho0;
+  m.tau_f = a.tau_f;
+  m.omega_f = a.omega_f;
+  m.G_f = a.G_f;
+  m.rho0_f = a.rho0_f;
+  m.inv_rho0_f = a.inv_rho0_f;
+  m.rho_ref_f = a.rho_ref_f;
+  m.tm = &tm;
+  m.x0 = (tt % tiles_x) * BX;
+  m.y0 = (tt / tiles_x) * BY;
+  m.zs = zc * zlen;
+  m.ze = min(m.NZ, m.zs + zlen);
+  m.nsites = a.nsites;
+  m.sp = a.nsites > 0 ? a.bucket_off[item] : 0;
+  m.send = a.nsites > 0 ? a.bucket_off[item + 1] : 0;
+  m.site_x = a.site_x;
+  m.site_y = a.site_y;
+  m.site_z = a.site_z;
+  m.bucket_site = a.bucket_site;
+  m.rate = a.rate;
+  m.budget = a.budget;
+  m.err = a.err;
+  m.debug_flags = a.debug_flags;
+  fused_march<LAT, ST, BX, BY, NS>(m, [&](int i) { return static_cast<T *>(a.out_pop[i]); });
 }
 
 template <int LAT, int ST, int BX, int BY, int NS>

@@ -66,6 +66,14 @@ class Rupture(C.Structure):
                 ("h_c", C.c_double), ("r_d", C.c_double)]
 
 
+class Domain(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("tau", C.c_double), ("G", C.c_double),
+                ("rho0", C.c_double), ("rho_ref", C.c_double), ("rho_l", C.c_double),
+                ("rho_g", C.c_double), ("width", C.c_double), ("noise_amp", C.c_double),
+                ("seed", C.c_uint64), ("nbubbles", C.c_int32), ("bubbles", Bubble * 4),
+                ("line", C.c_int64 * 5), ("rho_mid", C.c_double)]
+
+
 class LBMError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -97,12 +105,18 @@ def _load():
         "lbm_label_gas": (i32, [P_, P_, C.POINTER(i64)]),
         "lbm_diagnose": (i32, [P_, P_, P_, C.POINTER(i64)]),
         "lbm_film_probe": (i32, [P_, P_, d, C.POINTER(Film)]),
-        "lbm_run_until_rupture": (i32, [P_, P_, d, d, i64, i64, C.POINTER(Rupture)]),
+        "lbm_run_until_rupture": (i32, [P_, P_, d, d, d, i64, i64, C.POINTER(Rupture)]),
         "lbm_site_labels": (i32, [P_, P_, i32, C.POINTER(i64)]),
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
         "lbm_write_f": (i32, [P_, P_, sz]),
         "lbm_step_static_f32": (i32, [i32, i64, i64, i64, d, d, d, P_, P_, P_]),
+        "lbm_ensemble_create": (i32, [P_, i32, d, d, i32, ALLOC_FN, FREE_FN, P_, C.POINTER(P_)]),
+        "lbm_ensemble_destroy": (None, [P_]),
+        "lbm_ensemble_run": (i32, [P_, i64, C.POINTER(i64)]),
+        "lbm_ensemble_results": (i32, [P_, P_, i32]),
+        "lbm_ensemble_stats": (i32, [P_, P_]),
+        "lbm_ensemble_read_f": (i32, [P_, i32, P_, sz]),
         "lbm_last_error": (C.c_char_p, []),
         "lbm_version": (C.c_char_p, []),
     }
@@ -123,7 +137,8 @@ EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites"
            "lbm_run_until_rupture",
            "lbm_site_labels",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_last_error",
-           "lbm_version")
+           "lbm_version", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_run",
+           "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f")
 
 
 def lib():
@@ -323,13 +338,14 @@ class Lattice:
         return dict(found=bool(out.found), x1=out.x1, x2=out.x2, h=out.h, d2p_mid=out.d2p_mid,
                     r_d=out.r_d)
 
-    def run_until_rupture(self, line, rho_mid, eps_arm, diag_every, max_steps):
+    def run_until_rupture(self, line, rho_mid, eps_arm, diag_every, max_steps, h_max=8.0):
         """Rupture criterion (lbm_run_until_rupture): dict(fired, merged, steps,
         h_c, r_d)."""
         ln = np.ascontiguousarray(line, dtype=np.int64)
         out = Rupture()
         _check(_lib.lbm_run_until_rupture(self._h, _ptr(ln), float(rho_mid), float(eps_arm),
-                                          int(diag_every), int(max_steps), C.byref(out)))
+                                          float(h_max), int(diag_every), int(max_steps),
+                                          C.byref(out)))
         return dict(fired=bool(out.fired), merged=bool(out.merged), steps=int(out.steps),
                     h_c=out.h_c, r_d=out.r_d)
 
@@ -361,3 +377,74 @@ def step_static_f32(lattice, nx, ny, nz, tau, G, rho0, f_in_ptr, f_out_ptr, stre
     lat = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
     _check(_lib.lbm_step_static_f32(lat, nx, ny, nz, tau, G, rho0, C.c_void_p(f_in_ptr),
                                     C.c_void_p(f_out_ptr), C.c_void_p(stream) if stream else None))
+
+
+class Ensemble:
+    """Batched two-bubble D2Q9 domains with the on-device rupture criterion
+    (lbm_ensemble_* in include/lbm.h).  domains: list of dicts with the
+    lbm_domain fields (bubbles as (x, y, 0, r) rows, line as 5 ints)."""
+
+    def __init__(self, domains, eps_arm=1e-3, diag_every=20, torch_memory=True, h_max=8.0):
+        n = len(domains)
+        arr = (Domain * n)()
+        for k, dm in enumerate(domains):
+            a = arr[k]
+            for f in ("nx", "ny", "seed", "nbubbles"):
+                setattr(a, f, int(dm[f]) if f != "nbubbles" else len(dm["bubbles"]))
+            a.nbubbles = len(dm["bubbles"])
+            for f in ("tau", "G", "rho0", "rho_ref", "rho_l", "rho_g", "width", "noise_amp",
+                      "rho_mid"):
+                setattr(a, f, float(dm[f]))
+            for j, bb in enumerate(dm["bubbles"]):
+                a.bubbles[j] = Bubble(*[float(v) for v in bb])
+            for j, v in enumerate(dm["line"]):
+                a.line[j] = int(v)
+        self._mem = None
+        alloc, free = ALLOC_FN(), FREE_FN()
+        if torch_memory:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    self._mem = _TorchMemory()
+                    alloc, free = self._mem.alloc, self._mem.free
+            except ImportError:
+                pass
+        self.n = n
+        self.shapes = [(int(dm["ny"]), int(dm["nx"])) for dm in domains]
+        h = C.c_void_p()
+        _check(_lib.lbm_ensemble_create(C.cast(arr, C.c_void_p), n, float(eps_arm), float(h_max),
+                                        int(diag_every), alloc, free, None, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lbm_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, max_steps):
+        done = C.c_int64(0)
+        _check(_lib.lbm_ensemble_run(self._h, int(max_steps), C.byref(done)))
+        return int(done.value)
+
+    def results(self):
+        out = (Rupture * self.n)()
+        _check(_lib.lbm_ensemble_results(self._h, C.cast(out, C.c_void_p), self.n))
+        return [dict(fired=bool(r.fired), merged=bool(r.merged), steps=int(r.steps), h_c=r.h_c,
+                     r_d=r.r_d) for r in out]
+
+    def stats(self):
+        out = np.zeros(4)
+        _check(_lib.lbm_ensemble_stats(self._h, _ptr(out)))
+        return dict(steps=int(out[0]), updates=out[1], active=int(out[2]), launches=int(out[3]))
+
+    def read_f(self, d):
+        ny, nx = self.shapes[d]
+        out = np.empty((9, 1, ny, nx))
+        _check(_lib.lbm_ensemble_read_f(self._h, int(d), _ptr(out), out.nbytes))
+        return out

@@ -39,4 +39,43 @@ FOAM_768 = dict(
     sites=dict(n=4096, r_min=3.0, r_max=3.0, min_spacing=12.0, min_gap=0.0),
     rate=5e-5, budget=(20.0, 80.0), steps=50000, diag_every=100, rho_ref=2.0, threshold=1.0)
 
-WORKLOADS = {w["name"]: w for w in (TWO_DISKS_128, FOAM_128, FOAM_512, FOAM_768)}
+# 256 independent two-bubble D2Q9 domains (FP32): side log-uniform 64..512
+# (rounded to multiples of 8), gap U(2, 10), radius U(8, min(60, (L - 2 gap)/4
+# - 2)) so that the gap around the periodic wrap is no smaller, tau U(0.6,
+# 1.0), G = -5; run until the rupture criterion fires or 20000 steps
+ENSEMBLE_256 = dict(
+    name="d2q9_ensemble_256", n=256, side=(64, 512), gap=(2.0, 10.0), radius=(8.0, 60.0),
+    tau=(0.6, 1.0), G=-5.0, rho0=1.0, rho_ref=2.0, rho_l=2.0, rho_g=0.15, width=2.0,
+    noise=1e-3, seed=3, steps=20000, diag_every=20, eps_arm=1e-3, h_max=8.0)
+
+WORKLOADS = {w["name"]: w for w in (TWO_DISKS_128, FOAM_128, FOAM_512, FOAM_768, ENSEMBLE_256)}
+
+
+def ensemble_domains(recipe=ENSEMBLE_256, n=None, side=None):
+    """Draw the domain list of an ensemble recipe (numpy generator seeded with
+    recipe['seed']): dicts with the fields of lbm_domain.  Two gas disks of
+    radius R sit on the middle row at a surface-to-surface distance `gap`;
+    the film probe line runs from one centre to the other."""
+    import numpy as np
+    rng = np.random.default_rng(recipe["seed"])
+    n = recipe["n"] if n is None else n
+    lo, hi = recipe["side"] if side is None else side
+    out = []
+    for k in range(n):
+        L = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))) / 8.0)) * 8
+        gap = float(rng.uniform(*recipe["gap"]))
+        rmax = min(recipe["radius"][1], (L - 2 * gap) / 4 - 2)
+        R = float(rng.uniform(recipe["radius"][0], max(recipe["radius"][0], rmax)))
+        tau = float(rng.uniform(*recipe["tau"]))
+        yc = L // 2
+        c1 = L / 2 - R - gap / 2
+        c2 = L / 2 + R + gap / 2
+        x0 = int(np.floor(c1))
+        out.append(dict(
+            nx=L, ny=L, tau=tau, G=recipe["G"], rho0=recipe["rho0"], rho_ref=recipe["rho_ref"],
+            rho_l=recipe["rho_l"], rho_g=recipe["rho_g"], width=recipe["width"],
+            noise_amp=recipe["noise"], seed=recipe["seed"] * 100003 + k,
+            bubbles=[(c1, float(yc), 0.0, R), (c2, float(yc), 0.0, R)],
+            line=(x0, yc, 0, 0, int(np.ceil(c2)) - x0 + 1),
+            rho_mid=0.5 * (recipe["rho_l"] + recipe["rho_g"]), R=R, gap=gap))
+    return out
