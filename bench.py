@@ -327,6 +327,55 @@ def run_ours(args, world, rank, local):
     L.close()
 
 
+def run_ensemble(args):
+    """The batched two-bubble sweep (256 uneven D2Q9 domains) run until every
+    criterion fired or 20000 steps; MLUPS over all domain updates."""
+    import torch
+    from paper_1708_01608_gb300 import build_lib
+    from paper_1708_01608_gb300 import workloads as WL
+    build_lib.build()
+    from paper_1708_01608_gb300 import lbm
+    torch.cuda.set_device(0)
+    R = WL.ENSEMBLE_256
+    doms = WL.ensemble_domains(R)
+    E = lbm.Ensemble(doms, eps_arm=R["eps_arm"], diag_every=R["diag_every"], h_max=R["h_max"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E.run(R["steps"])
+    dt = time.perf_counter() - t0
+    st = E.stats()
+    res = E.results()
+    fired = [(d["R"], r["h_c"], r["r_d"], r["steps"]) for d, r in zip(doms, res) if r["fired"]]
+    line = {"metric": "batched D2Q9 ensemble MLUPS (256 two-bubble domains, run to the rupture "
+                      "criterion or 20000 steps)",
+            "value": st["updates"] / dt / 1e6, "unit": UNIT, "n_gpus": 1, "steps": st["steps"],
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": R["name"], "domains": len(doms),
+                       "cells": int(sum(d["nx"] * d["ny"] for d in doms)),
+                       "diag_every": R["diag_every"], "eps_arm": R["eps_arm"], "h_max": R["h_max"]},
+            "seconds": dt, "updates": st["updates"], "launches": st["launches"],
+            "fired": len(fired), "merged": sum(r["merged"] for r in res),
+            "h_c_vs_R": [[round(a, 2), round(b, 3), round(c, 1), s] for a, b, c, s in fired]}
+    E.close()
+    if args.single:
+        upd, t_single = 0.0, 0.0
+        for dm in doms:
+            L = lbm.Lattice("D2Q9", dm["nx"], dm["ny"], 1, tau=dm["tau"], G=dm["G"],
+                            storage="f32", rho_ref=dm["rho_ref"], kernel="fused")
+            L.seed_bubbles(np.array(dm["bubbles"]), dm["rho_l"], dm["rho_g"], dm["width"],
+                           dm["noise_amp"], dm["seed"])
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            r = L.run_until_rupture(dm["line"], dm["rho_mid"], R["eps_arm"], R["diag_every"],
+                                    R["steps"], R["h_max"])
+            t_single += time.perf_counter() - t1
+            upd += dm["nx"] * dm["ny"] * r["steps"]
+            L.close()
+        line["single_domain_mlups"] = upd / t_single / 1e6
+        line["single_domain_seconds"] = t_single
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(args):
     import torch
     from paper_1708_01608_gb300 import build_lib
@@ -360,6 +409,14 @@ def main():
                     help="no timing: build the workload lattice, run this many steps, exit "
                          "(a short fixed case for ncu captures)")
     ap.add_argument("--tile", type=int, default=0, help="fused tile id for --profile-steps")
+    ap.add_argument("--workload", default="foam128",
+                    choices=["foam128", "foam512", "ensemble256"],
+                    help="foam128: the default benchmark line; foam512: the 512^3 foam "
+                         "(FP32 or --storage f16/bf16); ensemble256: the batched two-bubble "
+                         "sweep run to completion")
+    ap.add_argument("--storage", default=None, choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--single", action="store_true",
+                    help="ensemble256: also run every domain alone, one after the other")
     args = ap.parse_args()
     if args.profile_steps > 0:
         run_profile_case(args)
@@ -367,6 +424,20 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup(args.gpus)
+    if args.workload != "foam128":
+        global W, METRIC, INNER, CELLS, B_ALG
+        from paper_1708_01608_gb300 import workloads as WL
+        if args.workload == "ensemble256":
+            run_ensemble(args)
+            return
+        W = dict(WL.FOAM_512)
+        METRIC = "D3Q19 Shan-Chen MLUPS (512^3 foam, 1000 bubbles, diagnostics every 100 steps)"
+        INNER = 100
+        CELLS = W["nx"] * W["ny"] * W["nz"]
+        args.no_cpu_baseline = True
+    if args.storage:
+        W = dict(W, storage=args.storage)
+    B_ALG = 2 * Q * {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[W["storage"]]
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)

@@ -245,9 +245,18 @@ void efree_all(lbm_ensemble *E) {
   E->bufs.clear();
 }
 
-// work items of the active domains of each class; rows are cut into chunks
-// of about 16k cells so that items are of similar size across domains
-lbm_status build_items(lbm_ensemble *E, bool upload_only_counts) {
+// Work items of the active domains of each class.  Rows are cut into chunks
+// of ENS_ZLEN: a CTA marches its chunk row by row, so the chunk length sets
+// the latency of a step, and short chunks give many independent items.
+constexpr int ENS_ZLEN = 16;
+
+int chunk_len(int ny) {
+  int zlen = std::min(ny, ENS_ZLEN);
+  const int nzc = (ny + zlen - 1) / zlen;
+  return (ny + nzc - 1) / nzc;
+}
+
+lbm_status build_items(lbm_ensemble *E, int counts[NCLASS]) {
   for (int c = 0; c < NCLASS; ++c) {
     std::vector<int4> it;
     for (int d = 0; d < E->n; ++d) {
@@ -255,17 +264,14 @@ lbm_status build_items(lbm_ensemble *E, bool upload_only_counts) {
       const int bx = CLASS_BX[c];
       const int nx = E->hdom[d].NX, ny = E->hdom[d].NZ;
       const int tiles_x = (nx + bx - 1) / bx;
-      int zlen = std::max(8, std::min(ny, 16384 / bx));
+      const int zlen = chunk_len(ny);
       const int nzc = (ny + zlen - 1) / zlen;
-      zlen = (ny + nzc - 1) / nzc;
       for (int zc = 0; zc < nzc; ++zc)
         for (int tx = 0; tx < tiles_x; ++tx)
           it.push_back(make_int4(d, tx * bx, zc * zlen, std::min(ny, (zc + 1) * zlen)));
     }
     const int cnt = (int)it.size();
-    if (!upload_only_counts) {
-      if (cnt > E->max_items[c]) return efail(LBM_ESTATE, "ensemble: work list grew");
-    }
+    counts[c] = cnt;
     if (cnt > 0)
       ECK(cudaMemcpyAsync(E->d_items[c], it.data(), sizeof(int4) * cnt, cudaMemcpyHostToDevice, E->s));
     ECK(cudaMemcpyAsync(E->d_count[c], &cnt, sizeof(int), cudaMemcpyHostToDevice, E->s));
@@ -277,9 +283,8 @@ lbm_status build_items(lbm_ensemble *E, bool upload_only_counts) {
 int count_items(const lbm_ensemble *E, int d, int c) {
   const int bx = CLASS_BX[c];
   const int nx = E->hdom[d].NX, ny = E->hdom[d].NZ;
-  int zlen = std::max(8, std::min(ny, 16384 / bx));
-  const int nzc = (ny + zlen - 1) / zlen;
-  return ((nx + bx - 1) / bx) * nzc;
+  const int zlen = chunk_len(ny);
+  return ((nx + bx - 1) / bx) * ((ny + zlen - 1) / zlen);
 }
 
 void drop_graph(lbm_ensemble *E) {
@@ -507,13 +512,9 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
       return bail(efail(LBM_ECUDA, "ensemble: initial state failed"));
     }
   }
-  for (int c = 0; c < NCLASS; ++c) {
-    int cnt = 0;
-    for (int d = 0; d < n; ++d)
-      if (E->cls[d] == c) cnt += count_items(E, d, c);
-    E->max_items[c] = cnt;
-  }
-  if ((st = build_items(E, false)) != LBM_OK) return bail(st);
+  int counts[NCLASS];
+  if ((st = build_items(E, counts)) != LBM_OK) return bail(st);
+  for (int c = 0; c < NCLASS; ++c) E->max_items[c] = counts[c];
   *out = E;
   return LBM_OK;
 }
@@ -526,6 +527,22 @@ void lbm_ensemble_destroy(lbm_ensemble *E) {
   if (E->s) cudaStreamDestroy(E->s);
   cudaGetLastError();
   delete E;
+}
+
+// After the active set changed: new work lists; the captured grids (one
+// CTA per item) are re-captured when a class emptied or shrank by half, so
+// that finished domains stop costing launches.
+static lbm_status refresh_work(lbm_ensemble *E) {
+  int counts[NCLASS];
+  ECKS(build_items(E, counts));
+  bool regrid = false;
+  for (int c = 0; c < NCLASS; ++c)
+    regrid |= (counts[c] == 0) != (E->max_items[c] == 0) || 2 * counts[c] < E->max_items[c];
+  if (regrid) {
+    drop_graph(E);
+    for (int c = 0; c < NCLASS; ++c) E->max_items[c] = counts[c];
+  }
+  return LBM_OK;
 }
 
 lbm_status lbm_ensemble_run(lbm_ensemble *E, int64_t max_steps, int64_t *steps_done) {
@@ -541,7 +558,7 @@ lbm_status lbm_ensemble_run(lbm_ensemble *E, int64_t max_steps, int64_t *steps_d
     ECKS(ens_interval(E));
     bool changed = false;
     for (int d = 0; d < E->n; ++d) changed |= before[d] != E->hstate[d].active;
-    if (changed) ECKS(build_items(E, false));
+    if (changed) ECKS(refresh_work(E));
   }
   if (steps_done) *steps_done = E->steps - start;
   return LBM_OK;
