@@ -232,14 +232,19 @@ lbm_status lbm_film_probe(lbm_ctx *ctx, const int64_t *line, double rho_mid, lbm
  * way), so the criterion applies to a thin film, h <= h_max: it is armed
  * once the midpoint value has been below -eps_arm, disarmed whenever the
  * film is thicker than h_max, and fires at the first probe of a thin film
- * where it is >= 0.  Stops when it fires (fired = 1, h_c = h and r_d of that
- * probe), when a probe finds no film (merged = 1: the bubbles joined before
- * the criterion), or after max_steps.  out->steps = steps taken by this
- * call.  Synchronous. */
+ * where it is >= 0.  Stops when it fires, when a probe finds no film
+ * (merged = 1: the bubbles joined before the criterion), or after
+ * max_steps.  On firing: fired = 1; h_c = the film thickness where
+ * d2p/dn2 crosses zero, interpolated linearly in d2p between the previous
+ * probe (d2p < 0) and the firing probe (d2p >= 0):
+ *   h_c = h_prev + (h - h_prev) * (-d_prev) / (d - d_prev),
+ * which removes the dependence on diag_every (the film thins by ~0.01
+ * cells per step near rupture); h_probe and r_d are those of the firing
+ * probe.  out->steps = steps taken by this call.  Synchronous. */
 typedef struct {
   int32_t fired, merged;
   int64_t steps;
-  double h_c, r_d;
+  double h_c, h_probe, r_d;
 } lbm_rupture;
 lbm_status lbm_run_until_rupture(lbm_ctx *ctx, const int64_t *line, double rho_mid,
                                   double eps_arm, double h_max, int64_t diag_every,
@@ -317,7 +322,8 @@ void lbm_ensemble_destroy(lbm_ensemble *ens);
 lbm_status lbm_ensemble_run(lbm_ensemble *ens, int64_t max_steps, int64_t *steps_done);
 
 /* Per domain: fired / merged flags, the step at which it stopped (or the
- * steps so far), h_c and r_d at firing. */
+ * steps so far), h_c (interpolated zero crossing), h_probe and r_d at
+ * firing, as lbm_run_until_rupture. */
 lbm_status lbm_ensemble_results(const lbm_ensemble *ens, lbm_rupture *out, int32_t n);
 
 /* out = {steps taken, lattice updates performed (sum over domains of cells x

@@ -225,16 +225,41 @@ def film_probe(lat, rho, p, start, axis, length, rho_mid):
     return dict(found=bool(out[0]), x1=out[1], x2=out[2], h=out[3], d2p_mid=out[4], r_d=out[5])
 
 
+def criterion_step(state, probe, eps_arm, h_max):
+    """One probe of the rupture criterion of Sec. 3.1 / Sec. 4.  state is
+    None at the start; probe = dict(found, h, d2p_mid, r_d) as film_probe.
+    The criterion concerns a thin film (h <= h_max): it is armed once the
+    film-midpoint d2p/dn2 has been below -eps_arm, disarmed whenever the film
+    is thicker than h_max, and fires at the first probe of a thin film where
+    d2p/dn2 >= 0.  A probe that finds no film is a merge before the
+    criterion.  On firing, h_c is the thickness at the zero of d2p/dn2 on
+    the straight line through the last two probes' (h, d2p) points (the
+    previous probe had d2p < 0: otherwise the criterion would have fired or
+    been disarmed there); h_probe and r_d are the firing probe's.
+    Returns (state, outcome) with outcome None while the run goes on."""
+    armed, last = (False, None) if state is None else state
+    if not probe["found"]:
+        return (armed, last), dict(fired=False, merged=True, h_c=0.0, h_probe=0.0, r_d=0.0)
+    h, d = probe["h"], probe["d2p_mid"]
+    if h > h_max:
+        armed = False
+    elif d < -eps_arm:
+        armed = True
+    elif armed and d >= 0.0:
+        h0, d0 = last
+        h_c = h0 + (h - h0) * (-d0 / (d - d0))
+        return (armed, last), dict(fired=True, merged=False, h_c=h_c, h_probe=h,
+                                   r_d=probe["r_d"])
+    return (armed, (h, d)), None
+
+
 def run_until_rupture(lat, f, tau, G, start, axis, length, rho_mid, eps_arm, max_steps,
                       diag_every, rho0=1.0, h_max=8.0):
-    """The rupture criterion of Sec. 3.1 / Sec. 4 as a plain loop: advance f,
-    probe the film every diag_every steps.  The criterion concerns a thin
-    film (h <= h_max): it is armed once the film-midpoint d2p/dn2 has been
-    below -eps_arm, disarmed whenever the film is thicker than h_max, and
-    fires at the first probe of a thin film where d2p/dn2 >= 0.  A probe
-    that finds no film ends the run as a merge before the criterion.
-    Returns dict(fired, merged, step, h_c, r_d, f)."""
-    armed = False
+    """The rupture criterion as a plain loop: advance f by diag_every steps,
+    probe the film (film_probe on the FP64 density and pressure) and apply
+    criterion_step, until it fires, the film is gone or max_steps.
+    Returns dict(fired, merged, step, h_c, h_probe, r_d, f)."""
+    state = None
     t = 0
     while t < max_steps:
         f = run(lat, f, diag_every, tau, G, rho0)
@@ -242,12 +267,7 @@ def run_until_rupture(lat, f, tau, G, start, axis, length, rho_mid, eps_arm, max
         rho = moments(lat, f)[0]
         _, p = eos(rho, G, rho0)
         pr = film_probe(lat, rho, p, start, axis, length, rho_mid)
-        if not pr["found"]:
-            return dict(fired=False, merged=True, step=t, h_c=0.0, r_d=0.0, f=f)
-        if pr["h"] > h_max:
-            armed = False
-        elif pr["d2p_mid"] < -eps_arm:
-            armed = True
-        elif armed and pr["d2p_mid"] >= 0.0:
-            return dict(fired=True, merged=False, step=t, h_c=pr["h"], r_d=pr["r_d"], f=f)
-    return dict(fired=False, merged=False, step=t, h_c=0.0, r_d=0.0, f=f)
+        state, out = criterion_step(state, pr, eps_arm, h_max)
+        if out is not None:
+            return dict(step=t, f=f, **out)
+    return dict(fired=False, merged=False, step=t, h_c=0.0, h_probe=0.0, r_d=0.0, f=f)

@@ -772,6 +772,7 @@ lbm_status lbm_run_until_rupture(lbm_ctx *c, const int64_t *line, double rho_mid
     return fail(LBM_EINVAL, "diag_every >= 1, max_steps >= 0, eps_arm >= 0, h_max > 0");
   std::memset(out, 0, sizeof(*out));
   bool armed = false;
+  double h_prev = 0.0, d_prev = 0.0;  // previous probe (d_prev < 0 whenever armed)
   int64_t t = 0;
   while (t < max_steps) {
     const int64_t n = std::min(diag_every, max_steps - t);
@@ -790,10 +791,13 @@ lbm_status lbm_run_until_rupture(lbm_ctx *c, const int64_t *line, double rho_mid
       armed = true;
     } else if (armed && pr.d2p_mid >= 0.0) {
       out->fired = 1;
-      out->h_c = pr.h;
+      out->h_c = h_prev + (pr.h - h_prev) * (-d_prev / (pr.d2p_mid - d_prev));
+      out->h_probe = pr.h;
       out->r_d = pr.r_d;
       return LBM_OK;
     }
+    h_prev = pr.h;
+    d_prev = pr.d2p_mid;
   }
   return LBM_OK;
 }

@@ -39,7 +39,7 @@ struct EnsDomain {
 struct EnsState {
   int32_t active, armed, fired, merged;
   int64_t step;
-  double h_c, r_d, last_d2p, last_h;
+  double h_c, h_probe, r_d, last_d2p, last_h;
 };
 
 // D2Q9 tile classes of the ensemble (the fused tile table's D2Q9 ids)
@@ -123,18 +123,20 @@ __global__ void k_ens_probe(const EnsDomain *doms, EnsState *st, int n, int pari
     s.merged = 1;
     s.active = 0;
   } else {
-    s.last_h = out[3];
-    s.last_d2p = out[4];
     if (out[3] > h_max) {
       s.armed = 0;  // thick film: the criterion does not apply
     } else if (out[4] < -eps_arm) {
       s.armed = 1;
     } else if (s.armed && out[4] >= 0.0) {
+      // zero crossing of d2p between the previous probe (d2p < 0) and this one
       s.fired = 1;
       s.active = 0;
-      s.h_c = out[3];
+      s.h_c = s.last_h + (out[3] - s.last_h) * (-s.last_d2p / (out[4] - s.last_d2p));
+      s.h_probe = out[3];
       s.r_d = out[5];
     }
+    s.last_h = out[3];
+    s.last_d2p = out[4];
   }
   st[d] = s;
 }
@@ -573,6 +575,7 @@ lbm_status lbm_ensemble_results(const lbm_ensemble *E, lbm_rupture *out, int32_t
     out[d].merged = s.merged;
     out[d].steps = s.active ? E->steps : s.step;
     out[d].h_c = s.h_c;
+    out[d].h_probe = s.h_probe;
     out[d].r_d = s.r_d;
   }
   return LBM_OK;

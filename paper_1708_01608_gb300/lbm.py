@@ -63,7 +63,7 @@ class Film(C.Structure):
 
 class Rupture(C.Structure):
     _fields_ = [("fired", C.c_int32), ("merged", C.c_int32), ("steps", C.c_int64),
-                ("h_c", C.c_double), ("r_d", C.c_double)]
+                ("h_c", C.c_double), ("h_probe", C.c_double), ("r_d", C.c_double)]
 
 
 class Domain(C.Structure):
@@ -340,14 +340,14 @@ class Lattice:
 
     def run_until_rupture(self, line, rho_mid, eps_arm, diag_every, max_steps, h_max=8.0):
         """Rupture criterion (lbm_run_until_rupture): dict(fired, merged, steps,
-        h_c, r_d)."""
+        h_c, h_probe, r_d); h_c is the interpolated zero crossing of d2p."""
         ln = np.ascontiguousarray(line, dtype=np.int64)
         out = Rupture()
         _check(_lib.lbm_run_until_rupture(self._h, _ptr(ln), float(rho_mid), float(eps_arm),
                                           float(h_max), int(diag_every), int(max_steps),
                                           C.byref(out)))
         return dict(fired=bool(out.fired), merged=bool(out.merged), steps=int(out.steps),
-                    h_c=out.h_c, r_d=out.r_d)
+                    h_c=out.h_c, h_probe=out.h_probe, r_d=out.r_d)
 
     def diagnose(self, want_labels=False):
         """One diagnostic interval: (totals[4], labels or None, components)."""
@@ -436,7 +436,7 @@ class Ensemble:
         out = (Rupture * self.n)()
         _check(_lib.lbm_ensemble_results(self._h, C.cast(out, C.c_void_p), self.n))
         return [dict(fired=bool(r.fired), merged=bool(r.merged), steps=int(r.steps), h_c=r.h_c,
-                     r_d=r.r_d) for r in out]
+                     h_probe=r.h_probe, r_d=r.r_d) for r in out]
 
     def stats(self):
         out = np.zeros(4)

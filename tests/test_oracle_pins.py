@@ -483,3 +483,47 @@ def test_film_probe_midpoint_tie_averages():
     p2[0, 0, 11] = 1.0
     r2 = O.film_probe(O.D2Q9, rho, p2, (0, 0, 0), 0, 30, 1.1)
     assert abs(r2["d2p_mid"] - 0.5 * (-2.0 + 1.0)) < 1e-15
+
+
+def _run_criterion(probes, eps_arm=1e-3, h_max=8.0):
+    state = None
+    for k, pr in enumerate(probes):
+        state, out = O.criterion_step(state, pr, eps_arm, h_max)
+        if out is not None:
+            return k, out
+    return None, None
+
+
+def _pr(h, d, r_d=4.5, found=True):
+    return dict(found=found, h=h, d2p_mid=d, r_d=r_d)
+
+
+def test_criterion_zero_crossing_of_a_linear_film():
+    """A film thinning at a constant rate with d2p/dn2 = a (h* - h): the
+    interpolated zero crossing is h* exactly (to rounding), whatever the
+    probe spacing; h_probe is the first probe past it."""
+    for dh in (0.05, 0.13, 0.4):
+        hs = 6.0 - dh * np.arange(int(5.0 / dh))
+        probes = [_pr(h, 0.02 * (2.37 - h)) for h in hs]
+        k, out = _run_criterion(probes)
+        assert out["fired"] and not out["merged"]
+        assert hs[k] <= 2.37 < hs[k - 1]
+        assert abs(out["h_c"] - 2.37) < 1e-12 and out["h_probe"] == hs[k]
+
+
+def test_criterion_arming_disarming_and_merge():
+    # never below -eps_arm: never armed, never fires
+    k, out = _run_criterion([_pr(5.0, -5e-4), _pr(4.0, 1e-3), _pr(3.0, 2e-3)])
+    assert out is None
+    # armed, then the film thickens past h_max: disarmed, a later d >= 0 does not fire
+    k, out = _run_criterion([_pr(6.0, -2e-3), _pr(9.0, 0.0), _pr(7.0, 1e-3)])
+    assert out is None
+    # armed by a thin film, fires at the first d >= 0; d = 0 exactly counts
+    k, out = _run_criterion([_pr(12.0, 1.0), _pr(6.0, -2e-3), _pr(5.0, -1e-3), _pr(4.0, 0.0)])
+    assert k == 3 and out["fired"] and out["h_c"] == 4.0
+    # a probe without film ends the run as a merge, armed or not
+    k, out = _run_criterion([_pr(6.0, -2e-3), _pr(0.0, 0.0, found=False)])
+    assert k == 1 and out["merged"] and not out["fired"]
+    # a film thicker than h_max with d >= 0 after arming does not fire
+    k, out = _run_criterion([_pr(7.9, -2e-3), _pr(8.1, 5e-3), _pr(7.0, -5e-4), _pr(6.0, 1e-3)])
+    assert out is None
