@@ -28,14 +28,21 @@ LIB = os.path.join(HERE, "_build", "libsc_oracle.so")
 D2Q9, D3Q19 = 0, 1
 
 
+# A prebuilt variant of the library (the mutation tests load deliberately
+# broken copies of sc_oracle.c through this variable).
+_LIB_OVERRIDE = os.environ.get("SC_ORACLE_LIB")
+
+GCC_FLAGS = ["-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-ffp-contract=off"]
+
+
 def build(force: bool = False) -> str:
     """Compile sc_oracle.c into _build/libsc_oracle.so (gcc, OpenMP)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         os.makedirs(os.path.dirname(LIB), exist_ok=True)
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
-             "-ffp-contract=off", "-o", tmp, SRC, "-lm"])
+        subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 

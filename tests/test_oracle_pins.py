@@ -468,6 +468,23 @@ def test_film_probe_constructed_slab_and_parabola():
     assert not r2["found"]
 
 
+def test_film_probe_disc_radius_of_a_wedge():
+    """A film whose liquid run widens by one cell per row away from the
+    centre row: rows with run <= h + 2 form the disc, so R_d = 5/2."""
+    nx, ny = 48, 30
+    rho = np.full((1, ny, nx), 2.0)
+    rg, mid = 0.2, 1.1
+    for y in range(ny):
+        gap = 6 + abs(y - 15)
+        a_end = 24 - gap // 2
+        rho[0, y, 4:a_end] = rg
+        rho[0, y, a_end + gap:44] = rg
+    p = np.zeros((1, ny, nx))
+    r = O.film_probe(O.D2Q9, rho, p, (8, 15, 0), 0, 30, mid)
+    assert r["found"] and abs(r["h"] - 6.0) < 1e-12
+    assert r["r_d"] == 2.5
+
+
 def test_film_probe_midpoint_tie_averages():
     nx = 32
     rho = np.full((1, 1, nx), 2.0)
