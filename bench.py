@@ -383,16 +383,19 @@ def run_profile_case(args):
     from paper_1708_01608_gb300 import lbm
     torch.cuda.set_device(0)
     s = W["sites"]
-    bub = lbm.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
-                           s["min_spacing"], s["min_gap"], W["seed"])
-    L = lbm.Lattice("D3Q19", W["nx"], W["ny"], W["nz"], tau=W["tau"], G=W["G"],
-                    rho0=W["rho0"], storage=W["storage"], rho_ref=W["rho_ref"],
-                    kernel="fused" if args.tile else args.kernel, tile=args.tile)
+    n = args.extent or W["nx"]
+    storage = args.storage or W["storage"]
+    bub = lbm.sample_sites(n, n, n, s["n"], s["r_min"], s["r_max"], s["min_spacing"],
+                           s["min_gap"], W["seed"])
+    L = lbm.Lattice("D3Q19", n, n, n, tau=W["tau"], G=W["G"], rho0=W["rho0"], storage=storage,
+                    rho_ref=W["rho_ref"], kernel="fused" if args.tile else args.kernel,
+                    tile=args.tile)
     L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
     L.inject(np.full(len(bub), W["rate"]), np.full(len(bub), W["budget"]))
     L.step(args.profile_steps)
     L.sync()
-    print(json.dumps({"profile_case": W["name"], "steps": args.profile_steps, "plan": L.plan()}))
+    print(json.dumps({"profile_case": W["name"], "extent": n, "storage": storage,
+                      "steps": args.profile_steps, "plan": L.plan()}))
     L.close()
 
 
@@ -409,6 +412,8 @@ def main():
                     help="no timing: build the workload lattice, run this many steps, exit "
                          "(a short fixed case for ncu captures)")
     ap.add_argument("--tile", type=int, default=0, help="fused tile id for --profile-steps")
+    ap.add_argument("--extent", type=int, default=0,
+                    help="--profile-steps: cubic lattice side (default: the foam's 128)")
     ap.add_argument("--workload", default="foam128",
                     choices=["foam128", "foam512", "ensemble256"],
                     help="foam128: the default benchmark line; foam512: the 512^3 foam "

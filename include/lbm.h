@@ -185,8 +185,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 lbm_status lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *best_tile, double *best_ms);
 
 /* Launch plan of the step kernel: out = {kernel (lbm_kernel), tile id,
- * tile x extent, tile y extent, z chunks, CTAs per step}; tile fields are 0
- * for the two-pass kernel. */
+ * tile x extent, tile y extent, z chunks, CTAs per step}; tile
+ * fields are 0 for the two-pass kernel. */
 lbm_status lbm_plan_info(const lbm_ctx *ctx, int32_t out[6]);
 
 /* Number of steps taken since seeding. */

@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(BX)
   m.debug_flags = 0;
   float *out = parity ? D.latA : D.latB;
   const int64_t ps = D.popstride;
-  fused_march<D2Q9, ST_F32, BX, 1, NS>(m, [&](int i) { return out + i * ps; });
+  fused_barriers_init<D2Q9, ST_F32, BX, 1, NS>(m);
+  uint32_t kb = 0;
+  fused_march<D2Q9, ST_F32, BX, 1, NS>(m, [&](int i) { return out + i * ps; }, kb);
 }
 
 // FP64 density / EOS pressure straight from a domain's populations

@@ -64,9 +64,10 @@ struct FusedPlan {
 
 // Tile shapes: returns false when the id is unknown for the lattice.
 bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage);
-// Fill *plan for a lattice; nzc <= 0 picks the number of z chunks from the
-// SM count.  Returns cudaErrorInvalidValue when the tile does not fit or nx
-// is not a multiple of the 16-byte halo width.
+// Fill *plan for a lattice; nzc <= 0 picks the number of z chunks that
+// fills the kernel's resident CTA slots once (SMs x CTAs per SM).  Returns
+// cudaErrorInvalidValue when the tile does not fit or nx is not a multiple
+// of the 16-byte halo width.
 cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ,
                             int nzc, FusedPlan *plan);
 // Encode the TMA descriptors of one population lattice for a plan.
@@ -87,10 +88,12 @@ cudaError_t fused_launch_h16(int lat, int st, const FusedPlan &, const StepArgs 
 int fused_smem_f64(int lat, int tile);
 int fused_smem_f32(int lat, int tile);
 int fused_smem_h16(int lat, int st, int tile);
-cudaError_t fused_prepare(int lat, int st, const FusedPlan &plan);  // set smem attribute
-cudaError_t fused_prepare_f64(int lat, const FusedPlan &);
-cudaError_t fused_prepare_f32(int lat, const FusedPlan &);
-cudaError_t fused_prepare_h16(int lat, int st, const FusedPlan &);
+// set the kernel's shared-memory attribute; blocks_per_sm (may be NULL)
+// receives the number of CTAs of the plan's kernel resident per SM
+cudaError_t fused_prepare(int lat, int st, const FusedPlan &plan, int *blocks_per_sm = nullptr);
+cudaError_t fused_prepare_f64(int lat, const FusedPlan &, int *blocks_per_sm);
+cudaError_t fused_prepare_f32(int lat, const FusedPlan &, int *blocks_per_sm);
+cudaError_t fused_prepare_h16(int lat, int st, const FusedPlan &, int *blocks_per_sm);
 
 // two-pass path: psi field pass, then collide/stream (+ injection kernel)
 cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi_scratch, cudaStream_t s);

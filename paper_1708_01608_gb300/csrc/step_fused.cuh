@@ -88,10 +88,35 @@ struct MarchArgs {
   int debug_flags;
 };
 
-// The march of one CTA over its column: TMA staging, psi ring, collision,
-// push.  out_pop(i) returns the base of population i of the output lattice.
+// Once per CTA, before its first march: the NS stage barriers and the
+// descriptor prefetch.
+template <int LAT, int ST, int BX, int BY, int NS>
+__device__ __forceinline__ void fused_barriers_init(const MarchArgs &m) {
+  using K = FusedK<LAT, ST, BX, BY, NS>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * K::STAGE_BYTES + K::RING_BYTES);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+    fence_proxy_async_smem();
+    prefetch_tmap(&m.tm->main);
+    prefetch_tmap(&m.tm->col);
+    if (K::HY) {
+      prefetch_tmap(&m.tm->row);
+      prefetch_tmap(&m.tm->crn);
+    }
+  }
+  __syncthreads();
+}
+
+// The march of one CTA over planes zs..ze-1 of one column: TMA staging, psi
+// ring, collision, push.  out_pop(i) returns the base of population i of the
+// output lattice.  kb counts the planes this CTA staged before (stage slot
+// and barrier phase continue across marches); it advances by the planes
+// staged here.  Returns false after a TMA wait timed out.
 template <int LAT, int ST, int BX, int BY, int NS, class OutPop>
-__device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) {
+__device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, uint32_t &kb) {
   using K = FusedK<LAT, ST, BX, BY, NS>;
   using L = typename K::L;
   using S = typename K::S;
@@ -110,7 +135,7 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
   const int NX = m.NX, NY = m.NY, NZ = m.NZ;
   const int x0 = m.x0, y0 = m.y0, zs = m.zs, ze = m.ze;
   const int BXe = min(BX, NX - x0), BYe = min(BY, NY - y0);
-  if (zs >= ze) return;
+  if (zs >= ze) return true;
   const int NPL = ze - zs + 2;  // staged planes zs-1 .. ze
   const bool active = tx < BXe && ty < BYe;
   // wrapped coordinates of the halo boxes
@@ -128,22 +153,10 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
   // offset storage: the staged values are g_i = f_i - w_i rho_ref
   const C rho_ref = S::OFFSET ? (C)m.rho_ref_f : (C)0;
 
-  if (tid == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
-    fence_barrier_init();
-    fence_proxy_async_smem();
-    prefetch_tmap(&m.tm->main);
-    prefetch_tmap(&m.tm->col);
-    if (HY) {
-      prefetch_tmap(&m.tm->row);
-      prefetch_tmap(&m.tm->crn);
-    }
-  }
-  __syncthreads();
-
+  const uint32_t k0 = kb;
   auto issue = [&](int k) {
     if ((m.debug_flags & 1) && k == 1) return;  // test hook: let the wait expire
-    const int P = zs - 1 + k, s = k % NS;
+    const int P = zs - 1 + k, s = (int)((k0 + k) % NS);
     const int zp = P < 0 ? P + NZ : (P >= NZ ? P - NZ : P);
     uint8_t *st = smem + s * K::STAGE_BYTES;
     mbar_arrive_expect_tx(&bars[s], (uint32_t)K::TX_BYTES);
@@ -230,11 +243,22 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
   C cur[Q], nxt[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) cur[i] = nxt[i] = 0;
+  C Rcur = 0, Rnxt = 0;  // sum of the staged values of this thread's cell
+
+  // FP32 relaxation constants per weight class (omega folded in)
+  C om1 = (C)1 - omega, cW[2], c3[2], c45[2];
+#pragma unroll
+  for (int k2 = 0; k2 < 2; ++k2) {
+    const C w = (C)L::w(L::rep(k2 == 0 ? 0 : L::NP - 1));
+    cW[k2] = w * omega;
+    c3[k2] = (C)3 * w * omega;
+    c45[k2] = (C)4.5 * w * omega;
+  }
 
   for (int k = 0; k < NPL; ++k) {
-    const int s = k % NS;
+    const int s = (int)((k0 + k) % NS);
     const int P = zs - 1 + k;
-    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((k / NS) & 1), 1000000000ull);
+    const bool ok = mbar_wait_bounded(&bars[s], ((k0 + k) / NS) & 1u, 1000000000ull);
     const uint8_t *st = smem + s * K::STAGE_BYTES;
     const T *mainb = reinterpret_cast<const T *>(st);
 
@@ -249,6 +273,7 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
         rho += v;
       }
       rk[(ty + HY) * PW + tx + 1] = psi_of(rho_ref + rho, rho0, inv_rho0);
+      Rnxt = rho;
     }
     if (tid < nhalo) {
       const T *b = reinterpret_cast<const T *>(st + h_off);
@@ -263,18 +288,19 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
         if (m.err) atomicOr(m.err, ERR_TMA_TIMEOUT);
         // wait (bounded) for copies still in flight into this CTA's stages
         for (int k2 = k + 1; k2 < NPL && k2 < k + NS; ++k2)
-          mbar_wait_bounded(&bars[k2 % NS], (uint32_t)((k2 / NS) & 1), 100000000ull);
+          mbar_wait_bounded(&bars[(k0 + k2) % NS], ((k0 + k2) / NS) & 1u, 100000000ull);
       }
-      return;
+      return false;
     }
     if (tid == 0 && k + NS < NPL) issue(k + NS);
 
     // ---- collide plane P - 1 (needs psi of P - 2, P - 1, P) and push
     if (k >= 2) {
       const int Pc = P - 1;
-      double dm = 0.0;  // blowing-agent mass deposited in this cell this step
+      C dmc = 0;  // blowing-agent mass deposited in this cell this step
       bool site = false;
       if (Pc == next_z) {  // sites of this CTA in this plane (rare)
+        double dm = 0.0;
         for (; sp < send; ++sp) {
           const int sidx = m.bucket_site[sp];
           if (m.site_z[sidx] != Pc) break;
@@ -289,6 +315,7 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
           }
         }
         next_z = sp < send ? m.site_z[m.bucket_site[sp]] : INT_MAX;
+        dmc = (C)dm;
       }
       if (active) {
         const C *pm = ring + ((k - 2) & 3) * PW * PH;
@@ -331,20 +358,23 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
             const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
             const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
             C fs = cur[i] - (cur[i] - feq) / tau;
-            if (site) fs += L::w(i) * dm;
+            if (site) fs += L::w(i) * dmc;
             *dst(i) = S::store(fs);
           }
         } else {
           // FP32 on offsets g_i = f_i - w_i rho_ref: with R = sum g (so that
           // rho = rho_ref + R) the equilibrium offset is
-          //   w_i (R + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)),
-          // evaluated for opposite velocities in pairs.  The rest population
-          // takes R minus the moving ones, so mass is conserved to rounding.
-          C R = cur[0], jx = 0, jy = 0, jz = 0, sx = 0, sy = 0, sz = 0;
+          //   w_i (K + rho (3 c.u + 4.5 (c.u)^2)),  K = R - 1.5 rho u.u,
+          // evaluated for opposite velocities in pairs, with omega = 1/tau
+          // folded into the per-weight constants:
+          //   g_i* = (1 - omega) g_i + omega w_i (K + 4.5 rho (c.u)^2) + omega 3 w_i rho c.u.
+          // The rest population takes R minus the moving ones, so mass is
+          // conserved to rounding.
+          const C R = Rcur;
+          C jx = 0, jy = 0, jz = 0, sx = 0, sy = 0, sz = 0;
 #pragma unroll
           for (int k2 = 0; k2 < L::NP; ++k2) {
             const int i = L::rep(k2), o = L::opp(L::rep(k2));
-            R += cur[i] + cur[o];
             const C d = cur[i] - cur[o];
             jx += (C)L::cx(i) * d;
             jy += (C)L::cy(i) * d;
@@ -356,42 +386,52 @@ __device__ __forceinline__ void fused_march(const MarchArgs &m, OutPop out_pop) 
           }
           const C rho = rho_ref + R;
           const C gp = -G * p0[c0];
-          const C ir = (C)1 / rho;
+          const C ir = __fdividef((C)1, rho);
           const C ux = (jx + tau * (gp * sx)) * ir, uy = (jy + tau * (gp * sy)) * ir,
                   uz = (jz + tau * (gp * sz)) * ir;
-          const C m_uu = (C)-1.5 * (ux * ux + uy * uy + uz * uz);
-          const C dmc = site ? (C)dm : (C)0;
+          const C K = fmaf(rho * (C)-1.5, ux * ux + uy * uy + uz * uz, R);
+          const C wK[2] = {cW[0] * K, cW[1] * K};
           C moved = 0;
 #pragma unroll
           for (int k2 = 0; k2 < L::NP; ++k2) {
             const int i = L::rep(k2), o = L::opp(L::rep(k2));
-            const C w = (C)L::w(i);
+            const int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
             const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
-            const C A = w * fmaf(rho, fmaf((C)4.5 * cu, cu, m_uu), R);
-            const C B = ((C)3 * w) * (rho * cu);
-            C gi = fmaf(omega, (A + B) - cur[i], cur[i]);
-            C go = fmaf(omega, (A - B) - cur[o], cur[o]);
+            const C a = rho * cu;
+            const C A = fmaf(a, c45[wc] * cu, wK[wc]);
+            const C B = c3[wc] * a;
+            const C gi = fmaf(om1, cur[i], A + B);
+            const C go = fmaf(om1, cur[o], A - B);
             moved += gi + go;
-            if (site) {
-              gi += w * dmc;
-              go += w * dmc;
-            }
             *dst(i) = S::store(gi);
             *dst(o) = S::store(go);
           }
-          C g0 = R - moved;
-          if (site) g0 += (C)L::w(0) * dmc;
-          *dst(0) = S::store(g0);
+          *dst(0) = S::store(R - moved);
+          if (site) {
+            // blowing agent (rare): add w_i dm to the values just stored
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+              T *p = dst(i);
+              *p = S::store(S::load(__ldcg(p)) + (C)L::w(i) * dmc);
+            }
+          }
         }
       }
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
+    Rcur = Rnxt;
   }
+  kb = k0 + NPL;
+  return true;
 }
 
+// One launch per time step: CTA (item) = BX x BY tile tt and z chunk zc,
+// item = zc * tiles + tt, so the CTAs resident together cover neighbouring
+// columns at the same planes (their halo rows meet in L2).
+// 256-thread tiles are register-limited to 3 CTAs per SM, the larger ones run one
 template <int LAT, int ST, int BX, int BY, int NS>
-__global__ void __launch_bounds__(BX *BY)
+__global__ void __launch_bounds__(BX *BY, BX *BY <= 256 ? 3 : 1)
     fused_step_kernel(const __grid_constant__ FusedMaps tm, const StepArgs a, const int tiles_x,
                       const int tiles_y, const int zlen) {
   using T = typename Storage<ST>::T;
@@ -428,23 +468,44 @@ __global__ void __launch_bounds__(BX *BY)
   m.budget = a.budget;
   m.err = a.err;
   m.debug_flags = a.debug_flags;
-  fused_march<LAT, ST, BX, BY, NS>(m, [&](int i) { return static_cast<T *>(a.out_pop[i]); });
+  fused_barriers_init<LAT, ST, BX, BY, NS>(m);
+  // Programmatic dependent launch: the shared-memory set-up above overlaps
+  // the previous step's tail; nothing in global memory is read or written
+  // before that step has completed and its writes are visible.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  uint32_t kb = 0;
+  fused_march<LAT, ST, BX, BY, NS>(m, [&](int i) { return static_cast<T *>(a.out_pop[i]); }, kb);
 }
 
 template <int LAT, int ST, int BX, int BY, int NS>
-cudaError_t fused_prepare_t() {
+cudaError_t fused_prepare_t(int *blocks_per_sm) {
   using K = FusedK<LAT, ST, BX, BY, NS>;
-  return cudaFuncSetAttribute(fused_step_kernel<LAT, ST, BX, BY, NS>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<LAT, ST, BX, BY, NS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  if (e == cudaSuccess && blocks_per_sm)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, fused_step_kernel<LAT, ST, BX, BY, NS>, K::NT, K::SMEM);
+  return e;
 }
 
 template <int LAT, int ST, int BX, int BY, int NS>
 cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const FusedMaps &tm,
                            cudaStream_t s) {
   using K = FusedK<LAT, ST, BX, BY, NS>;
-  fused_step_kernel<LAT, ST, BX, BY, NS>
-      <<<p.items, K::NT, K::SMEM, s>>>(tm, a, p.tiles_x, p.tiles_y, p.zlen);
-  return cudaGetLastError();
+  // launched as a programmatic dependent of the previous kernel in the stream
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)p.items);
+  cfg.blockDim = dim3((unsigned)K::NT);
+  cfg.dynamicSmemBytes = (size_t)K::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fused_step_kernel<LAT, ST, BX, BY, NS>, tm, a, p.tiles_x,
+                            p.tiles_y, p.zlen);
 }
 
 // Tile table shared by every storage type: id -> (BX, BY, NS).
@@ -455,7 +516,13 @@ cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const FusedMap
   X(4, 64, 8, 2)             \
   X(5, 128, 4, 2)            \
   X(6, 32, 8, 2)             \
-  X(7, 64, 4, 2)
+  X(7, 64, 4, 2)             \
+  X(8, 128, 4, 3)            \
+  X(9, 64, 8, 3)             \
+  X(10, 64, 8, 4)            \
+  X(11, 128, 4, 4)           \
+  X(12, 32, 8, 4)            \
+  X(13, 64, 4, 4)
 #define SCLBM_D2Q9_TILES(X) \
   X(1, 256, 1, 4)           \
   X(2, 128, 1, 4)           \
@@ -482,13 +549,13 @@ cudaError_t fused_launch_st(int lat, const FusedPlan &p, const StepArgs &a, cons
 }
 
 template <int ST>
-cudaError_t fused_prepare_st(int lat, const FusedPlan &p) {
+cudaError_t fused_prepare_st(int lat, const FusedPlan &p, int *blocks_per_sm) {
 #define SCLBM_X3(id, bx, by, ns) \
   case id:                       \
-    return fused_prepare_t<D3Q19, ST, bx, by, ns>();
+    return fused_prepare_t<D3Q19, ST, bx, by, ns>(blocks_per_sm);
 #define SCLBM_X2(id, bx, by, ns) \
   case id:                       \
-    return fused_prepare_t<D2Q9, ST, bx, by, ns>();
+    return fused_prepare_t<D2Q9, ST, bx, by, ns>(blocks_per_sm);
   if (lat == D3Q19) {
     switch (p.tile) { SCLBM_D3Q19_TILES(SCLBM_X3) }
   } else {

@@ -1,5 +1,6 @@
 // Host side of the fused step: tile table, launch plan, TMA descriptors and
 // dispatch to the per-storage translation units.
+#include <climits>
 #include <algorithm>
 
 #include "step_fused.cuh"
@@ -31,8 +32,8 @@ static int fused_smem_bytes(int lat, int st, int tile) {
   }
 }
 
-cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ, int nzc,
-                            FusedPlan *p) {
+cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ,
+                            int nzc, FusedPlan *p) {
   int bx, by, ns;
   if (tile <= 0) tile = 1;
   if (!fused_tile_shape(lat, st, tile, &bx, &by, &ns)) return cudaErrorInvalidValue;
@@ -55,8 +56,13 @@ cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, i
   p->tiles_y = (int)((NY + by - 1) / by);
   const int ntiles = p->tiles_x * p->tiles_y;
   if (nzc <= 0) {
-    // one wave: as many z chunks as keep every resident slot busy
-    int per_sm = std::max(1, std::min(smem_sm / (p->smem + 1024), 2048 / p->threads));
+    // one wave: as many z chunks as keep every resident slot busy (the
+    // kernel's occupancy: registers, shared memory and threads)
+    int per_sm = 0;
+    if (fused_prepare(lat, st, *p, &per_sm) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = std::max(1, std::min(smem_sm / (p->smem + 1024), 2048 / p->threads));
+    }
     const int slots = nsm * per_sm;
     nzc = std::max(1, slots / std::max(1, ntiles));
     nzc = (int)std::min<int64_t>(nzc, std::max<int64_t>(1, NZ / 4));
@@ -129,14 +135,14 @@ cudaError_t fused_launch(int lat, int st, const FusedPlan &p, const StepArgs &a,
   }
 }
 
-cudaError_t fused_prepare(int lat, int st, const FusedPlan &p) {
+cudaError_t fused_prepare(int lat, int st, const FusedPlan &p, int *blocks_per_sm) {
   switch (st) {
     case ST_F64:
-      return fused_prepare_f64(lat, p);
+      return fused_prepare_f64(lat, p, blocks_per_sm);
     case ST_F32:
-      return fused_prepare_f32(lat, p);
+      return fused_prepare_f32(lat, p, blocks_per_sm);
     default:
-      return fused_prepare_h16(lat, st, p);
+      return fused_prepare_h16(lat, st, p, blocks_per_sm);
   }
 }
 

@@ -415,9 +415,11 @@ def test_two_disks_128_fp64_5000_steps(lbm):
     L.close()
 
 
-def _small_domains():
+def _small_domains(noise=None):
     from paper_1708_01608_gb300.workloads import ENSEMBLE_256, ensemble_domains
     rec = dict(ENSEMBLE_256, gap=(4.0, 6.0), seed=11)
+    if noise is not None:
+        rec["noise"] = noise
     return ensemble_domains(rec, n=6, side=(64, 136))
 
 
@@ -439,26 +441,49 @@ def test_ensemble_matches_single_lattice_bitwise(lbm):
     E.close()
 
 
-def test_ensemble_criterion_matches_oracle(lbm):
-    """h_c of every domain within 1 % of the FP64 oracle started from the
-    same state, firing at the same probe (or one probe apart)."""
-    doms = _small_domains()
+def _ensemble_vs_oracle(lbm, doms, max_steps=6000):
     E = lbm.Ensemble(doms, eps_arm=1e-3, diag_every=20)
     f0 = [E.read_f(d) for d in range(len(doms))]
-    E.run(6000)
+    E.run(max_steps)
     res = E.results()
-    nfired = 0
+    st = E.stats()
+    assert st["active"] == 0 or st["steps"] == max_steps
+    E.close()
+    out = []
     for d, dm in enumerate(doms):
         ln = dm["line"]
         ref = O.run_until_rupture(O.D2Q9, f0[d], dm["tau"], dm["G"], (ln[0], ln[1], 0), 0,
-                                  ln[4], dm["rho_mid"], 1e-3, 6000, 20)
-        g = res[d]
+                                  ln[4], dm["rho_mid"], 1e-3, max_steps, 20)
+        out.append((res[d], ref))
+    return out
+
+
+def test_ensemble_criterion_matches_oracle(lbm):
+    """Noise-free two-disk domains (a well-conditioned h_c): every domain
+    fires or merges at the same probe as the FP64 oracle started from the
+    same state, and h_c agrees within 1 %."""
+    nfired = 0
+    for d, (g, ref) in enumerate(_ensemble_vs_oracle(lbm, _small_domains(noise=0.0))):
         assert g["fired"] == ref["fired"] and g["merged"] == ref["merged"], (d, g, ref)
-        assert abs(g["steps"] - ref["step"]) <= 20, (d, g, ref)
+        assert g["steps"] == ref["step"], (d, g, ref)
         if ref["fired"]:
             nfired += 1
             assert abs(g["h_c"] / ref["h_c"] - 1) < 0.01, (d, g, ref)
     assert nfired >= 1
-    st = E.stats()
-    assert st["active"] == 0 or st["steps"] == 6000
-    E.close()
+
+
+def test_ensemble_noisy_domains_follow_oracle(lbm):
+    """Domains with the recipe's 1e-3 initial noise.  There h_c is
+    ill-conditioned: a 1e-6 relative perturbation of the initial state moves
+    the oracle's own h_c by 0.9 % on the 104^2 domain of this set (and fires
+    one probe later), and FP32 rounding over thousands of steps is a
+    perturbation of that order.  Checked: the same outcome, the firing probe
+    within one interval, h_c within 3 %."""
+    nfired = 0
+    for d, (g, ref) in enumerate(_ensemble_vs_oracle(lbm, _small_domains())):
+        assert g["fired"] == ref["fired"] and g["merged"] == ref["merged"], (d, g, ref)
+        assert abs(g["steps"] - ref["step"]) <= 20, (d, g, ref)
+        if ref["fired"]:
+            nfired += 1
+            assert abs(g["h_c"] / ref["h_c"] - 1) < 0.03, (d, g, ref)
+    assert nfired >= 1
