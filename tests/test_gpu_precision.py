@@ -126,10 +126,7 @@ def test_density_field_error_3d(lbm):
     n = 64
     bub = np.array([[x, y, z, 5.0] for x in (16, 48) for y in (16, 48) for z in (16, 48)],
                    dtype=float)
-    L = lbm.Lattice("D3Q19", n, n, n, tau=0.8, G=-5.0, storage="f64")
-    L.seed_bubbles(bub, 2.0, 0.15, 2.0, 1e-3, 7)
-    f0 = L.read("f")
-    L.close()
+    f0, _ = O.init(O.D3Q19, n, n, n, bub, 2.0, 0.15, 2.0, 1e-3, 7)
     ref = O.moments(O.D3Q19, O.run(O.D3Q19, f0, 200, 0.8, -5.0))[0]
     rows = {}
     for st in FORMS:
@@ -149,10 +146,8 @@ def test_two_disk_h_c(lbm):
     interpolated h_c of the criterion, probes every 20 steps."""
     from paper_1708_01608_gb300.workloads import TWO_DISKS_128 as W
     line = (42, 64, 0, 0, 45)
-    L = lbm.Lattice("D2Q9", 128, 128, 1, tau=W["tau"], G=W["G"], storage="f64")
-    L.seed_bubbles(np.array(W["bubbles"]), W["rho_l"], W["rho_g"], W["width"], 0.0, W["seed"])
-    f0 = L.read("f")
-    L.close()
+    f0, _ = O.init(O.D2Q9, 128, 128, 1, np.array(W["bubbles"]), W["rho_l"], W["rho_g"],
+                   W["width"], 0.0, W["seed"])
     ref = O.run_until_rupture(O.D2Q9, f0, W["tau"], W["G"], line[:3], 0, line[4], 1.075, 1e-3,
                               5000, 20)
     assert ref["fired"]
