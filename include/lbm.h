@@ -271,6 +271,51 @@ lbm_status lbm_diagnose(lbm_ctx *ctx, double totals[4], int32_t *labels, int64_t
 lbm_status lbm_site_labels(lbm_ctx *ctx, int32_t *site_labels, int32_t n,
                            int64_t *merge_events);
 
+/* Bubble census (Sec. 4 counts bubbles and merging defects; Fig. 4 compares
+ * bubble areas): labels the gas of the current state as lbm_label_gas does
+ * (site labels and merge events included), then measures every component.
+ * roots[q] / sizes[q] (q < min(ncomp, cap); either array may be NULL) are
+ * the label (smallest linear cell index) and the size in cells of the
+ * components, in increasing order of the label; *ncomp (may be NULL) is the
+ * number of components; hist[b] (b < nbins, 1 <= nbins <= 63; may be NULL)
+ * counts components of size 2^b <= s < 2^(b+1), the last bin open-ended.
+ * Synchronous.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+lbm_status lbm_bubble_sizes(lbm_ctx *ctx, int64_t *roots, int64_t *sizes, int64_t cap,
+                            int64_t *ncomp, int64_t *hist, int32_t nbins);
+
+/* Film test at every lattice point (Sec. 4: the rupture criterion applied
+ * "at each lattice point" of a foam).  Labels the gas and computes the FP64
+ * EOS pressure of the current state, then for every liquid cell and every
+ * lattice axis a (0 = x, 1 = y, 2 = z in user coordinates): walking from the
+ * cell along +e_a and -e_a for at most h_max cells to the first gas cell
+ * (labels L+ and L-, distances d+ and d-), the cell lies in a film along a
+ * when both exist, L+ != L- and the liquid run t = d+ + d- - 1 <= h_max; it
+ * is a midpoint of that film when |d+ - d-| <= 1.  At a midpoint,
+ * d2p = p(x+e_a) - 2 p(x) + p(x-e_a) drives the two-bubble criterion per
+ * (cell, axis): armed when d2p < -eps_arm, fired when armed and d2p >= 0
+ * (arming cleared); a (cell, axis) that is not a film midpoint is disarmed.
+ * The arming state lives in the context (cleared by lbm_seed_bubbles and
+ * lbm_write_f) and carries over between calls.  out receives the counts;
+ * fired[q] (q < min(out->fired, cap); may be NULL) the fired (cell, axis)
+ * records in increasing (cell, axis) order.  When more than cap fire, which
+ * cap of them are returned is unspecified; the counts are exact.
+ * Synchronous.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+typedef struct {
+  int64_t film;      /* (cell, axis) pairs lying in a film */
+  int64_t midpoints; /* ... of them film midpoints */
+  int64_t armed;     /* (cell, axis) pairs armed after this call */
+  int64_t fired;     /* (cell, axis) pairs whose criterion fired in this call */
+} lbm_film_census;
+typedef struct {
+  int64_t cell;                   /* linear index x + nx (y + ny z) */
+  int32_t axis;                   /* 0, 1, 2 */
+  int32_t label_minus, label_plus; /* bubbles on the -axis and +axis sides */
+  int32_t thickness;              /* liquid cells between them */
+  double d2p;                     /* second difference of p along the axis */
+} lbm_film_cell;
+lbm_status lbm_film_cells(lbm_ctx *ctx, int32_t h_max, double eps_arm, lbm_film_census *out,
+                          lbm_film_cell *fired, int64_t cap);
+
 /* FP64 totals: out[0] = sum rho, out[1..3] = sum j over all cells, with a
  * fixed-order block reduction (repeated calls give identical bits).  FP64
  * storage sums every population in FP64; the FP32-arithmetic storages sum

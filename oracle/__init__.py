@@ -76,6 +76,10 @@ def _L():
         _lib.orc_totals.argtypes = [C.c_int, i64, i64, i64, P, P]
         _lib.orc_film_probe.argtypes = [C.c_int, i64, i64, i64, P, P, i64, i64, i64, C.c_int, i64,
                                         d, P]
+        _lib.orc_bubble_sizes.argtypes = [i64, P, i64, P, P]
+        _lib.orc_bubble_sizes.restype = i64
+        _lib.orc_size_histogram.argtypes = [i64, P, C.c_int, P]
+        _lib.orc_film_cells.argtypes = [C.c_int, i64, i64, i64, P, P, C.c_int, d, P, P, i64, P, P]
     return _lib
 
 
@@ -230,6 +234,46 @@ def film_probe(lat, rho, p, start, axis, length, rho_mid):
     _L().orc_film_probe(lat, nx, ny, nz, _p(rho), _p(p), int(start[0]), int(start[1]),
                         int(start[2]), int(axis), int(length), float(rho_mid), _p(out))
     return dict(found=bool(out[0]), x1=out[1], x2=out[2], h=out[3], d2p_mid=out[4], r_d=out[5])
+
+
+def bubble_sizes(labels):
+    """(roots, sizes) of the gas components of a label field (label_gas), in
+    increasing order of the root label (Sec. 4 bubble census)."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    n = _L().orc_bubble_sizes(lab.size, _p(lab), 0, None, None)
+    roots = np.zeros(max(n, 1), dtype=np.int64)
+    sizes = np.zeros(max(n, 1), dtype=np.int64)
+    _L().orc_bubble_sizes(lab.size, _p(lab), n, _p(roots), _p(sizes))
+    return roots[:n], sizes[:n]
+
+
+def size_histogram(sizes, nbins):
+    """Counts of sizes s with 2^b <= s < 2^(b+1), b = 0..nbins-1 (the last bin
+    open-ended)."""
+    sz = np.ascontiguousarray(sizes, dtype=np.int64)
+    hist = np.zeros(nbins, dtype=np.int64)
+    _L().orc_size_histogram(len(sz), _p(sz), nbins, _p(hist))
+    return hist
+
+
+def film_cells(lat, labels, p, h_max, eps_arm, state, cap=1 << 16):
+    """The per-lattice-point film test of Sec. 4 (see sc_oracle.c): updates
+    the uint8 arming state (shape of the lattice) in place and returns
+    (counts dict(film, midpoints, armed, fired), fired records (k, 5) int64
+    = cell, axis, label on the -axis side, label on the +axis side,
+    thickness; their d2 values)."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    p = _f64(p)
+    nz, ny, nx = lab.shape
+    assert state.dtype == np.uint8 and state.shape == lab.shape and state.flags.c_contiguous
+    counts = np.zeros(4, dtype=np.int64)
+    rec = np.zeros((cap, 5), dtype=np.int64)
+    d2 = np.zeros(cap)
+    _L().orc_film_cells(lat, nx, ny, nz, _p(lab), _p(p), int(h_max), float(eps_arm), _p(state),
+                        _p(counts), cap, _p(rec), _p(d2))
+    nf = int(min(counts[3], cap))
+    return (dict(film=int(counts[0]), midpoints=int(counts[1]), armed=int(counts[2]),
+                 fired=int(counts[3])), rec[:nf], d2[:nf])
 
 
 def criterion_step(state, probe, eps_arm, h_max):

@@ -597,3 +597,129 @@ void orc_film_probe(int lat, int64_t nx, int64_t ny, int64_t nz, const double *r
   out[4] = d2;
   out[5] = 0.5 * (double)extent;
 }
+
+/* ---- bubble census (Sec. 4: bubble sizes, merging defects) ----------------
+ * From gas labels (orc_label_gas: label = smallest linear index of the
+ * component, -1 liquid): the size in cells of every component, listed in
+ * increasing order of its label.  roots/sizes hold up to cap entries (either
+ * may be NULL); returns the number of components. */
+int64_t orc_bubble_sizes(int64_t N, const int32_t *label, int64_t cap, int64_t *roots,
+                         int64_t *sizes) {
+  int64_t *count = (int64_t *)calloc((size_t)(N > 0 ? N : 1), sizeof(int64_t));
+  for (int64_t k = 0; k < N; ++k)
+    if (label[k] >= 0) count[label[k]] += 1;
+  int64_t n = 0;
+  for (int64_t r = 0; r < N; ++r) {
+    if (count[r] == 0) continue;
+    if (n < cap) {
+      if (roots) roots[n] = r;
+      if (sizes) sizes[n] = count[r];
+    }
+    ++n;
+  }
+  free(count);
+  return n;
+}
+
+/* Histogram of component sizes in powers of two: bin b counts sizes s with
+ * 2^b <= s < 2^(b+1); the last bin also takes everything larger. */
+void orc_size_histogram(int64_t n, const int64_t *sizes, int nbins, int64_t *hist) {
+  for (int b = 0; b < nbins; ++b) hist[b] = 0;
+  for (int64_t q = 0; q < n; ++q) {
+    int b = 0;
+    while (b + 1 < nbins && ((int64_t)1 << (b + 1)) <= sizes[q]) ++b;
+    hist[b] += 1;
+  }
+}
+
+/* ---- the film test at every lattice point (Sec. 4) ------------------------
+ * Sec. 4 applies the rupture criterion "at each lattice point" of a foam.
+ * For every liquid cell (label -1) and every lattice axis a:
+ *   walk from the cell along +e_a for at most h_max cells to the first gas
+ *   cell (label L+, distance d+), and likewise along -e_a (L-, d-);
+ *   the cell lies in a film along a when both exist, L+ != L- (two different
+ *   bubbles) and the liquid run between them, t = d+ + d- - 1 cells, is at
+ *   most h_max;
+ *   it is a midpoint of that film when |d+ - d-| <= 1 (the middle cell of an
+ *   odd run, the two middle cells of an even one);
+ *   at a midpoint, d2 = p(x+e_a) - 2 p(x) + p(x-e_a) (FP64 EOS pressure) drives
+ *   the criterion of the two-bubble probe, per (cell, axis): it is armed when
+ *   d2 < -eps_arm, and fires when armed and d2 >= 0 (the arming is then
+ *   cleared).  A (cell, axis) that is not a film midpoint is disarmed.
+ * state[k] bit a holds the arming of (k, a) across calls.
+ * counts = {film (cell, axis) pairs, midpoints, armed after the update,
+ * fired}; the fired records, in increasing (cell, axis) order, fill up to
+ * cap entries of rec (cell, axis, L-, L+, t) and d2 (either may be NULL). */
+void orc_film_cells(int lat, int64_t nx, int64_t ny, int64_t nz, const int32_t *label,
+                    const double *p, int h_max, double eps_arm, uint8_t *state,
+                    int64_t *counts, int64_t cap, int64_t *rec, double *d2out) {
+  int dims = lat == ORC_D2Q9 ? 2 : 3;
+  int64_t N = nx * ny * nz;
+  int64_t nfilm = 0, nmid = 0, narmed = 0, nfired = 0;
+  for (int64_t k = 0; k < N; ++k) {
+    int64_t x = k % nx, y = (k / nx) % ny, z = k / (nx * ny);
+    for (int a = 0; a < dims; ++a) {
+      uint8_t bit = (uint8_t)(1u << a);
+      int film = 0, mid = 0;
+      int32_t Lp = -1, Lm = -1;
+      int dp = 0, dm = 0;
+      if (label[k] < 0) {
+        for (int s = 1; s <= h_max; ++s) {
+          int e[3] = {0, 0, 0};
+          e[a] = s;
+          int64_t m = nb(x, y, z, e[0], e[1], e[2], nx, ny, nz);
+          if (label[m] >= 0) {
+            Lp = label[m];
+            dp = s;
+            break;
+          }
+        }
+        for (int s = 1; s <= h_max; ++s) {
+          int e[3] = {0, 0, 0};
+          e[a] = -s;
+          int64_t m = nb(x, y, z, e[0], e[1], e[2], nx, ny, nz);
+          if (label[m] >= 0) {
+            Lm = label[m];
+            dm = s;
+            break;
+          }
+        }
+        film = Lp >= 0 && Lm >= 0 && Lp != Lm && dp + dm - 1 <= h_max;
+        mid = film && (dp - dm <= 1 && dm - dp <= 1);
+      }
+      if (film) ++nfilm;
+      if (!mid) {
+        state[k] = (uint8_t)(state[k] & ~bit);
+        continue;
+      }
+      ++nmid;
+      int e[3] = {0, 0, 0};
+      e[a] = 1;
+      double d2 = p[nb(x, y, z, e[0], e[1], e[2], nx, ny, nz)] - 2.0 * p[k] +
+                  p[nb(x, y, z, -e[0], -e[1], -e[2], nx, ny, nz)];
+      if (d2 < -eps_arm) {
+        state[k] = (uint8_t)(state[k] | bit);
+      } else if ((state[k] & bit) && d2 >= 0.0) {
+        state[k] = (uint8_t)(state[k] & ~bit);
+        if (nfired < cap) {
+          if (rec) {
+            int64_t *r = rec + 5 * nfired;
+            r[0] = k;
+            r[1] = a;
+            r[2] = Lm;
+            r[3] = Lp;
+            r[4] = dp + dm - 1;
+          }
+          if (d2out) d2out[nfired] = d2;
+        }
+        ++nfired;
+      }
+    }
+  }
+  for (int64_t k = 0; k < N; ++k)
+    for (int a = 0; a < dims; ++a) narmed += (state[k] >> a) & 1;
+  counts[0] = nfilm;
+  counts[1] = nmid;
+  counts[2] = narmed;
+  counts[3] = nfired;
+}

@@ -71,6 +71,9 @@ struct lbm_ctx {
   DevBuf psi_scratch;
   // diagnostics
   DevBuf d_err, d_rho, d_p, d_tmp, d_j, d_u, d_labels, d_ncomp, d_part, d_tot, d_site_lab;
+  // bubble census and per-point film test
+  DevBuf d_count, d_census, d_film_state, d_film_counts, d_film_rec;
+  bool film_state_clear = false;  // d_film_state must be zeroed before use
   std::vector<int32_t> site_labels, prev_site_labels;
   bool have_prev = false;
   int64_t merge_events = 0;
@@ -320,7 +323,9 @@ void lbm_destroy(lbm_ctx *c) {
   DevBuf *bufs[] = {&c->fA,     &c->fB,     &c->d_sx,    &c->d_sy,   &c->d_sz,     &c->d_rate,
                     &c->d_budget, &c->d_goff, &c->d_gsite, &c->d_boff, &c->d_blist, &c->d_cells, &c->d_bub,
                     &c->psi_scratch, &c->d_err, &c->d_rho, &c->d_p, &c->d_tmp, &c->d_j, &c->d_u,
-                    &c->d_labels, &c->d_ncomp, &c->d_part, &c->d_tot, &c->d_site_lab};
+                    &c->d_labels, &c->d_ncomp, &c->d_part, &c->d_tot, &c->d_site_lab,
+                    &c->d_count, &c->d_census, &c->d_film_state, &c->d_film_counts,
+                    &c->d_film_rec};
   for (DevBuf *b : bufs) dfree(c, *b);
   delete c;
 }
@@ -405,6 +410,7 @@ lbm_status lbm_seed_bubbles(lbm_ctx *c, const lbm_bubble *b, int32_t n, double r
   c->seeded = true;
   c->have_prev = false;
   c->merge_events = 0;
+  c->film_state_clear = false;
   c->site_labels.assign(n, -1);
   CK(cudaStreamSynchronize(c->s));  // host staging buffers go out of scope
   return LBM_OK;
@@ -835,6 +841,93 @@ lbm_status lbm_diagnose(lbm_ctx *c, double totals[4], int32_t *labels, int64_t *
   return LBM_OK;
 }
 
+lbm_status lbm_bubble_sizes(lbm_ctx *c, int64_t *roots, int64_t *sizes, int64_t cap,
+                            int64_t *ncomp, int64_t *hist, int32_t nbins) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (cap < 0 || nbins < 0 || nbins > 63 || (hist && nbins < 1))
+    return fail(LBM_EINVAL, "cap >= 0 and 1 <= nbins <= 63 when hist is given");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(enqueue_labels(c, false));
+  unsigned long long nc = 0;
+  CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
+  CKS(sync_and_check(c));
+  count_merges(c);
+  const int64_t n = (int64_t)nc;
+  const int nb = std::max(nbins, 1);
+  CKS(dalloc(c, c->d_count, sizeof(int32_t) * c->N));
+  // [n_dev][hist: 64][roots: n][sizes: n]
+  CKS(dalloc(c, c->d_census, sizeof(int64_t) * (65 + 2 * (size_t)std::max<int64_t>(n, 1))));
+  auto *base = static_cast<unsigned long long *>(c->d_census.p);
+  int64_t *d_roots = reinterpret_cast<int64_t *>(base + 65), *d_sizes = d_roots + std::max<int64_t>(n, 1);
+  CK(diag_bubble_sizes(c->v, static_cast<const int32_t *>(c->d_labels.p),
+                       static_cast<int32_t *>(c->d_count.p), base, n, d_roots, d_sizes, nb,
+                       base + 1, c->s));
+  std::vector<int64_t> r((size_t)n), sz((size_t)n);
+  std::vector<unsigned long long> h((size_t)nb), cnt(1);
+  CK(cudaMemcpyAsync(cnt.data(), base, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaMemcpyAsync(h.data(), base + 1, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, c->s));
+  if (n > 0) {
+    CK(cudaMemcpyAsync(r.data(), d_roots, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(sz.data(), d_sizes, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->s));
+  }
+  CKS(sync_and_check(c));
+  if ((int64_t)cnt[0] != n) return fail(LBM_ECUDA, "bubble census: component count mismatch");
+  // canonical order: increasing root label
+  std::vector<int64_t> order((size_t)n);
+  for (int64_t q = 0; q < n; ++q) order[q] = q;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return r[a] < r[b]; });
+  for (int64_t q = 0; q < std::min(n, cap); ++q) {
+    if (roots) roots[q] = r[order[q]];
+    if (sizes) sizes[q] = sz[order[q]];
+  }
+  if (ncomp) *ncomp = n;
+  if (hist)
+    for (int b = 0; b < nbins; ++b) hist[b] = (int64_t)h[b];
+  return LBM_OK;
+}
+
+lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_census *out,
+                          lbm_film_cell *fired, int64_t cap) {
+  if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+  if (h_max < 1 || h_max > 1024 || !(eps_arm >= 0) || cap < 0)
+    return fail(LBM_EINVAL, "1 <= h_max <= 1024, eps_arm >= 0, cap >= 0");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  CKS(enqueue_labels(c, false));
+  CKS(compute_pressure(c));
+  CKS(dalloc(c, c->d_film_state, (size_t)c->N));
+  if (!c->film_state_clear) {
+    CK(cudaMemsetAsync(c->d_film_state.p, 0, (size_t)c->N, c->s));
+    c->film_state_clear = true;
+  }
+  CKS(dalloc(c, c->d_film_counts, 4 * sizeof(unsigned long long)));
+  CKS(dalloc(c, c->d_film_rec, film_record_bytes() * (size_t)std::max<int64_t>(cap, 1)));
+  CK(diag_film_cells(c->v, static_cast<const int32_t *>(c->d_labels.p),
+                     static_cast<const double *>(c->d_p.p), h_max, eps_arm,
+                     static_cast<uint8_t *>(c->d_film_state.p),
+                     static_cast<unsigned long long *>(c->d_film_counts.p), cap, c->d_film_rec.p,
+                     c->s));
+  unsigned long long cnt[4];
+  CK(cudaMemcpyAsync(cnt, c->d_film_counts.p, sizeof(cnt), cudaMemcpyDeviceToHost, c->s));
+  CKS(sync_and_check(c));
+  count_merges(c);
+  out->film = (int64_t)cnt[0];
+  out->midpoints = (int64_t)cnt[1];
+  out->armed = (int64_t)cnt[2];
+  out->fired = (int64_t)cnt[3];
+  const int64_t nrec = std::min<int64_t>(out->fired, cap);
+  if (fired && nrec > 0) {
+    CK(cudaMemcpy(fired, c->d_film_rec.p, sizeof(lbm_film_cell) * nrec, cudaMemcpyDeviceToHost));
+    std::sort(fired, fired + nrec, [](const lbm_film_cell &a, const lbm_film_cell &b) {
+      return a.cell != b.cell ? a.cell < b.cell : a.axis < b.axis;
+    });
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_site_labels(lbm_ctx *c, int32_t *site_labels, int32_t n, int64_t *merge_events) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (site_labels) {
@@ -936,6 +1029,7 @@ lbm_status lbm_write_f(lbm_ctx *c, const double *src, size_t bytes) {
   }
   CK(cudaStreamSynchronize(c->s));
   c->seeded = true;
+  c->film_state_clear = false;
   return LBM_OK;
 }
 

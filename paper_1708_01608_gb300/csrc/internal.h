@@ -149,5 +149,18 @@ cudaError_t diag_film_probe(const View &v, const double *rho, const double *p, i
                             double mid, double *out, cudaStream_t s);
 cudaError_t diag_gather_labels(const int32_t *labels, const int32_t *cells, int32_t n,
                                int32_t *out, cudaStream_t s);
+// bubble census (census.cu): component sizes from labels (count_scratch: N
+// int32), unordered (root, size) entries up to cap, *n_dev = components,
+// hist[nbins] = log2 size histogram
+cudaError_t diag_bubble_sizes(const View &v, const int32_t *labels, int32_t *count_scratch,
+                              unsigned long long *n_dev, int64_t cap, int64_t *roots,
+                              int64_t *sizes, int nbins, unsigned long long *hist,
+                              cudaStream_t s);
+// film test at every lattice point (census.cu): counts[4] = {film, midpoints,
+// armed, fired}; fired records (film_record_bytes() each, unordered) up to cap
+size_t film_record_bytes();
+cudaError_t diag_film_cells(const View &v, const int32_t *labels, const double *p, int h_max,
+                            double eps_arm, uint8_t *state, unsigned long long *counts,
+                            int64_t cap, void *records, cudaStream_t s);
 
 }  // namespace sclbm

@@ -66,6 +66,17 @@ class Rupture(C.Structure):
                 ("h_c", C.c_double), ("h_probe", C.c_double), ("r_d", C.c_double)]
 
 
+class FilmCensus(C.Structure):
+    _fields_ = [("film", C.c_int64), ("midpoints", C.c_int64), ("armed", C.c_int64),
+                ("fired", C.c_int64)]
+
+
+# lbm_film_cell as a numpy record
+FILM_CELL = np.dtype([("cell", np.int64), ("axis", np.int32), ("label_minus", np.int32),
+                      ("label_plus", np.int32), ("thickness", np.int32), ("d2p", np.float64)],
+                     align=True)
+
+
 class Domain(C.Structure):
     _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("tau", C.c_double), ("G", C.c_double),
                 ("rho0", C.c_double), ("rho_ref", C.c_double), ("rho_l", C.c_double),
@@ -107,6 +118,8 @@ def _load():
         "lbm_film_probe": (i32, [P_, P_, d, C.POINTER(Film)]),
         "lbm_run_until_rupture": (i32, [P_, P_, d, d, d, i64, i64, C.POINTER(Rupture)]),
         "lbm_site_labels": (i32, [P_, P_, i32, C.POINTER(i64)]),
+        "lbm_bubble_sizes": (i32, [P_, P_, P_, i64, C.POINTER(i64), P_, i32]),
+        "lbm_film_cells": (i32, [P_, i32, d, C.POINTER(FilmCensus), P_, i64]),
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
         "lbm_write_f": (i32, [P_, P_, sz]),
@@ -135,7 +148,7 @@ EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites"
            "lbm_autotune", "lbm_plan_info",
            "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose", "lbm_film_probe",
            "lbm_run_until_rupture",
-           "lbm_site_labels",
+           "lbm_site_labels", "lbm_bubble_sizes", "lbm_film_cells",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_last_error",
            "lbm_version", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_run",
            "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f")
@@ -364,6 +377,28 @@ class Lattice:
         _check(_lib.lbm_site_labels(self._h, _ptr(out) if self.nsites else None, self.nsites,
                                     C.byref(ev)))
         return out, int(ev.value)
+
+    def bubble_sizes(self, nbins=32, cap=1 << 20):
+        """Label the gas and measure its components (lbm_bubble_sizes):
+        (roots, sizes) in increasing root order and the log2 size histogram."""
+        roots = np.zeros(max(cap, 1), dtype=np.int64)
+        sizes = np.zeros(max(cap, 1), dtype=np.int64)
+        hist = np.zeros(max(nbins, 1), dtype=np.int64)
+        nc = C.c_int64(0)
+        _check(_lib.lbm_bubble_sizes(self._h, _ptr(roots), _ptr(sizes), int(cap), C.byref(nc),
+                                     _ptr(hist), int(nbins)))
+        n = min(int(nc.value), cap)
+        return roots[:n], sizes[:n], hist[:nbins]
+
+    def film_cells(self, h_max=12, eps_arm=1e-3, cap=1 << 16):
+        """The film test at every lattice point (lbm_film_cells): (counts
+        dict, fired records as a FILM_CELL array in (cell, axis) order)."""
+        out = FilmCensus()
+        rec = np.zeros(max(cap, 1), dtype=FILM_CELL)
+        _check(_lib.lbm_film_cells(self._h, int(h_max), float(eps_arm), C.byref(out), _ptr(rec),
+                                   int(cap)))
+        return (dict(film=out.film, midpoints=out.midpoints, armed=out.armed, fired=out.fired),
+                rec[:min(out.fired, cap)])
 
     def totals(self):
         out = np.zeros(4)

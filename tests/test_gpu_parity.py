@@ -523,3 +523,83 @@ def test_ensemble_noisy_domains_follow_oracle(lbm):
             nfired += 1
             assert abs(g["h_c"] / ref["h_c"] - 1) < 0.03, (d, g, ref)
     assert nfired >= 1
+
+
+# ---------------------------------------------------------------- bubble census
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_bubble_sizes_match_oracle(lbm, storage):
+    """A seeded 48^3 foam state (16 bubbles r 4..9, 20 oracle steps, some of
+    them shrinking away) in the lattice's storage format: component roots,
+    sizes (7 to ~2400 cells) and the log2 histogram bit-exact."""
+    n = 48
+    got, bub = O.sample_sites(n, n, n, 16, 4.0, 9.0, 0.0, 2.0, 4)
+    assert got == 16
+    f0, _ = O.init(O.D3Q19, n, n, n, bub, 2.0, 0.15, 2.0, 1e-3, 4)
+    f = as_stored("D3Q19", O.run(O.D3Q19, f0, 20, 0.9, -5.0), storage, 2.0)
+    L = lbm.Lattice("D3Q19", n, n, n, tau=0.9, G=-5.0, storage=storage, rho_ref=2.0)
+    L.write_f(f)
+    roots, sizes, hist = L.bubble_sizes(nbins=16)
+    lab_o, n_o = O.label_gas(O.D3Q19, O.moments(O.D3Q19, f)[0], 1.0)
+    r_o, s_o = O.bubble_sizes(lab_o)
+    assert len(roots) == n_o >= 10
+    assert (roots == r_o).all() and (sizes == s_o).all()
+    assert (hist == O.size_histogram(s_o, 16)).all()
+    L.close()
+
+
+# ------------------------------------------------------- film at every lattice point
+
+def _film_oracle(lat, f, G, h_max, eps_arm, state):
+    rho = O.moments(lat, f)[0]
+    lab, _ = O.label_gas(lat, rho, 1.0)
+    _, p = O.eos(rho, G)
+    return O.film_cells(lat, lab, p, h_max, eps_arm, state)
+
+
+def _same_film(got, ref):
+    (cg, rg), (co, ro, d2o) = got, ref
+    assert cg == co, (cg, co)
+    assert len(rg) == len(ro)
+    for k, name in enumerate(("cell", "axis", "label_minus", "label_plus", "thickness")):
+        assert (rg[name] == ro[:, k]).all(), name
+    assert np.abs(rg["d2p"] - d2o).max(initial=0) < 1e-12
+
+
+def test_film_cells_two_disks_match_oracle(lbm):
+    """The oracle's two-disk state at 2800 steps written into the lattice,
+    then 160 more steps on each side: census and fired cells of the film
+    test at every lattice point agree at both calls (arming carried over),
+    and the thinning film fires."""
+    L, W, f0 = _two_disks(lbm)
+    f1 = O.run(O.D2Q9, f0, 2800, W["tau"], W["G"])
+    L.write_f(f1)
+    state = np.zeros((1, 128, 128), dtype=np.uint8)
+    a1 = L.film_cells(12, 1e-3)
+    _same_film(a1, _film_oracle(O.D2Q9, f1, W["G"], 12, 1e-3, state))
+    assert a1[0]["armed"] > 0
+    L.step(160)
+    f2 = O.run(O.D2Q9, f1, 160, W["tau"], W["G"])
+    a2 = L.film_cells(12, 1e-3)
+    _same_film(a2, _film_oracle(O.D2Q9, f2, W["G"], 12, 1e-3, state))
+    assert a2[0]["fired"] > 0
+    L.close()
+
+
+def test_film_cells_3d_match_oracle(lbm):
+    """Two spheres r = 10 on 48 x 40 x 40 (FP64), 3 cells apart through the
+    periodic x wrap: census and fired cells over three calls 30 steps apart,
+    while the film between them drains (these spheres join within ~100
+    steps, at the film's rim rather than by its rupture)."""
+    bub = np.array([[13.5, 20, 20, 10.0], [36.5, 20, 20, 10.0]])
+    f = oracle_init("D3Q19", 48, 40, 40, bub, 2.0, 0.15, 2.0, 1e-3, 6)
+    L = lbm.Lattice("D3Q19", 48, 40, 40, tau=1.0, G=-5.0, storage="f64")
+    L.write_f(f)
+    state = np.zeros((40, 40, 48), dtype=np.uint8)
+    for call in range(3):
+        got = L.film_cells(12, 1e-3)
+        _same_film(got, _film_oracle(O.D3Q19, f, -5.0, 12, 1e-3, state))
+        assert got[0]["film"] > 0 and got[0]["midpoints"] > 0 and got[0]["armed"] > 0
+        L.step(30)
+        f = O.run(O.D3Q19, f, 30, 1.0, -5.0)
+    L.close()

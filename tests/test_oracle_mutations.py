@@ -57,6 +57,16 @@ MUTATIONS = [
     ("d2 = 0.5 * (dd[0] + dd[1]);", "d2 = dd[1];"),
     ("int64_t cc = xm - fl < 0.5 ? c : c + 1;", "int64_t cc = xm - fl < 0.5 ? c + 1 : c;"),
     ("if (t < 0 || t > h + 2.0) break;", "if (t < 0 || t > h + 3.0) break;"),
+    # bubble census and the film test at every lattice point
+    ("if (label[k] >= 0) count[label[k]] += 1;", "if (label[k] > 0) count[label[k]] += 1;"),
+    ("while (b + 1 < nbins && ((int64_t)1 << (b + 1)) <= sizes[q]) ++b;",
+     "while (b + 1 < nbins && ((int64_t)1 << (b + 1)) < sizes[q]) ++b;"),
+    ("film = Lp >= 0 && Lm >= 0 && Lp != Lm && dp + dm - 1 <= h_max;",
+     "film = Lp >= 0 && Lm >= 0 && dp + dm - 1 <= h_max;"),
+    ("film = Lp >= 0 && Lm >= 0 && Lp != Lm && dp + dm - 1 <= h_max;",
+     "film = Lp >= 0 && Lm >= 0 && Lp != Lm && dp + dm <= h_max;"),
+    ("mid = film && (dp - dm <= 1 && dm - dp <= 1);", "mid = film && (dp - dm <= 1);"),
+    ("} else if ((state[k] & bit) && d2 >= 0.0) {", "} else if (d2 >= 0.0) {"),
 ]
 
 

@@ -544,3 +544,131 @@ def test_criterion_arming_disarming_and_merge():
     # a film thicker than h_max with d >= 0 after arming does not fire
     k, out = _run_criterion([_pr(7.9, -2e-3), _pr(8.1, 5e-3), _pr(7.0, -5e-4), _pr(6.0, 1e-3)])
     assert out is None
+
+
+# ---------------------------------------------------------------- bubble census
+
+@pytest.mark.parametrize("shape,lat", [((1, 12, 17), "D2Q9"), ((6, 7, 9), "D3Q19")])
+def test_bubble_sizes_match_graph_components(shape, lat):
+    """Component sizes against networkx on random masks (periodic, face
+    connectivity), keyed by the smallest cell index of each component."""
+    nx_ = pytest.importorskip("networkx")
+    rng = np.random.default_rng(7)
+    nz, ny, nx = shape
+    for trial in range(4):
+        rho = np.where(rng.random(shape) < 0.45, 0.3, 1.7)
+        lab, n = O.label_gas(O.D2Q9 if lat == "D2Q9" else O.D3Q19, rho, 1.0)
+        roots, sizes = O.bubble_sizes(lab)
+        g = nx_.Graph()
+        gas = np.argwhere(rho.reshape(-1) < 1.0).reshape(-1)
+        g.add_nodes_from(gas.tolist())
+        for k in gas:
+            x, y, z = k % nx, (k // nx) % ny, k // (nx * ny)
+            for dx, dy, dz in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+                if lat == "D2Q9" and dz:
+                    continue
+                m = (x + dx) % nx + nx * (((y + dy) % ny) + ny * ((z + dz) % nz))
+                if rho.reshape(-1)[m] < 1.0:
+                    g.add_edge(int(k), int(m))
+        comps = sorted((min(c), len(c)) for c in nx_.connected_components(g))
+        assert n == len(comps) == len(roots)
+        assert [int(r) for r in roots] == [c[0] for c in comps]
+        assert [int(s) for s in sizes] == [c[1] for c in comps]
+        assert sizes.sum() == (rho < 1.0).sum()
+
+
+def test_size_histogram_bins():
+    sizes = [1, 2, 3, 4, 7, 8, 15, 16, 1000, 1]
+    assert list(O.size_histogram(sizes, 4)) == [2, 2, 2, 4]
+    assert list(O.size_histogram(sizes, 12)) == [2, 2, 2, 2, 1, 0, 0, 0, 0, 1, 0, 0]
+    assert list(O.size_histogram([], 3)) == [0, 0, 0]
+
+
+# ------------------------------------------------------- film at every lattice point
+
+def _slab_labels(nx, ny, a_lo, a_hi, t, gap_gas=None):
+    """Two gas blocks across all rows: A = [a_lo, a_hi), B = [a_hi + t, a_hi + t +
+    (a_hi - a_lo)); labels as label_gas gives them."""
+    rho = np.full((1, ny, nx), 2.0)
+    rho[0, :, a_lo:a_hi] = 0.2
+    rho[0, :, a_hi + t:a_hi + t + (a_hi - a_lo)] = 0.2
+    lab, n = O.label_gas(O.D2Q9, rho, 1.0)
+    return lab, n
+
+
+@pytest.mark.parametrize("t", [3, 4, 12])
+def test_film_cells_slab_arm_then_fire(t):
+    """A liquid slab of t cells between two bubbles (x axis): t film cells per
+    row, 1 (odd t) or 2 (even t) midpoints per row; a pressure with d2 < 0
+    arms every midpoint, one with d2 >= 0 then fires every one, with the
+    bubbles' labels on the two sides and the thickness t."""
+    nx, ny, h_max = 48, 5, 12
+    lab, n = _slab_labels(nx, ny, 4, 12, t)
+    assert n == 2
+    xs = np.arange(nx, dtype=float)[None, None, :] * np.ones((1, ny, 1))
+    state = np.zeros(lab.shape, dtype=np.uint8)
+    mids = 1 if t % 2 else 2
+    c1, r1, d21 = O.film_cells(O.D2Q9, lab, -0.01 * xs ** 2, h_max, 1e-3, state)
+    assert c1 == dict(film=t * ny, midpoints=mids * ny, armed=mids * ny, fired=0)
+    c2, r2, d22 = O.film_cells(O.D2Q9, lab, 0.01 * xs ** 2, h_max, 1e-3, state)
+    assert c2 == dict(film=t * ny, midpoints=mids * ny, armed=0, fired=mids * ny)
+    a_root, b_root = 4, 12 + t
+    xm = [12 + (t - 1) // 2] if t % 2 else [12 + t // 2 - 1, 12 + t // 2]
+    want = sorted(x + nx * y for y in range(ny) for x in xm)
+    assert list(r2[:, 0]) == want
+    assert (r2[:, 1] == 0).all() and (r2[:, 2] == a_root).all() and (r2[:, 3] == b_root).all()
+    assert (r2[:, 4] == t).all() and np.allclose(d22, 0.02)
+    # a third call: nothing is armed any more
+    c3, _, _ = O.film_cells(O.D2Q9, lab, 0.01 * xs ** 2, h_max, 1e-3, state)
+    assert c3["fired"] == 0 and c3["armed"] == 0
+
+
+def test_film_cells_rules():
+    nx, ny = 48, 4
+    xs = np.arange(nx, dtype=float)[None, None, :] * np.ones((1, ny, 1))
+    p_arm, p_fire = -0.01 * xs ** 2, 0.01 * xs ** 2
+    # thicker than h_max: no film
+    lab, _ = _slab_labels(nx, ny, 4, 12, 9)
+    st = np.zeros(lab.shape, dtype=np.uint8)
+    c, _, _ = O.film_cells(O.D2Q9, lab, p_arm, 8, 1e-3, st)
+    assert c["film"] == 0 and c["midpoints"] == 0
+    # one bubble seen on both sides through the periodic wrap: no film
+    rho = np.full((1, ny, 12), 2.0)
+    rho[0, :, 0:6] = 0.2
+    lab1, n1 = O.label_gas(O.D2Q9, rho, 1.0)
+    assert n1 == 1
+    c, _, _ = O.film_cells(O.D2Q9, lab1, np.zeros_like(rho), 12, 1e-3,
+                           np.zeros(lab1.shape, dtype=np.uint8))
+    assert c["film"] == 0
+    # armed, then the film thickens beyond h_max: disarmed, no fire afterwards
+    lab4, _ = _slab_labels(nx, ny, 4, 12, 4)
+    st = np.zeros(lab4.shape, dtype=np.uint8)
+    O.film_cells(O.D2Q9, lab4, p_arm, 12, 1e-3, st)
+    assert st.any()
+    lab10, _ = _slab_labels(nx, ny, 4, 12, 10)
+    c, _, _ = O.film_cells(O.D2Q9, lab10, p_fire, 8, 1e-3, st)
+    assert c["film"] == 0 and c["armed"] == 0 and not st.any()
+    c, _, _ = O.film_cells(O.D2Q9, lab4, p_fire, 12, 1e-3, st)
+    assert c["fired"] == 0
+    # |d2| below eps_arm neither arms nor fires
+    st = np.zeros(lab4.shape, dtype=np.uint8)
+    c, _, _ = O.film_cells(O.D2Q9, lab4, -1e-4 * xs ** 2, 12, 1e-3, st)
+    assert c["armed"] == 0
+
+
+def test_film_cells_3d_along_z():
+    """Two gas slabs stacked in z with a 5-cell liquid layer: the film runs
+    along z only; midpoints on the middle plane."""
+    nx, ny, nz = 6, 5, 30
+    rho = np.full((nz, ny, nx), 2.0)
+    rho[2:8] = 0.2
+    rho[13:19] = 0.2
+    lab, n = O.label_gas(O.D3Q19, rho, 1.0)
+    assert n == 2
+    zs = np.arange(nz, dtype=float)[:, None, None] * np.ones((1, ny, nx))
+    st = np.zeros(lab.shape, dtype=np.uint8)
+    c, _, _ = O.film_cells(O.D3Q19, lab, -0.01 * zs ** 2, 12, 1e-3, st)
+    assert c["film"] == 5 * nx * ny and c["midpoints"] == nx * ny and c["armed"] == nx * ny
+    assert (st[10] == 4).all() and st.sum() == 4 * nx * ny
+    c, r, _ = O.film_cells(O.D3Q19, lab, 0.01 * zs ** 2, 12, 1e-3, st)
+    assert c["fired"] == nx * ny and (r[:, 1] == 2).all() and (r[:, 0] // (nx * ny) == 10).all()
