@@ -3,9 +3,11 @@
 
 One bench step = one diagnostic interval of the 128^3 D3Q19 FP32 foam
 workload (64 nucleation sites, r = 3, blowing agent 1e-4 per step, budget 50):
-100 fused collide-stream-force steps with injection, then the FP64 totals,
-the gas labelling and the per-site merge bookkeeping, all through the C ABI.
-Throughput is MLUPS = cells * 100 / seconds / 1e6.
+100 fused collide-stream-force steps with injection, then the diagnostics of
+the interval: FP64 totals and gas labelling in one pass, the per-site merge
+bookkeeping, the FP64 EOS pressure and the film test at every lattice point,
+and the bubble census with its size histogram, all through the C ABI.
+Throughput is MLUPS = cells * 100 / seconds / 1e6 over the whole step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -147,6 +149,18 @@ def max_over_ranks(world, x):
     return float(t.item())
 
 
+FILM_H_MAX, FILM_EPS_ARM, FILM_CAP, CENSUS_BINS = 12, 1e-3, 4096, 32
+
+
+def site_budgets(n):
+    """Blowing-agent budget per site: a number, or (lo, hi) drawn uniformly
+    from the recipe's seed."""
+    b = W["budget"]
+    if isinstance(b, tuple):
+        return np.random.default_rng(W["seed"]).uniform(b[0], b[1], n)
+    return np.full(n, float(b))
+
+
 def make_lattice(lbm, kernel="auto"):
     s = W["sites"]
     bub = lbm.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
@@ -156,9 +170,22 @@ def make_lattice(lbm, kernel="auto"):
                     rho_ref=W["rho_ref"], kernel=kernel)
     L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
     rate = np.full(len(bub), W["rate"])
-    budget = np.full(len(bub), W["budget"])
+    budget = site_budgets(len(bub))
     L.inject(rate, budget)
     return L, rate, budget
+
+
+def diagnostics(L):
+    """The diagnostic interval through the C ABI (labels computed once)."""
+    L.diagnose(want_labels=False)               # FP64 totals + gas labels in one pass
+    L.site_labels()                             # per-site labels, merge events
+    L.film_cells(FILM_H_MAX, FILM_EPS_ARM, FILM_CAP)  # FP64 pressure, film test per point
+    L.bubble_sizes(CENSUS_BINS)                 # bubble census + size histogram
+
+
+# kernels of one diagnostic interval: scan + final, union + compress, site
+# gather, moments (pressure), film test, census count + list
+DIAG_LAUNCHES = 9
 
 
 def cpu_baseline(seconds_target=15.0):
@@ -172,7 +199,7 @@ def cpu_baseline(seconds_target=15.0):
     cells = (np.floor(bub[:, 0] + 0.5) + W["nx"] * (np.floor(bub[:, 1] + 0.5)
              + W["ny"] * np.floor(bub[:, 2] + 0.5))).astype(np.int64)
     rate = np.full(len(bub), W["rate"])
-    budget = np.full(len(bub), W["budget"])
+    budget = site_budgets(len(bub))
     O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)  # warm
     n, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds_target:
@@ -198,7 +225,7 @@ def run_reference(args, world, rank):
     cells = (np.floor(bub[:, 0] + 0.5) + W["nx"] * (np.floor(bub[:, 1] + 0.5)
              + W["ny"] * np.floor(bub[:, 2] + 0.5))).astype(np.int64)
     rate = np.full(len(bub), W["rate"])
-    budget = np.full(len(bub), W["budget"])
+    budget = site_budgets(len(bub))
     for _ in range(warm):
         f = O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)
     t0 = time.perf_counter()
@@ -241,8 +268,7 @@ def run_ours(args, world, rank, local):
         L.step(INNER)
         if e_end is not None:
             e_end.record(stream)
-        L.diagnose(want_labels=False)   # FP64 totals + gas labels in one pass
-        L.site_labels()                 # per-site labels, merge events
+        diagnostics(L)
 
     for _ in range(args.warmup):
         bench_step()
@@ -272,29 +298,40 @@ def run_ours(args, world, rank, local):
     rate_h = torch.tensor(rate, dtype=torch.float64).pin_memory().numpy()
     budget_h = L.read_budgets()
     budget_pin = torch.tensor(budget_h, dtype=torch.float64).pin_memory().numpy()
+    rec = torch.empty(FILM_CAP * lbm.FILM_CELL.itemsize, dtype=torch.uint8,
+                      pin_memory=True).numpy()
+    roots = torch.empty(1 << 16, dtype=torch.int64, pin_memory=True).numpy()
+    sizes = torch.empty(1 << 16, dtype=torch.int64, pin_memory=True).numpy()
+    hist = np.zeros(CENSUS_BINS, dtype=np.int64)
     import ctypes as C
     nc = C.c_int64(0)
     tot = np.zeros(4)
+    census = lbm.FilmCensus()
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         L.inject(rate_h, budget_pin)                      # H2D: rates and budgets
         L.step(INNER)
-        lbm._check(lbm.lib().lbm_diagnose(L.handle, tot.ctypes.data_as(C.c_void_p),
-                                          labels.ctypes.data_as(C.c_void_p),
-                                          C.byref(nc)))   # D2H: totals, labels
+        lib = lbm.lib()
+        lbm._check(lib.lbm_diagnose(L.handle, vp(tot), vp(labels), C.byref(nc)))
+        lbm._check(lib.lbm_film_cells(L.handle, FILM_H_MAX, FILM_EPS_ARM, C.byref(census),
+                                      vp(rec), FILM_CAP))
+        lbm._check(lib.lbm_bubble_sizes(L.handle, vp(roots), vp(sizes), len(roots), C.byref(nc),
+                                        vp(hist), CENSUS_BINS))  # D2H: totals, labels, census
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
     h2d = rate_h.nbytes + budget_pin.nbytes
-    d2h = labels.nbytes + tot.nbytes + 8
+    d2h = (labels.nbytes + tot.nbytes + 8 + 32 + lbm.FILM_CELL.itemsize * min(census.fired, FILM_CAP)
+           + 16 * min(nc.value, len(roots)) + hist.nbytes + 8)
 
     units = CELLS * INNER * args.steps * world
     value = units / (ms / 1e3) / 1e6
     e2e_val = units / e2e_s / 1e6
     peak, src = peak_hbm()
     achieved = B_ALG * CELLS / (step_kernel_ms / 1e3) / 1e9
-    launches_per_step = INNER + 2 + 2 + 1   # steps, scan + final, union + compress, site gather
+    launches_per_step = INNER + DIAG_LAUNCHES
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -302,7 +339,8 @@ def run_ours(args, world, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if W["storage"] == "f64" else "f32",
             "data": "synthetic",
             "config": {"workload": W["name"], "lattice": "D3Q19", "extent": [W["nx"], W["ny"], W["nz"]],
                        "storage": W["storage"], "tau": W["tau"], "G": W["G"], "sites": W["sites"]["n"],
@@ -310,7 +348,10 @@ def run_ours(args, world, rank, local):
                        "plan": {"kernel": plan[0], "tile": plan[1], "tile_xy": [plan[2], plan[3]],
                                 "z_chunks": plan[4], "ctas": plan[5]},
                        "rho_ref": W["rho_ref"],
-                       "l2": "inputs larger than L2: two 159 MB population lattices",
+                       "l2": "inputs larger than L2: two %.0f MB population lattices"
+                             % (Q * CELLS * B_ALG / (2 * Q) / 1e6),
+                       "diagnostics": {"film_h_max": FILM_H_MAX, "film_eps_arm": FILM_EPS_ARM,
+                                       "census_bins": CENSUS_BINS},
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -391,7 +432,7 @@ def run_profile_case(args):
                     rho_ref=W["rho_ref"], kernel="fused" if args.tile else args.kernel,
                     tile=args.tile)
     L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
-    L.inject(np.full(len(bub), W["rate"]), np.full(len(bub), W["budget"]))
+    L.inject(np.full(len(bub), W["rate"]), site_budgets(len(bub)))
     L.step(args.profile_steps)
     L.sync()
     print(json.dumps({"profile_case": W["name"], "extent": n, "storage": storage,
@@ -415,9 +456,10 @@ def main():
     ap.add_argument("--extent", type=int, default=0,
                     help="--profile-steps: cubic lattice side (default: the foam's 128)")
     ap.add_argument("--workload", default="foam128",
-                    choices=["foam128", "foam512", "ensemble256"],
+                    choices=["foam128", "foam512", "foam768", "ensemble256"],
                     help="foam128: the default benchmark line; foam512: the 512^3 foam "
-                         "(FP32 or --storage f16/bf16); ensemble256: the batched two-bubble "
+                         "(FP32 or --storage f16/bf16); foam768: the 768^3 FP16-offset full "
+                         "foam with 4096 injection sites; ensemble256: the batched two-bubble "
                          "sweep run to completion")
     ap.add_argument("--storage", default=None, choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--single", action="store_true",
@@ -435,8 +477,14 @@ def main():
         if args.workload == "ensemble256":
             run_ensemble(args)
             return
-        W = dict(WL.FOAM_512)
-        METRIC = "D3Q19 Shan-Chen MLUPS (512^3 foam, 1000 bubbles, diagnostics every 100 steps)"
+        if args.workload == "foam512":
+            W = dict(WL.FOAM_512)
+            METRIC = ("D3Q19 Shan-Chen MLUPS (512^3 foam, 1000 bubbles, diagnostics every "
+                      "100 steps)")
+        else:
+            W = dict(WL.FOAM_768)
+            METRIC = ("D3Q19 Shan-Chen MLUPS (768^3 full foam, FP16-offset storage, 4096 sites "
+                      "with injection, diagnostics every 100 steps)")
         INNER = 100
         CELLS = W["nx"] * W["ny"] * W["nz"]
         args.no_cpu_baseline = True

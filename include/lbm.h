@@ -175,9 +175,11 @@ lbm_status lbm_read_budgets(lbm_ctx *ctx, double *budget, int32_t n);
  * an earlier step. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
-/* Autotuner: time every fused-kernel tile that fits this lattice and storage
- * (two warm-up steps, then `steps` timed steps each, starting from the
- * current state) and keep the fastest for later lbm_step calls.  The
+/* Autotuner: time every fused-kernel tile that fits this lattice and storage,
+ * each with the one-wave number of z chunks, half and double it (two
+ * warm-up steps, then the best of two rounds of `steps` timed steps,
+ * starting from the current state), and keep the fastest for later lbm_step
+ * calls.  The
  * populations, budgets and step counter are restored afterwards, so the
  * call has no effect on results.  *best_tile and *best_ms (either may be
  * NULL) receive the chosen tile id and its time per step.  Errors: ESTATE

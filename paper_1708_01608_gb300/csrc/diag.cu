@@ -204,15 +204,34 @@ __device__ __forceinline__ void cell_moments(const View &v, const void *stored, 
   }
 }
 
+// density alone, in the same order (and so the same bits) as cell_moments
 template <int LAT, int ST>
+__device__ __forceinline__ double cell_rho(const View &v, const void *stored, int x, int y, int z) {
+  using L = Lattice<LAT>;
+  double rho = 0.0;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) rho += load_d<ST>(stored, sidx(i, x, y, z, v), L::w(i) * v.rho_ref);
+  return rho;
+}
+
+// FP64 EOS pressure p = rho/3 + G/6 psi^2, psi = rho0 (1 - exp(-rho/rho0))
+__device__ __forceinline__ double eos_p(double r, double G, double rho0) {
+  const double s = rho0 * (1.0 - exp(-r / rho0));
+  return r / 3.0 + G / 6.0 * s * s;
+}
+
+template <int LAT, int ST, bool J>
 __global__ void k_moments(const View v, const void *stored, double G, double rho0, double *rho,
                           double *jx, double *jy, double *jz, double *psi, double *p, int *err) {
   const int64_t N = v.NX * v.NY * v.NZ;
   bool bad = false;
   GRID_LOOP(k, N) {
     const Idx c = idx_of(k, v);
-    double r, a, b, d;
-    cell_moments<LAT, ST>(v, stored, c, r, a, b, d);
+    double r, a = 0, b = 0, d = 0;
+    if (J)
+      cell_moments<LAT, ST>(v, stored, c, r, a, b, d);
+    else
+      r = cell_rho<LAT, ST>(v, stored, c.x, c.y, c.z);
     if (!isfinite(r)) bad = true;
     const double s = rho0 * (1.0 - exp(-r / rho0));
     if (rho) rho[k] = r;
@@ -220,7 +239,7 @@ __global__ void k_moments(const View v, const void *stored, double G, double rho
     if (jy) jy[k] = b;
     if (jz) jz[k] = d;
     if (psi) psi[k] = s;
-    if (p) p[k] = r / 3.0 + G / 6.0 * s * s;
+    if (p) p[k] = eos_p(r, G, rho0);
   }
   if (bad && err) atomicOr(err, ERR_NONFINITE);
 }
@@ -506,6 +525,119 @@ __global__ void k_gather_labels(const int32_t *L, const int32_t *cells, int32_t 
 }
 
 
+// ---- film test at every lattice point (Sec. 4) -------------------------------
+using FilmRec = lbm_film_cell;  // written as the C ABI hands it out
+
+// One thread per cell.  For each lattice axis: walk to the first gas cell on
+// each side (at most h_max cells), classify film / midpoint, and update the
+// arming bit of (cell, axis) as the two-bubble criterion does.  The FP64
+// pressure of a midpoint and its two neighbours along the axis is computed
+// from their populations (the bits diag_moments would store).
+template <int LAT, int ST>
+__global__ void __launch_bounds__(TPB)
+    k_film_cells(const View v, const int32_t *labels, const void *stored, double G, double rho0,
+                 int h_max, double eps_arm, uint8_t *state, unsigned long long *counts,
+                 int64_t cap, FilmRec *rec) {
+  __shared__ unsigned long long sh[4];
+  if (threadIdx.x < 4) sh[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t N = v.NX * v.NY * v.NZ;
+  const int naxes = v.lat == D2Q9 ? 2 : 3;
+  unsigned long long nfilm = 0, nmid = 0, narmed = 0;
+  GRID_LOOP(k, N) {
+    const Idx c = idx_of(k, v);
+    const int x = c.x, y = c.y, z = c.z;
+    uint8_t st = state[k];
+    const bool liquid = labels[k] < 0;
+    for (int ua = 0; ua < naxes; ++ua) {
+      // user axis ua -> view axis (D2Q9: x, z)
+      const int va = v.lat == D2Q9 && ua == 1 ? 2 : ua;
+      const int n_a = va == 0 ? (int)v.NX : (va == 1 ? (int)v.NY : (int)v.NZ);
+      const int c_a = va == 0 ? x : (va == 1 ? y : z);
+      // periodic coordinate along the axis without an integer division
+      // (|s| <= h_max; the loops run more than once only when n_a < h_max)
+      auto wrap_a = [&](int q) -> int {
+        while (q >= n_a) q -= n_a;
+        while (q < 0) q += n_a;
+        return q;
+      };
+      auto cell_at = [&](int s) -> int64_t {
+        const int q = wrap_a(c_a + s);
+        const int xx = va == 0 ? q : x, yy = va == 1 ? q : y, zz = va == 2 ? q : z;
+        return ((int64_t)zz * v.NY + yy) * v.NX + xx;
+      };
+      auto p_at = [&](int s) -> double {
+        const int q = wrap_a(c_a + s);
+        const int xx = va == 0 ? q : x, yy = va == 1 ? q : y, zz = va == 2 ? q : z;
+        return eos_p(cell_rho<LAT, ST>(v, stored, xx, yy, zz), G, rho0);
+      };
+      const uint8_t bit = (uint8_t)(1u << ua);
+      bool mid = false;
+      int32_t Lp = -1, Lm = -1;
+      int dp = 0, dm = 0;
+      if (liquid) {
+        // first gas cell within h_max along +e (then -e), four loads in flight
+        auto first_gas = [&](int sign, int32_t &lab_out) -> int {
+          for (int s0 = 1; s0 <= h_max; s0 += 4) {
+            int32_t l4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              l4[q] = s0 + q <= h_max ? labels[cell_at(sign * (s0 + q))] : -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (l4[q] >= 0) {
+                lab_out = l4[q];
+                return s0 + q;
+              }
+          }
+          return 0;
+        };
+        dp = first_gas(1, Lp);
+        if (Lp >= 0) dm = first_gas(-1, Lm);
+        const bool film = Lp >= 0 && Lm >= 0 && Lp != Lm && dp + dm - 1 <= h_max;
+        nfilm += film;
+        mid = film && dp - dm <= 1 && dm - dp <= 1;
+      }
+      if (!mid) {
+        st = (uint8_t)(st & ~bit);
+        continue;
+      }
+      ++nmid;
+      const double d2 = p_at(1) - 2.0 * p_at(0) + p_at(-1);
+      if (d2 < -eps_arm) {
+        st = (uint8_t)(st | bit);
+      } else if ((st & bit) && d2 >= 0.0) {
+        st = (uint8_t)(st & ~bit);
+        const unsigned long long q = atomicAdd(&counts[3], 1ull);
+        if ((int64_t)q < cap) {
+          FilmRec r;
+          r.cell = k;
+          r.axis = ua;
+          r.label_minus = Lm;
+          r.label_plus = Lp;
+          r.thickness = dp + dm - 1;
+          r.d2p = d2;
+          rec[q] = r;
+        }
+      }
+    }
+    state[k] = st;
+    narmed += __popc((unsigned)st);
+  }
+  // every thread of the block reaches this point (grid-stride loop)
+  const unsigned wf = __reduce_add_sync(0xffffffffu, (unsigned)nfilm);
+  const unsigned wm = __reduce_add_sync(0xffffffffu, (unsigned)nmid);
+  const unsigned wa = __reduce_add_sync(0xffffffffu, (unsigned)narmed);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sh[0], (unsigned long long)wf);
+    atomicAdd(&sh[1], (unsigned long long)wm);
+    atomicAdd(&sh[2], (unsigned long long)wa);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
+}
+
+
 // ---- film probe on FP64 density and pressure fields -------------------------
 struct FieldAcc {
   View v;
@@ -607,9 +739,14 @@ cudaError_t diag_store_pop(const View &v, const double *f, int i, void *stored, 
 cudaError_t diag_moments(const View &v, const void *stored, double G, double rho0, double *rho,
                          double *jx, double *jy, double *jz, double *psi, double *p, int *err,
                          cudaStream_t s) {
+  const bool want_j = jx || jy || jz;
   dispatch(v, [&](auto L, auto S) {
-    k_moments<decltype(L)::value, decltype(S)::value>
-        <<<nblocks(ncells(v)), TPB, 0, s>>>(v, stored, G, rho0, rho, jx, jy, jz, psi, p, err);
+    if (want_j)
+      k_moments<decltype(L)::value, decltype(S)::value, true>
+          <<<nblocks(ncells(v)), TPB, 0, s>>>(v, stored, G, rho0, rho, jx, jy, jz, psi, p, err);
+    else
+      k_moments<decltype(L)::value, decltype(S)::value, false>
+          <<<nblocks(ncells(v)), TPB, 0, s>>>(v, stored, G, rho0, rho, jx, jy, jz, psi, p, err);
   });
   return cudaGetLastError();
 }
@@ -690,6 +827,22 @@ cudaError_t diag_label(const View &v, const double *rho, double thr, int32_t *la
   k_ccl_init<<<nblocks(N), TPB, 0, s>>>(N, rho, thr, labels);
   k_ccl_union<<<nblocks(N), TPB, 0, s>>>(v, labels);
   k_ccl_compress<<<nblocks(N), TPB, 0, s>>>(N, labels, ncomp_dev);
+  return cudaGetLastError();
+}
+
+size_t film_record_bytes() { return sizeof(FilmRec); }
+
+cudaError_t diag_film_cells(const View &v, const int32_t *labels, const void *stored, double G,
+                            double rho0, int h_max, double eps_arm, uint8_t *state,
+                            unsigned long long *counts, int64_t cap, void *records,
+                            cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 4, s);
+  if (e != cudaSuccess) return e;
+  dispatch(v, [&](auto L, auto S) {
+    k_film_cells<decltype(L)::value, decltype(S)::value><<<nblocks(ncells(v)), TPB, 0, s>>>(
+        v, labels, stored, G, rho0, h_max, eps_arm, state, counts, cap,
+        static_cast<FilmRec *>(records));
+  });
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "internal.h"
 #include "lattice.cuh"
@@ -176,9 +177,27 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
     for (int k = 0; k < NS && k < NPL; ++k) issue(k);
   }
 
-  int sp = m.sp;  // this CTA's injection sites [sp, send), sorted by z
+  // This CTA's injection sites [sp, send), sorted by z.  The next one is
+  // held in registers (plane, cell, rate and budget: only this CTA changes
+  // the budgets of its sites during the step), so that a site plane costs
+  // no dependent global loads.
+  int sp = m.sp;
   const int send = m.send;
-  int next_z = sp < send ? m.site_z[m.bucket_site[sp]] : INT_MAX;  // plane of the next site
+  int next_z = INT_MAX, site_x = 0, site_y = 0, site_i = 0;
+  double site_rate = 0.0, site_budget = 0.0;
+  auto load_site = [&]() {
+    if (sp < send) {
+      site_i = m.bucket_site[sp];
+      next_z = m.site_z[site_i];
+      site_x = m.site_x[site_i];
+      site_y = m.site_y[site_i];
+      site_rate = m.rate[site_i];
+      site_budget = m.budget[site_i];
+    } else {
+      next_z = INT_MAX;
+    }
+  };
+  load_site();
 
   // destination coordinates of the push, fixed per thread (periodic)
   const int x = x0 + tx, y = y0 + ty;
@@ -301,20 +320,16 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
       bool site = false;
       if (Pc == next_z) {  // sites of this CTA in this plane (rare)
         double dm = 0.0;
-        for (; sp < send; ++sp) {
-          const int sidx = m.bucket_site[sp];
-          if (m.site_z[sidx] != Pc) break;
-          if (active && m.site_x[sidx] == x && m.site_y[sidx] == y) {
-            const double b = m.budget[sidx];
-            if (b > 0.0) {
-              const double d = fmin(m.rate[sidx], b);
-              m.budget[sidx] = b - d;
-              dm += d;
-              site = true;
-            }
+        while (next_z == Pc) {
+          if (active && site_x == x && site_y == y && site_budget > 0.0) {
+            const double d = fmin(site_rate, site_budget);
+            m.budget[site_i] = site_budget - d;
+            dm += d;
+            site = true;
           }
+          ++sp;
+          load_site();
         }
-        next_z = sp < send ? m.site_z[m.bucket_site[sp]] : INT_MAX;
         dmc = (C)dm;
       }
       if (active) {
@@ -391,30 +406,38 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
                   uz = (jz + tau * (gp * sz)) * ir;
           const C K = fmaf(rho * (C)-1.5, ux * ux + uy * uy + uz * uz, R);
           const C wK[2] = {cW[0] * K, cW[1] * K};
-          C moved = 0;
+          // relax and push; SITE adds the blowing agent w_i dm to every
+          // population of the cell (a separate copy of the loop, run only
+          // by the site cell's warp)
+          auto relax_push = [&](auto with_site) {
+            constexpr bool SITE = decltype(with_site)::value;
+            C moved = 0;
 #pragma unroll
-          for (int k2 = 0; k2 < L::NP; ++k2) {
-            const int i = L::rep(k2), o = L::opp(L::rep(k2));
-            const int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
-            const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
-            const C a = rho * cu;
-            const C A = fmaf(a, c45[wc] * cu, wK[wc]);
-            const C B = c3[wc] * a;
-            const C gi = fmaf(om1, cur[i], A + B);
-            const C go = fmaf(om1, cur[o], A - B);
-            moved += gi + go;
-            *dst(i) = S::store(gi);
-            *dst(o) = S::store(go);
-          }
-          *dst(0) = S::store(R - moved);
-          if (site) {
-            // blowing agent (rare): add w_i dm to the values just stored
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-              T *p = dst(i);
-              *p = S::store(S::load(__ldcg(p)) + (C)L::w(i) * dmc);
+            for (int k2 = 0; k2 < L::NP; ++k2) {
+              const int i = L::rep(k2), o = L::opp(L::rep(k2));
+              const int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
+              const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
+              const C a = rho * cu;
+              const C A = fmaf(a, c45[wc] * cu, wK[wc]);
+              const C B = c3[wc] * a;
+              const C gi = fmaf(om1, cur[i], A + B);
+              const C go = fmaf(om1, cur[o], A - B);
+              moved += gi + go;
+              if (SITE) {
+                *dst(i) = S::store(gi + (C)L::w(i) * dmc);
+                *dst(o) = S::store(go + (C)L::w(o) * dmc);
+              } else {
+                *dst(i) = S::store(gi);
+                *dst(o) = S::store(go);
+              }
             }
-          }
+            const C g0 = R - moved;
+            *dst(0) = S::store(SITE ? g0 + (C)L::w(0) * dmc : g0);
+          };
+          if (site)
+            relax_push(std::true_type{});
+          else
+            relax_push(std::false_type{});
         }
       }
     }
