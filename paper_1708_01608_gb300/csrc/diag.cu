@@ -652,10 +652,10 @@ struct FieldAcc {
 __global__ void k_film_probe(const View v, const double *rho, const double *p, int64_t x0,
                              int64_t y0, int64_t z0, int ex, int ey, int ez, int px_, int py_,
                              int pz_, int64_t len, double mid, double *out) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
   const FieldAcc acc{v, rho, p};
   const int e[3] = {ex, ey, ez}, ep[3] = {px_, py_, pz_};
-  film_probe_dev(acc, x0, y0, z0, e, ep, len, mid, out);
+  film_probe_block(acc, x0, y0, z0, e, ep, len, mid, out);
 }
 }  // namespace
 
@@ -775,8 +775,8 @@ cudaError_t diag_line_d2(const View &v, const double *p, int64_t x0, int64_t y0,
 cudaError_t diag_film_probe(const View &v, const double *rho, const double *p, int64_t x0,
                             int64_t y0, int64_t z0, const int e[3], const int ep[3], int64_t len,
                             double mid, double *out, cudaStream_t s) {
-  k_film_probe<<<1, 32, 0, s>>>(v, rho, p, x0, y0, z0, e[0], e[1], e[2], ep[0], ep[1], ep[2], len,
-                                mid, out);
+  k_film_probe<<<1, 128, 0, s>>>(v, rho, p, x0, y0, z0, e[0], e[1], e[2], ep[0], ep[1], ep[2],
+                                 len, mid, out);
   return cudaGetLastError();
 }
 

@@ -82,6 +82,11 @@ __global__ void __launch_bounds__(BX)
   float *out = parity ? D.latA : D.latB;
   const int64_t ps = D.popstride;
   fused_barriers_init<D2Q9, ST_F32, BX, 1, NS>(m);
+  // programmatic dependent launch within a class chain: the work item and
+  // the domain record are never written by a step, the lattices are read
+  // and written only after the previous step has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   uint32_t kb = 0;
   fused_march<D2Q9, ST_F32, BX, 1, NS>(m, [&](int i) { return out + i * ps; }, kb);
 }
@@ -91,9 +96,13 @@ struct PopAcc {
   const EnsDomain *D;
   const float *lat;
   __device__ int64_t off(int64_t x, int64_t z) const {
-    int64_t xx = x % D->NX, zz = z % D->NZ;
-    if (xx < 0) xx += D->NX;
-    if (zz < 0) zz += D->NZ;
+    // periodic wrap without a 64-bit division (probe coordinates stay
+    // within a few extents of the domain)
+    int64_t xx = x, zz = z;
+    while (xx >= D->NX) xx -= D->NX;
+    while (xx < 0) xx += D->NX;
+    while (zz >= D->NZ) zz -= D->NZ;
+    while (zz < 0) zz += D->NZ;
     return zz * D->px + xx;
   }
   __device__ double rho(int64_t x, int64_t, int64_t z) const {
@@ -111,14 +120,18 @@ struct PopAcc {
   }
 };
 
+// one CTA per domain: the film probe in parallel, then thread 0 advances the
+// domain's rupture state machine
 __global__ void k_ens_probe(const EnsDomain *doms, EnsState *st, int n, int parity,
                             const int64_t *step_now, double eps_arm, double h_max) {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= n || !st[d].active) return;
+  const int d = blockIdx.x;
+  if (d >= n || !st[d].active) return;  // uniform over the CTA
   const EnsDomain &D = doms[d];
   const PopAcc acc{&D, parity ? D.latB : D.latA};
-  double out[6];
-  film_probe_dev(acc, D.x0, 0, D.z0, D.e, D.ep, D.len, D.rho_mid, out);
+  __shared__ double out[6];
+  film_probe_block(acc, D.x0, 0, D.z0, D.e, D.ep, D.len, D.rho_mid, out);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   EnsState s = st[d];
   s.step = *step_now;
   if (out[0] == 0.0) {  // no film: merged before the criterion
@@ -149,10 +162,19 @@ cudaError_t ens_prepare_t() {
                               FusedK<D2Q9, ST_F32, BX, 1, NS>::SMEM);
 }
 template <int BX, int NS>
-void ens_launch_t(int grid, const EnsDomain *doms, const FusedMaps *a, const FusedMaps *b,
+cudaError_t ens_launch_t(int grid, const EnsDomain *doms, const FusedMaps *a, const FusedMaps *b,
                   const int4 *items, const int *count, int parity, cudaStream_t s) {
-  ens_step_kernel<BX, NS>
-      <<<grid, BX, FusedK<D2Q9, ST_F32, BX, 1, NS>::SMEM, s>>>(doms, a, b, items, count, parity);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)BX);
+  cfg.dynamicSmemBytes = (size_t)FusedK<D2Q9, ST_F32, BX, 1, NS>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ens_step_kernel<BX, NS>, doms, a, b, items, count, parity);
 }
 // class -> (BX, NS) of the D2Q9 fused tile table
 cudaError_t ens_prepare(int cls) {
@@ -162,12 +184,13 @@ cudaError_t ens_prepare(int cls) {
     default: return ens_prepare_t<64, 6>();
   }
 }
-void ens_launch(int cls, int grid, const EnsDomain *doms, const FusedMaps *a, const FusedMaps *b,
-                const int4 *items, const int *count, int parity, cudaStream_t s) {
+cudaError_t ens_launch(int cls, int grid, const EnsDomain *doms, const FusedMaps *a,
+                       const FusedMaps *b, const int4 *items, const int *count, int parity,
+                       cudaStream_t s) {
   switch (cls) {
-    case 0: ens_launch_t<256, 4>(grid, doms, a, b, items, count, parity, s); break;
-    case 1: ens_launch_t<128, 4>(grid, doms, a, b, items, count, parity, s); break;
-    default: ens_launch_t<64, 6>(grid, doms, a, b, items, count, parity, s); break;
+    case 0: return ens_launch_t<256, 4>(grid, doms, a, b, items, count, parity, s);
+    case 1: return ens_launch_t<128, 4>(grid, doms, a, b, items, count, parity, s);
+    default: return ens_launch_t<64, 6>(grid, doms, a, b, items, count, parity, s);
   }
 }
 int class_tile_id(int cls) { return cls == 0 ? 1 : (cls == 1 ? 2 : 3); }
@@ -184,6 +207,10 @@ struct lbm_ensemble {
   std::vector<EnsState> hstate;
   std::vector<int> cls;  // tile class per domain
   cudaStream_t s = nullptr;
+  // side streams of the captured interval: the tile classes hold disjoint
+  // domains, so their chains of steps run concurrently
+  cudaStream_t side[NCLASS] = {};
+  cudaEvent_t fork = nullptr, join[NCLASS] = {};
   lbm_alloc_fn alloc = nullptr;
   lbm_free_fn free = nullptr;
   void *user = nullptr;
@@ -197,6 +224,8 @@ struct lbm_ensemble {
   int4 *d_items[NCLASS] = {};
   int *d_count[NCLASS] = {};
   int max_items[NCLASS] = {};
+  int zlen = 16;  // rows per work item (chosen at every regrid)
+  int nsm = 152;
   double eps_arm = 0, h_max = 8;
   int diag_every = 100;
   int64_t steps = 0;
@@ -250,12 +279,14 @@ void efree_all(lbm_ensemble *E) {
 }
 
 // Work items of the active domains of each class.  Rows are cut into chunks
-// of ENS_ZLEN: a CTA marches its chunk row by row, so the chunk length sets
-// the latency of a step, and short chunks give many independent items.
-constexpr int ENS_ZLEN = 16;
+// of at most zmax rows: a CTA marches its chunk row by row, so the chunk
+// length sets the latency of a step, and short chunks give many independent
+// items.  Every chunk also stages the two rows around it, so long chunks
+// are cheaper while there are enough of them to fill the GPU.
+constexpr int ENS_ZLEN_MAX = 16, ENS_ZLEN_MIN = 2;
 
-int chunk_len(int ny) {
-  int zlen = std::min(ny, ENS_ZLEN);
+int chunk_len(int ny, int zmax) {
+  int zlen = std::min(ny, zmax);
   const int nzc = (ny + zlen - 1) / zlen;
   return (ny + nzc - 1) / nzc;
 }
@@ -268,7 +299,7 @@ lbm_status build_items(lbm_ensemble *E, int counts[NCLASS]) {
       const int bx = CLASS_BX[c];
       const int nx = E->hdom[d].NX, ny = E->hdom[d].NZ;
       const int tiles_x = (nx + bx - 1) / bx;
-      const int zlen = chunk_len(ny);
+      const int zlen = chunk_len(ny, E->zlen);
       const int nzc = (ny + zlen - 1) / zlen;
       for (int zc = 0; zc < nzc; ++zc)
         for (int tx = 0; tx < tiles_x; ++tx)
@@ -284,11 +315,24 @@ lbm_status build_items(lbm_ensemble *E, int counts[NCLASS]) {
   return LBM_OK;
 }
 
-int count_items(const lbm_ensemble *E, int d, int c) {
+int count_items(const lbm_ensemble *E, int d, int c, int zmax) {
   const int bx = CLASS_BX[c];
   const int nx = E->hdom[d].NX, ny = E->hdom[d].NZ;
-  const int zlen = chunk_len(ny);
+  const int zlen = chunk_len(ny, zmax);
   return ((nx + bx - 1) / bx) * ((ny + zlen - 1) / zlen);
+}
+
+// the longest chunk (16, 8, 4, 2 rows) that still gives the active domains
+// at least four CTAs per SM
+int choose_zlen(const lbm_ensemble *E) {
+  int z = ENS_ZLEN_MAX;
+  for (; z > ENS_ZLEN_MIN; z /= 2) {
+    int64_t items = 0;
+    for (int d = 0; d < E->n; ++d)
+      if (E->hstate[d].active) items += count_items(E, d, E->cls[d], z);
+    if (items >= 4LL * E->nsm) break;
+  }
+  return z;
 }
 
 void drop_graph(lbm_ensemble *E) {
@@ -300,13 +344,19 @@ void drop_graph(lbm_ensemble *E) {
 
 // one diagnostic interval: diag_every steps of every class, then the probe
 lbm_status enqueue_interval(lbm_ensemble *E) {
-  for (int t = 0; t < E->diag_every; ++t)
-    for (int c = 0; c < NCLASS; ++c)
-      if (E->max_items[c] > 0)
-        ens_launch(c, E->max_items[c], E->d_dom, E->d_mapsA, E->d_mapsB, E->d_items[c],
-                   E->d_count[c], t & 1, E->s);
-  k_ens_probe<<<(E->n + 127) / 128, 128, 0, E->s>>>(E->d_dom, E->d_state, E->n, 0, E->d_step,
-                                                    E->eps_arm, E->h_max);
+  // fork: one chain of diag_every steps per tile class, joined before the probe
+  ECK(cudaEventRecord(E->fork, E->s));
+  for (int c = 0; c < NCLASS; ++c) {
+    if (E->max_items[c] == 0) continue;
+    ECK(cudaStreamWaitEvent(E->side[c], E->fork, 0));
+    for (int t = 0; t < E->diag_every; ++t)
+      ECK(ens_launch(c, E->max_items[c], E->d_dom, E->d_mapsA, E->d_mapsB, E->d_items[c],
+                     E->d_count[c], t & 1, E->side[c]));
+    ECK(cudaEventRecord(E->join[c], E->side[c]));
+    ECK(cudaStreamWaitEvent(E->s, E->join[c], 0));
+  }
+  k_ens_probe<<<E->n, 128, 0, E->s>>>(E->d_dom, E->d_state, E->n, 0, E->d_step, E->eps_arm,
+                                       E->h_max);
   ECK(cudaGetLastError());
   return LBM_OK;
 }
@@ -382,9 +432,14 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
     lbm_ensemble_destroy(E);
     return st;
   };
-  if (cudaStreamCreateWithFlags(&E->s, cudaStreamNonBlocking) != cudaSuccess) {
+  bool streams_ok = cudaStreamCreateWithFlags(&E->s, cudaStreamNonBlocking) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&E->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int c = 0; c < NCLASS && streams_ok; ++c)
+    streams_ok = cudaStreamCreateWithFlags(&E->side[c], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&E->join[c], cudaEventDisableTiming) == cudaSuccess;
+  if (!streams_ok) {
     cudaGetLastError();
-    delete E;
+    lbm_ensemble_destroy(E);
     return efail(LBM_ECUDA, "ensemble: stream creation failed");
   }
   // arena layout
@@ -455,7 +510,7 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
   // work-list capacity per class: every domain could be moved to any class
   for (int c = 0; c < NCLASS; ++c) {
     int cap = 0;
-    for (int d = 0; d < n; ++d) cap += count_items(E, d, c);
+    for (int d = 0; d < n; ++d) cap += count_items(E, d, c, ENS_ZLEN_MIN);
     E->max_items[c] = 0;
     if ((st = ealloc(E, sizeof(int4) * cap, &p)) != LBM_OK) return bail(st);
     E->d_items[c] = static_cast<int4 *>(p);
@@ -516,6 +571,11 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
       return bail(efail(LBM_ECUDA, "ensemble: initial state failed"));
     }
   }
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&E->nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  E->zlen = choose_zlen(E);
   int counts[NCLASS];
   if ((st = build_items(E, counts)) != LBM_OK) return bail(st);
   for (int c = 0; c < NCLASS; ++c) E->max_items[c] = counts[c];
@@ -528,6 +588,11 @@ void lbm_ensemble_destroy(lbm_ensemble *E) {
   if (E->s) cudaStreamSynchronize(E->s);
   drop_graph(E);
   efree_all(E);
+  for (int c = 0; c < NCLASS; ++c) {
+    if (E->side[c]) cudaStreamDestroy(E->side[c]);
+    if (E->join[c]) cudaEventDestroy(E->join[c]);
+  }
+  if (E->fork) cudaEventDestroy(E->fork);
   if (E->s) cudaStreamDestroy(E->s);
   cudaGetLastError();
   delete E;
@@ -537,11 +602,14 @@ void lbm_ensemble_destroy(lbm_ensemble *E) {
 // CTA per item) are re-captured when a class emptied or shrank by half, so
 // that finished domains stop costing launches.
 static lbm_status refresh_work(lbm_ensemble *E) {
+  const int z = choose_zlen(E);
+  bool regrid = z != E->zlen;
+  E->zlen = z;
   int counts[NCLASS];
   ECKS(build_items(E, counts));
-  bool regrid = false;
   for (int c = 0; c < NCLASS; ++c)
     regrid |= (counts[c] == 0) != (E->max_items[c] == 0) || 2 * counts[c] < E->max_items[c];
+  for (int c = 0; c < NCLASS; ++c) regrid |= counts[c] > E->max_items[c];
   if (regrid) {
     drop_graph(E);
     for (int c = 0; c < NCLASS; ++c) E->max_items[c] = counts[c];
