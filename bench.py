@@ -42,10 +42,11 @@ CELLS = W["nx"] * W["ny"] * W["nz"]
 Q = 19
 B_ALG = 2 * Q * 4                             # bytes per lattice update, FP32 storage
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes per launch of the fused kernel from an ncu capture of this
-# workload (dram__bytes_read.sum + dram__bytes_write.sum); None = not captured
-# for the current kernel.
-NCU_TRAFFIC_PER_LAUNCH = {4: 276.7e6}  # tile id -> bytes (profiles/fused_step_d3q19_f32_128.md)
+# DRAM bytes per launch of the fused kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the current kernel), keyed by
+# (workload, storage, tile id); workloads without a capture report null.
+NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.3e6,
+                          ("d3q19_foam_128", "f32", 5): 277.3e6}
 
 
 def peak_hbm():
@@ -358,7 +359,7 @@ def run_ours(args, world, rank, local):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src,
-                         "traffic": NCU_TRAFFIC_PER_LAUNCH.get(plan[1]),
+                         "traffic": NCU_TRAFFIC_PER_LAUNCH.get((W["name"], W["storage"], plan[1])),
                          "kernel": "fused_step_kernel", "bytes_per_update": B_ALG,
                          "kernel_ms": step_kernel_ms},
             "cpu_baseline": cpu,
