@@ -123,14 +123,20 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus):
+    """One process per GPU (torch.distributed.run sets RANK, WORLD_SIZE,
+    LOCAL_RANK, MASTER_*): NCCL on GPUs, gloo where there is none (the
+    host-side logic of the N > 1 path is tested that way on CPU)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -141,13 +147,22 @@ def barrier(world):
 
 
 def max_over_ranks(world, x):
+    """The slowest rank's time: every rank gets the maximum."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(units_per_rank, world, seconds):
+    """Whole-job throughput in millions of units per second: every rank
+    processes units_per_rank (independent replicas), the job takes the
+    slowest rank's seconds."""
+    return units_per_rank * world / seconds / 1e6
 
 
 FILM_H_MAX, FILM_EPS_ARM, FILM_CAP, CENSUS_BINS = 12, 1e-3, 4096, 32
@@ -213,6 +228,17 @@ def cpu_baseline(seconds_target=15.0):
                       f"({dt:.1f} s, OpenMP over all host cores)"}
 
 
+def base_config():
+    """The workload's config, the same for both arms."""
+    return {"workload": W["name"], "lattice": "D3Q19", "extent": [W["nx"], W["ny"], W["nz"]],
+            "storage": W["storage"], "tau": W["tau"], "G": W["G"], "sites": W["sites"]["n"],
+            "lbm_steps_per_bench_step": INNER, "rho_ref": W["rho_ref"],
+            "l2": "inputs larger than L2: two %.0f MB population lattices"
+                  % (CELLS * B_ALG / 2 / 1e6),
+            "diagnostics": {"film_h_max": FILM_H_MAX, "film_eps_arm": FILM_EPS_ARM,
+                            "census_bins": CENSUS_BINS}}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -238,8 +264,9 @@ def run_reference(args, world, rank):
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": W["name"], "cells": CELLS, "sites": s["n"],
-                       "sample": "one LBM time step of the full lattice per bench step"},
+            "config": dict(base_config(),
+                           sample="the FP64 oracle, one LBM time step of the full lattice "
+                                  "with injection per bench step"),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(),
                              "kind": "oracle",
                              "sample": f"{steps} oracle time steps of the full 128^3 lattice"},
@@ -327,9 +354,9 @@ def run_ours(args, world, rank, local):
     d2h = (labels.nbytes + tot.nbytes + 8 + 32 + lbm.FILM_CELL.itemsize * min(census.fired, FILM_CAP)
            + 16 * min(nc.value, len(roots)) + hist.nbytes + 8)
 
-    units = CELLS * INNER * args.steps * world
-    value = units / (ms / 1e3) / 1e6
-    e2e_val = units / e2e_s / 1e6
+    units = CELLS * INNER * args.steps  # per rank
+    value = job_value(units, world, ms / 1e3)
+    e2e_val = job_value(units, world, e2e_s)
     peak, src = peak_hbm()
     achieved = B_ALG * CELLS / (step_kernel_ms / 1e3) / 1e9
     launches_per_step = INNER + DIAG_LAUNCHES
@@ -343,17 +370,10 @@ def run_ours(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if W["storage"] == "f64" else "f32",
             "data": "synthetic",
-            "config": {"workload": W["name"], "lattice": "D3Q19", "extent": [W["nx"], W["ny"], W["nz"]],
-                       "storage": W["storage"], "tau": W["tau"], "G": W["G"], "sites": W["sites"]["n"],
-                       "lbm_steps_per_bench_step": INNER, "kernel": args.kernel,
-                       "plan": {"kernel": plan[0], "tile": plan[1], "tile_xy": [plan[2], plan[3]],
-                                "z_chunks": plan[4], "ctas": plan[5]},
-                       "rho_ref": W["rho_ref"],
-                       "l2": "inputs larger than L2: two %.0f MB population lattices"
-                             % (Q * CELLS * B_ALG / (2 * Q) / 1e6),
-                       "diagnostics": {"film_h_max": FILM_H_MAX, "film_eps_arm": FILM_EPS_ARM,
-                                       "census_bins": CENSUS_BINS},
-                       "parallelism": f"replicas x{world}"},
+            "config": dict(base_config(), kernel=args.kernel,
+                           plan={"kernel": plan[0], "tile": plan[1], "tile_xy": [plan[2], plan[3]],
+                                 "z_chunks": plan[4], "ctas": plan[5]},
+                           parallelism=f"replicas x{world}"),
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,

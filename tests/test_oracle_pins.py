@@ -9,6 +9,8 @@ them.  CPU only.
 import math
 
 import networkx as nx
+import os
+
 import numpy as np
 import pytest
 from scipy import integrate, optimize
@@ -53,9 +55,14 @@ def test_velocity_set_isotropy(lat):
 
 
 def test_splitmix64_published_vector():
-    """SplitMix64 seeded with 1234567: the published first outputs."""
-    assert [O.splitmix64(1234567, k) for k in range(3)] == [
-        6457827717110365317, 3203168211198807973, 9817491932198370423]
+    """SplitMix64 seeded with 1234567: the published first outputs
+    (tests/golden/splitmix64_seed1234567.txt, with its citation)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "splitmix64_seed1234567.txt")
+    with open(path) as fh:
+        want = [int(line) for line in fh if line.strip() and not line.startswith("#")]
+    assert len(want) == 5
+    assert [O.splitmix64(1234567, k) for k in range(len(want))] == want
 
 
 # ---------------------------------------------------------------- EOS / psi
