@@ -15,6 +15,9 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace sclbm {
 
 enum { D2Q9 = 0, D3Q19 = 1 };
@@ -141,6 +144,44 @@ __device__ __forceinline__ double psi_of(double rho, double rho0, double inv_rho
 // (FP32: the hardware exponential, a few ulp, far below FP32 storage noise)
 __device__ __forceinline__ float psi_of(float rho, float rho0, float inv_rho0) {
   return rho0 * (1.0f - __expf(-rho * inv_rho0));
+}
+
+// ---- compile-time helpers of the FP32 collision ----------------------------
+// f(integral_constant<int, 0>), ..., f(integral_constant<int, N-1>)
+template <class F, int... K>
+__device__ __forceinline__ void static_for_impl(F &f, std::integer_sequence<int, K...>) {
+  (f(std::integral_constant<int, K>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+// acc + c v and acc + c w v for a velocity component c in {-1, 0, 1}: terms
+// with c = 0 vanish at compile time (a product with 0.0 is not removable
+// under IEEE rules, so c v must not be written out for c = 0)
+template <int CC>
+__device__ __forceinline__ float cacc(float acc, float v) {
+  if constexpr (CC > 0) return acc + v;
+  else if constexpr (CC < 0) return acc - v;
+  else return acc;
+}
+template <int CC>
+__device__ __forceinline__ float cfma(float acc, float w, float v) {
+  if constexpr (CC > 0) return fmaf(w, v, acc);
+  else if constexpr (CC < 0) return fmaf(-w, v, acc);
+  else return acc;
+}
+// c.u for a moving velocity c with components in {-1, 0, 1}: nonzero terms only
+template <int A, int B, int Z>
+__device__ __forceinline__ float cdot(float x, float y, float z) {
+  static_assert(A != 0 || B != 0 || Z != 0, "moving velocities only");
+  float r;
+  if constexpr (A != 0) r = A > 0 ? x : -x;
+  else if constexpr (B != 0) r = B > 0 ? y : -y;
+  else r = Z > 0 ? z : -z;
+  if constexpr (A != 0 && B != 0) r = B > 0 ? r + y : r - y;
+  if constexpr ((A != 0 || B != 0) && Z != 0) r = Z > 0 ? r + z : r - z;
+  return r;
 }
 
 // ---- small PTX helpers ----------------------------------------------------

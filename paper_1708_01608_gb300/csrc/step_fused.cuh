@@ -259,9 +259,19 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
   const int32_t ox[3] = {xm, x, xp};
   const int32_t oy[3] = {(int32_t)(ym * m.px), (int32_t)(y * m.px), (int32_t)(yp * m.px)};
 
+  // The staged values of this thread's cell: FP64 keeps them per velocity;
+  // the FP32 path keeps the opposite pairs (i, opp(i)) as float2 so that
+  // their sums and relaxations run as paired FP32 instructions.
   C cur[Q], nxt[Q];
+  float2 cur2[L::NP], nxt2[L::NP];
+  float cur0 = 0.0f, nxt0 = 0.0f;
+  if constexpr (F64) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) cur[i] = nxt[i] = 0;
+    for (int i = 0; i < Q; ++i) cur[i] = nxt[i] = 0;
+  } else {
+#pragma unroll
+    for (int k2 = 0; k2 < L::NP; ++k2) cur2[k2] = nxt2[k2] = make_float2(0.0f, 0.0f);
+  }
   C Rcur = 0, Rnxt = 0;  // sum of the staged values of this thread's cell
 
   // FP32 relaxation constants per weight class (omega folded in)
@@ -274,6 +284,10 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
     c45[k2] = (C)4.5 * w * omega;
   }
 
+  // two planes per iteration where registers allow (512-thread tiles): the
+  // staged values then change register sets instead of being copied
+  constexpr int UNROLL = NT > 256 ? 2 : 1;
+#pragma unroll UNROLL
   for (int k = 0; k < NPL; ++k) {
     const int s = (int)((k0 + k) % NS);
     const int P = zs - 1 + k;
@@ -285,11 +299,23 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
     C *rk = ring + (k & 3) * PW * PH;
     if (active) {
       C rho = 0;
+      if constexpr (F64) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const C v = S::load(mainb[(i * BY + ty) * BX + tx]);
-        nxt[i] = v;
-        rho += v;
+        for (int i = 0; i < Q; ++i) {
+          const C v = S::load(mainb[(i * BY + ty) * BX + tx]);
+          nxt[i] = v;
+          rho += v;
+        }
+      } else {
+        float2 s2;
+        static_for<L::NP>([&](auto kc) {
+          constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
+          nxt2[k2] = make_float2(S::load(mainb[(i * BY + ty) * BX + tx]),
+                                 S::load(mainb[(o * BY + ty) * BX + tx]));
+          s2 = k2 == 0 ? nxt2[k2] : __fadd2_rn(s2, nxt2[k2]);
+        });
+        nxt0 = S::load(mainb[ty * BX + tx]);
+        rho = (s2.x + s2.y) + nxt0;
       }
       rk[(ty + HY) * PW + tx + 1] = psi_of(rho_ref + rho, rho0, inv_rho0);
       Rnxt = rho;
@@ -297,8 +323,18 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
     if (tid < nhalo) {
       const T *b = reinterpret_cast<const T *>(st + h_off);
       C rho = 0;
+      if constexpr (F64) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) rho += S::load(b[i * h_pstride]);
+        for (int i = 0; i < Q; ++i) rho += S::load(b[i * h_pstride]);
+      } else {
+        float2 s2;
+        static_for<L::NP>([&](auto kc) {
+          constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
+          const float2 v = make_float2(S::load(b[i * h_pstride]), S::load(b[o * h_pstride]));
+          s2 = k2 == 0 ? v : __fadd2_rn(s2, v);
+        });
+        rho = (s2.x + s2.y) + S::load(b[0]);
+      }
       rk[h_slot] = psi_of(rho_ref + rho, rho0, inv_rho0);
     }
 
@@ -386,19 +422,20 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
           // The rest population takes R minus the moving ones, so mass is
           // conserved to rounding.
           const C R = Rcur;
-          C jx = 0, jy = 0, jz = 0, sx = 0, sy = 0, sz = 0;
-#pragma unroll
-          for (int k2 = 0; k2 < L::NP; ++k2) {
-            const int i = L::rep(k2), o = L::opp(L::rep(k2));
-            const C d = cur[i] - cur[o];
-            jx += (C)L::cx(i) * d;
-            jy += (C)L::cy(i) * d;
-            jz += (C)L::cz(i) * d;
-            const C dp = (C)L::w(i) * (psi_at(i) - psi_at(o));
-            sx += (C)L::cx(i) * dp;
-            sy += (C)L::cy(i) * dp;
-            sz += (C)L::cz(i) * dp;
-          }
+          // -0 is the additive identity, so the first term is no addition
+          C jx = -0.0f, jy = -0.0f, jz = -0.0f, sx = -0.0f, sy = -0.0f, sz = -0.0f;
+          static_for<L::NP>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
+            constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const C d = cur2[k2].x - cur2[k2].y;
+            jx = cacc<cx>(jx, d);
+            jy = cacc<cy>(jy, d);
+            jz = cacc<cz>(jz, d);
+            const C dps = psi_at(i) - psi_at(o), w = (C)L::w(i);
+            sx = cfma<cx>(sx, w, dps);
+            sy = cfma<cy>(sy, w, dps);
+            sz = cfma<cz>(sz, w, dps);
+          });
           const C rho = rho_ref + R;
           const C gp = -G * p0[c0];
           const C ir = __fdividef((C)1, rho);
@@ -406,23 +443,24 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
                   uz = (jz + tau * (gp * sz)) * ir;
           const C K = fmaf(rho * (C)-1.5, ux * ux + uy * uy + uz * uz, R);
           const C wK[2] = {cW[0] * K, cW[1] * K};
+          const float2 om1_2 = make_float2(om1, om1);
           // relax and push; SITE adds the blowing agent w_i dm to every
           // population of the cell (a separate copy of the loop, run only
           // by the site cell's warp)
           auto relax_push = [&](auto with_site) {
             constexpr bool SITE = decltype(with_site)::value;
-            C moved = 0;
-#pragma unroll
-            for (int k2 = 0; k2 < L::NP; ++k2) {
-              const int i = L::rep(k2), o = L::opp(L::rep(k2));
-              const int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
-              const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
+            float2 moved2;
+            static_for<L::NP>([&](auto kc) {
+              constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
+              constexpr int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
+              const C cu = cdot<L::cx(i), L::cy(i), L::cz(i)>(ux, uy, uz);
               const C a = rho * cu;
               const C A = fmaf(a, c45[wc] * cu, wK[wc]);
               const C B = c3[wc] * a;
-              const C gi = fmaf(om1, cur[i], A + B);
-              const C go = fmaf(om1, cur[o], A - B);
-              moved += gi + go;
+              // (g_i, g_o) = (1 - omega) (g_i, g_o) + (A + B, A - B): one paired FMA
+              const float2 g = __ffma2_rn(om1_2, cur2[k2], make_float2(A + B, A - B));
+              moved2 = k2 == 0 ? g : __fadd2_rn(moved2, g);
+              const C gi = g.x, go = g.y;
               if (SITE) {
                 *dst(i) = S::store(gi + (C)L::w(i) * dmc);
                 *dst(o) = S::store(go + (C)L::w(o) * dmc);
@@ -430,8 +468,8 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
                 *dst(i) = S::store(gi);
                 *dst(o) = S::store(go);
               }
-            }
-            const C g0 = R - moved;
+            });
+            const C g0 = R - (moved2.x + moved2.y);
             *dst(0) = S::store(SITE ? g0 + (C)L::w(0) * dmc : g0);
           };
           if (site)
@@ -441,8 +479,14 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
         }
       }
     }
+    if constexpr (F64) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
+      for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < L::NP; ++k2) cur2[k2] = nxt2[k2];
+      cur0 = nxt0;
+    }
     Rcur = Rnxt;
   }
   kb = k0 + NPL;
