@@ -45,8 +45,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the fused kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the current kernel), keyed by
 # (workload, storage, tile id); workloads without a capture report null.
-NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.3e6,
-                          ("d3q19_foam_128", "f32", 5): 277.3e6}
+NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.8e6,
+                          ("d3q19_foam_128", "f32", 5): 277.5e6}
 
 
 def peak_hbm():
