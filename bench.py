@@ -455,9 +455,12 @@ def run_profile_case(args):
     L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
     L.inject(np.full(len(bub), W["rate"]), site_budgets(len(bub)))
     L.step(args.profile_steps)
+    if args.profile_diagnostics:
+        diagnostics(L)  # one diagnostic interval after the steps
     L.sync()
     print(json.dumps({"profile_case": W["name"], "extent": n, "storage": storage,
-                      "steps": args.profile_steps, "plan": L.plan()}))
+                      "steps": args.profile_steps, "diagnostics": args.profile_diagnostics,
+                      "plan": L.plan()}))
     L.close()
 
 
@@ -476,6 +479,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="fused tile id for --profile-steps")
     ap.add_argument("--extent", type=int, default=0,
                     help="--profile-steps: cubic lattice side (default: the foam's 128)")
+    ap.add_argument("--profile-diagnostics", action="store_true",
+                    help="--profile-steps: then run one diagnostic interval")
     ap.add_argument("--workload", default="foam128",
                     choices=["foam128", "foam512", "foam768", "ensemble256"],
                     help="foam128: the default benchmark line; foam512: the 512^3 foam "

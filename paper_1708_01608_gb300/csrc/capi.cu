@@ -74,6 +74,7 @@ struct lbm_ctx {
   // bubble census and per-point film test
   DevBuf d_count, d_census, d_film_state, d_film_counts, d_film_rec;
   bool film_state_clear = false;  // d_film_state must be zeroed before use
+  int64_t census_cap = 4096;       // device capacity of the census list (grows)
   // d_rho / d_p hold the FP64 density and pressure of the current state;
   // d_labels its gas labels (cleared by stepping and by state writes)
   bool p_valid = false, labels_valid = false;
@@ -868,29 +869,37 @@ lbm_status lbm_bubble_sizes(lbm_ctx *c, int64_t *roots, int64_t *sizes, int64_t 
   CKS(set_device(c));
   CKS(check_sticky(c));
   CKS(ensure_labels(c));
-  unsigned long long nc = 0;
-  CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
-  CKS(sync_and_check(c));
-  count_merges(c);
-  const int64_t n = (int64_t)nc;
   const int nb = std::max(nbins, 1);
   CKS(dalloc(c, c->d_count, sizeof(int32_t) * c->N));
-  // [n_dev][hist: 64][roots: n][sizes: n]
-  CKS(dalloc(c, c->d_census, sizeof(int64_t) * (65 + 2 * (size_t)std::max<int64_t>(n, 1))));
-  auto *base = static_cast<unsigned long long *>(c->d_census.p);
-  int64_t *d_roots = reinterpret_cast<int64_t *>(base + 65), *d_sizes = d_roots + std::max<int64_t>(n, 1);
-  CK(diag_bubble_sizes(c->v, static_cast<const int32_t *>(c->d_labels.p),
-                       static_cast<int32_t *>(c->d_count.p), base, n, d_roots, d_sizes, nb,
-                       base + 1, c->s));
-  std::vector<int64_t> r((size_t)n), sz((size_t)n);
+  // One synchronisation in the common case: the list is written up to the
+  // device capacity, which grows (and the list is redone) when a lattice has
+  // more components than ever before.
+  unsigned long long nc = 0;
+  std::vector<int64_t> r, sz;
   std::vector<unsigned long long> h((size_t)nb), cnt(1);
-  CK(cudaMemcpyAsync(cnt.data(), base, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
-  CK(cudaMemcpyAsync(h.data(), base + 1, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, c->s));
-  if (n > 0) {
-    CK(cudaMemcpyAsync(r.data(), d_roots, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(sz.data(), d_sizes, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->s));
+  int64_t n = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t capdev = c->census_cap;
+    // [n_dev][hist: 64][roots: capdev][sizes: capdev]
+    CKS(dalloc(c, c->d_census, sizeof(int64_t) * (65 + 2 * (size_t)capdev)));
+    auto *base = static_cast<unsigned long long *>(c->d_census.p);
+    int64_t *d_roots = reinterpret_cast<int64_t *>(base + 65), *d_sizes = d_roots + capdev;
+    CK(diag_bubble_sizes(c->v, static_cast<const int32_t *>(c->d_labels.p),
+                         static_cast<int32_t *>(c->d_count.p), base, capdev, d_roots, d_sizes,
+                         nb, base + 1, c->s));
+    r.resize((size_t)capdev);
+    sz.resize((size_t)capdev);
+    CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(cnt.data(), base, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(h.data(), base + 1, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(r.data(), d_roots, sizeof(int64_t) * capdev, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(sz.data(), d_sizes, sizeof(int64_t) * capdev, cudaMemcpyDeviceToHost, c->s));
+    CKS(sync_and_check(c));
+    n = (int64_t)nc;
+    if (n <= capdev) break;
+    c->census_cap = n;  // more components than the list holds: grow, redo
   }
-  CKS(sync_and_check(c));
+  count_merges(c);
   if ((int64_t)cnt[0] != n) return fail(LBM_ECUDA, "bubble census: component count mismatch");
   // canonical order: increasing root label
   std::vector<int64_t> order((size_t)n);
@@ -930,6 +939,9 @@ lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
                      c->s));
   unsigned long long cnt[4];
   CK(cudaMemcpyAsync(cnt, c->d_film_counts.p, sizeof(cnt), cudaMemcpyDeviceToHost, c->s));
+  if (fired && cap > 0)  // up to cap records, copied with the counts (one synchronisation)
+    CK(cudaMemcpyAsync(fired, c->d_film_rec.p, sizeof(lbm_film_cell) * cap,
+                       cudaMemcpyDeviceToHost, c->s));
   CKS(sync_and_check(c));
   count_merges(c);
   out->film = (int64_t)cnt[0];
@@ -938,7 +950,6 @@ lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
   out->fired = (int64_t)cnt[3];
   const int64_t nrec = std::min<int64_t>(out->fired, cap);
   if (fired && nrec > 0) {
-    CK(cudaMemcpy(fired, c->d_film_rec.p, sizeof(lbm_film_cell) * nrec, cudaMemcpyDeviceToHost));
     std::sort(fired, fired + nrec, [](const lbm_film_cell &a, const lbm_film_cell &b) {
       return a.cell != b.cell ? a.cell < b.cell : a.axis < b.axis;
     });

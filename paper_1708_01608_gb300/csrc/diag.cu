@@ -17,12 +17,17 @@ namespace {
 struct Idx {
   int x, y, z;
 };
+// Lattices hold fewer than 2^31 cells (lbm_create), so cell indices and
+// their decomposition use 32-bit arithmetic: a 64-bit division is a long
+// emulated sequence on the GPU, partly on the narrow FP64 pipe.
 __device__ __forceinline__ Idx idx_of(int64_t k, const View &v) {
   Idx c;
-  c.x = (int)(k % v.NX);
-  const int64_t r = k / v.NX;
-  c.y = (int)(r % v.NY);
-  c.z = (int)(r / v.NY);
+  const uint32_t kk = (uint32_t)k, nx = (uint32_t)v.NX, ny = (uint32_t)v.NY;
+  const uint32_t r = kk / nx;
+  c.x = (int)(kk - r * nx);
+  const uint32_t zq = r / ny;
+  c.y = (int)(r - zq * ny);
+  c.z = (int)zq;
   return c;
 }
 __device__ __forceinline__ int wr(int a, int n) {
@@ -30,7 +35,7 @@ __device__ __forceinline__ int wr(int a, int n) {
   return r < 0 ? r + n : r;
 }
 __device__ __forceinline__ int64_t lin(int x, int y, int z, const View &v) {
-  return ((int64_t)z * v.NY + y) * v.NX + x;
+  return (int64_t)(((uint32_t)z * (uint32_t)v.NY + (uint32_t)y) * (uint32_t)v.NX + (uint32_t)x);
 }
 __device__ __forceinline__ int64_t sidx(int i, int x, int y, int z, const View &v) {
   return (int64_t)i * v.px * v.NY * v.NZ + ((int64_t)z * v.NY + y) * v.px + x;
@@ -554,17 +559,19 @@ __global__ void __launch_bounds__(TPB)
       const int va = v.lat == D2Q9 && ua == 1 ? 2 : ua;
       const int n_a = va == 0 ? (int)v.NX : (va == 1 ? (int)v.NY : (int)v.NZ);
       const int c_a = va == 0 ? x : (va == 1 ? y : z);
-      // periodic coordinate along the axis without an integer division
-      // (|s| <= h_max; the loops run more than once only when n_a < h_max)
+      // periodic coordinate along the axis: |s| <= h_max, so one add or
+      // subtract suffices unless the axis is shorter than h_max (tiny
+      // lattices only take the remainder)
       auto wrap_a = [&](int q) -> int {
-        while (q >= n_a) q -= n_a;
-        while (q < 0) q += n_a;
+        if (q >= n_a) q -= n_a;
+        else if (q < 0) q += n_a;
+        if ((unsigned)q >= (unsigned)n_a) q = ((q % n_a) + n_a) % n_a;
         return q;
       };
       auto cell_at = [&](int s) -> int64_t {
         const int q = wrap_a(c_a + s);
         const int xx = va == 0 ? q : x, yy = va == 1 ? q : y, zz = va == 2 ? q : z;
-        return ((int64_t)zz * v.NY + yy) * v.NX + xx;
+        return lin(xx, yy, zz, v);
       };
       auto p_at = [&](int s) -> double {
         const int q = wrap_a(c_a + s);

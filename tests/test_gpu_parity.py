@@ -603,3 +603,27 @@ def test_film_cells_3d_match_oracle(lbm):
         L.step(30)
         f = O.run(O.D3Q19, f, 30, 1.0, -5.0)
     L.close()
+
+
+def test_bubble_sizes_many_components(lbm):
+    """More components than the census list first holds: 32 x 32 x 48 with a
+    gas cell at every even (x, y, z) is 6144 isolated cells, and six gas rows
+    through the wrap add larger components; the list grows and stays
+    bit-exact."""
+    nx, ny, nz = 32, 32, 48
+    rho = np.full((nz, ny, nx), 1.8)
+    rho[::2, ::2, ::2] = 0.3
+    rho[1::8, 1, :] = 0.3          # rows along x through the wrap: 6 components of 32 cells
+    _, w = O.velocities(O.D3Q19)
+    f = w[:, None, None, None] * rho[None]
+    L = lbm.Lattice("D3Q19", nx, ny, nz, storage="f64")
+    L.write_f(f)
+    roots, sizes, hist = L.bubble_sizes(nbins=8)
+    lab_o, n_o = O.label_gas(O.D3Q19, O.moments(O.D3Q19, f)[0], 1.0)
+    r_o, s_o = O.bubble_sizes(lab_o)
+    assert n_o > 4096 and len(roots) == n_o
+    assert (roots == r_o).all() and (sizes == s_o).all()
+    assert (hist == O.size_histogram(s_o, 8)).all()
+    roots2, sizes2, _ = L.bubble_sizes(nbins=8)     # again, with the grown list
+    assert (roots2 == r_o).all() and (sizes2 == s_o).all()
+    L.close()
