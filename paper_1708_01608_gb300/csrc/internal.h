@@ -60,10 +60,13 @@ struct FusedPlan {
   int threads;
   int smem;      // dynamic shared memory bytes
   int hx;        // halo columns per box (16 bytes of elements)
+  int xc;        // cells per thread along x: 1, or 2 for the x-pair kernel
 };
 
-// Tile shapes: returns false when the id is unknown for the lattice.
-bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage);
+// Tile shapes: returns false when the id is unknown for the lattice and
+// storage.  *xc (may be NULL) receives the cells per thread along x.
+bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage,
+                      int *xc = nullptr);
 // Fill *plan for a lattice; nzc <= 0 picks the number of z chunks that
 // fills the kernel's resident CTA slots once (SMs x CTAs per SM).  Returns
 // cudaErrorInvalidValue when the tile does not fit or nx is not a multiple
@@ -94,6 +97,19 @@ cudaError_t fused_prepare(int lat, int st, const FusedPlan &plan, int *blocks_pe
 cudaError_t fused_prepare_f64(int lat, const FusedPlan &, int *blocks_per_sm);
 cudaError_t fused_prepare_f32(int lat, const FusedPlan &, int *blocks_per_sm);
 cudaError_t fused_prepare_h16(int lat, int st, const FusedPlan &, int *blocks_per_sm);
+// x-pair kernels (FP32, FP16, BF16 storage; one translation unit each)
+cudaError_t fused_x2_launch_f32(int lat, const FusedPlan &, const StepArgs &, const FusedMaps &,
+                                cudaStream_t);
+cudaError_t fused_x2_launch_f16(int lat, const FusedPlan &, const StepArgs &, const FusedMaps &,
+                                cudaStream_t);
+cudaError_t fused_x2_launch_bf16(int lat, const FusedPlan &, const StepArgs &,
+                                 const FusedMaps &, cudaStream_t);
+cudaError_t fused_x2_prepare_f32(int lat, const FusedPlan &, int *blocks_per_sm);
+cudaError_t fused_x2_prepare_f16(int lat, const FusedPlan &, int *blocks_per_sm);
+cudaError_t fused_x2_prepare_bf16(int lat, const FusedPlan &, int *blocks_per_sm);
+int fused_x2_smem_f32(int lat, int tile);
+int fused_x2_smem_f16(int lat, int tile);
+int fused_x2_smem_bf16(int lat, int tile);
 
 // two-pass path: psi field pass, then collide/stream (+ injection kernel)
 cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi_scratch, cudaStream_t s);

@@ -90,15 +90,15 @@ struct MarchArgs {
 };
 
 // Once per CTA, before its first march: the NS stage barriers and the
-// descriptor prefetch.
-template <int LAT, int ST, int BX, int BY, int NS>
-__device__ __forceinline__ void fused_barriers_init(const MarchArgs &m) {
-  using K = FusedK<LAT, ST, BX, BY, NS>;
+// descriptor prefetch.  K gives the shared-memory layout (stages, then the
+// psi ring, then the barriers).
+template <class K>
+__device__ __forceinline__ void fused_barriers_init_k(const MarchArgs &m) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * K::STAGE_BYTES + K::RING_BYTES);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + K::NS * K::STAGE_BYTES + K::RING_BYTES);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < K::NS; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
     fence_proxy_async_smem();
     prefetch_tmap(&m.tm->main);
@@ -109,6 +109,10 @@ __device__ __forceinline__ void fused_barriers_init(const MarchArgs &m) {
     }
   }
   __syncthreads();
+}
+template <int LAT, int ST, int BX, int BY, int NS>
+__device__ __forceinline__ void fused_barriers_init(const MarchArgs &m) {
+  fused_barriers_init_k<FusedK<LAT, ST, BX, BY, NS>>(m);
 }
 
 // The march of one CTA over planes zs..ze-1 of one column: TMA staging, psi
@@ -493,15 +497,10 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
   return true;
 }
 
-// One launch per time step: CTA (item) = BX x BY tile tt and z chunk zc,
-// item = zc * tiles + tt, so the CTAs resident together cover neighbouring
-// columns at the same planes (their halo rows meet in L2).
-// 256-thread tiles are register-limited to 3 CTAs per SM, the larger ones run one
-template <int LAT, int ST, int BX, int BY, int NS>
-__global__ void __launch_bounds__(BX *BY, BX *BY <= 256 ? 3 : 1)
-    fused_step_kernel(const __grid_constant__ FusedMaps tm, const StepArgs a, const int tiles_x,
-                      const int tiles_y, const int zlen) {
-  using T = typename Storage<ST>::T;
+// The march of CTA blockIdx.x of a step launch: item = zc * tiles + tt.
+__device__ __forceinline__ MarchArgs march_args_of(const FusedMaps &tm, const StepArgs &a,
+                                                   int tiles_x, int tiles_y, int zlen, int BX,
+                                                   int BY) {
   const int item = blockIdx.x;
   const int ntiles = tiles_x * tiles_y;
   const int zc = item / ntiles, tt = item % ntiles;
@@ -535,6 +534,19 @@ __global__ void __launch_bounds__(BX *BY, BX *BY <= 256 ? 3 : 1)
   m.budget = a.budget;
   m.err = a.err;
   m.debug_flags = a.debug_flags;
+  return m;
+}
+
+// One launch per time step: CTA (item) = BX x BY tile tt and z chunk zc,
+// item = zc * tiles + tt, so the CTAs resident together cover neighbouring
+// columns at the same planes (their halo rows meet in L2).
+// 256-thread tiles are register-limited to 3 CTAs per SM, the larger ones run one
+template <int LAT, int ST, int BX, int BY, int NS>
+__global__ void __launch_bounds__(BX *BY, BX *BY <= 256 ? 3 : 1)
+    fused_step_kernel(const __grid_constant__ FusedMaps tm, const StepArgs a, const int tiles_x,
+                      const int tiles_y, const int zlen) {
+  using T = typename Storage<ST>::T;
+  const MarchArgs m = march_args_of(tm, a, tiles_x, tiles_y, zlen, BX, BY);
   fused_barriers_init<LAT, ST, BX, BY, NS>(m);
   // Programmatic dependent launch: the shared-memory set-up above overlaps
   // the previous step's tail; nothing in global memory is read or written
@@ -594,6 +606,24 @@ cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const FusedMap
   X(1, 256, 1, 4)           \
   X(2, 128, 1, 4)           \
   X(3, 64, 1, 6)
+// x-pair tiles (two cells per thread, step_fused_x2.cuh; FP32 and 16-bit
+// storage only): id -> (BX, BY, NS)
+#define SCLBM_D3Q19_X2_TILES(X) \
+  X(14, 64, 8, 3)               \
+  X(15, 64, 8, 4)               \
+  X(16, 128, 4, 3)              \
+  X(17, 128, 4, 4)              \
+  X(18, 64, 4, 4)               \
+  X(19, 128, 8, 2)              \
+  X(20, 128, 8, 3)              \
+  X(21, 64, 16, 3)              \
+  X(22, 32, 8, 4)               \
+  X(23, 64, 8, 2)               \
+  X(24, 128, 4, 2)
+#define SCLBM_D2Q9_X2_TILES(X) \
+  X(4, 256, 1, 4)              \
+  X(5, 256, 1, 6)              \
+  X(6, 128, 1, 6)
 
 // Dispatch of one storage type over the tile table.
 template <int ST>

@@ -7,24 +7,40 @@
 
 namespace sclbm {
 
-bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage) {
-  (void)st;
+bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage, int *xc) {
+  int cells = 1;
 #define SCLBM_T(id, BX, BY, NS) \
   case id:                      \
     *bx = BX;                   \
     *by = BY;                   \
     *nstage = NS;               \
+    if (xc) *xc = cells;        \
     return true;
   if (lat == D3Q19) {
     switch (tile) { SCLBM_D3Q19_TILES(SCLBM_T) }
   } else {
     switch (tile) { SCLBM_D2Q9_TILES(SCLBM_T) }
   }
+  if (st == ST_F64) return false;  // the x-pair kernel computes in FP32
+  cells = 2;
+  if (lat == D3Q19) {
+    switch (tile) { SCLBM_D3Q19_X2_TILES(SCLBM_T) }
+  } else {
+    switch (tile) { SCLBM_D2Q9_X2_TILES(SCLBM_T) }
+  }
 #undef SCLBM_T
   return false;
 }
 
-static int fused_smem_bytes(int lat, int st, int tile) {
+static int fused_smem_bytes(int lat, int st, int tile, int xc) {
+  if (xc == 2) {
+    switch (st) {
+      case ST_F32: return fused_x2_smem_f32(lat, tile);
+      case ST_F16: return fused_x2_smem_f16(lat, tile);
+      case ST_BF16: return fused_x2_smem_bf16(lat, tile);
+      default: return -1;
+    }
+  }
   switch (st) {
     case ST_F64: return fused_smem_f64(lat, tile);
     case ST_F32: return fused_smem_f32(lat, tile);
@@ -34,16 +50,17 @@ static int fused_smem_bytes(int lat, int st, int tile) {
 
 cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ,
                             int nzc, FusedPlan *p) {
-  int bx, by, ns;
+  int bx, by, ns, xc;
   if (tile <= 0) tile = 1;
-  if (!fused_tile_shape(lat, st, tile, &bx, &by, &ns)) return cudaErrorInvalidValue;
+  if (!fused_tile_shape(lat, st, tile, &bx, &by, &ns, &xc)) return cudaErrorInvalidValue;
   p->tile = tile;
   p->bx = bx;
   p->by = by;
   p->nstage = ns;
-  p->threads = bx * by;
+  p->xc = xc;
+  p->threads = bx * by / xc;
   p->hx = (int)(16 / storage_bytes(st));
-  p->smem = fused_smem_bytes(lat, st, tile);
+  p->smem = fused_smem_bytes(lat, st, tile, xc);
   if (NX % p->hx != 0) return cudaErrorInvalidValue;  // halo boxes must start on 16 bytes
   int dev = 0, nsm = 0, smem_optin = 0, smem_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -125,6 +142,14 @@ CUresult fused_encode_maps(int lat, int st, const FusedPlan &p, const void *base
 
 cudaError_t fused_launch(int lat, int st, const FusedPlan &p, const StepArgs &a,
                          const FusedMaps &tm, cudaStream_t s) {
+  if (p.xc == 2) {
+    switch (st) {
+      case ST_F32: return fused_x2_launch_f32(lat, p, a, tm, s);
+      case ST_F16: return fused_x2_launch_f16(lat, p, a, tm, s);
+      case ST_BF16: return fused_x2_launch_bf16(lat, p, a, tm, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (st) {
     case ST_F64:
       return fused_launch_f64(lat, p, a, tm, s);
@@ -136,6 +161,14 @@ cudaError_t fused_launch(int lat, int st, const FusedPlan &p, const StepArgs &a,
 }
 
 cudaError_t fused_prepare(int lat, int st, const FusedPlan &p, int *blocks_per_sm) {
+  if (p.xc == 2) {
+    switch (st) {
+      case ST_F32: return fused_x2_prepare_f32(lat, p, blocks_per_sm);
+      case ST_F16: return fused_x2_prepare_f16(lat, p, blocks_per_sm);
+      case ST_BF16: return fused_x2_prepare_bf16(lat, p, blocks_per_sm);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (st) {
     case ST_F64:
       return fused_prepare_f64(lat, p, blocks_per_sm);

@@ -90,6 +90,23 @@ CASES = [
     ("D2Q9", (130, 21, 1), "f64", "two_pass", 0),
     ("D2Q9", (130, 21, 1), "f32", "auto", 0),
     ("D2Q9", (304, 37, 1), "f16", "fused", 1),
+    # x-pair tiles (two cells per thread)
+    ("D3Q19", (40, 28, 20), "f32", "fused", 14),
+    ("D3Q19", (72, 13, 9), "f32", "fused", 16),
+    ("D3Q19", (136, 12, 6), "f32", "fused", 16),
+    ("D3Q19", (36, 20, 12), "f32", "fused", 18),
+    ("D3Q19", (72, 13, 9), "f32", "fused", 23),
+    ("D3Q19", (136, 9, 5), "f32", "fused", 24),
+    ("D3Q19", (40, 28, 20), "f32", "fused", 22),
+    ("D3Q19", (40, 28, 20), "f16", "fused", 15),
+    ("D3Q19", (40, 20, 12), "f16", "fused", 17),
+    ("D3Q19", (72, 40, 9), "f16", "fused", 21),
+    ("D3Q19", (136, 12, 6), "f16", "fused", 19),
+    ("D3Q19", (40, 28, 20), "f16", "fused", 20),
+    ("D3Q19", (40, 28, 20), "bf16", "fused", 14),
+    ("D2Q9", (300, 37, 1), "f32", "fused", 4),
+    ("D2Q9", (132, 21, 1), "f32", "fused", 6),
+    ("D2Q9", (304, 37, 1), "f16", "fused", 5),
 ]
 
 
@@ -135,6 +152,31 @@ def test_tiny_and_degenerate_lattices(lbm, lat, ext, kernel):
     L.step(7)
     fo = O.run(LAT[lat], f0, 7, 0.8, -5.0)
     assert rel_err(L.read("f"), fo) < 1e-12
+    L.close()
+
+
+@pytest.mark.parametrize("lat,ext,tile", [("D3Q19", (4, 1, 5), 14), ("D3Q19", (8, 2, 1), 22),
+                                          ("D3Q19", (4, 9, 2), 18), ("D3Q19", (36, 9, 3), 16),
+                                          ("D3Q19", (68, 3, 4), 14), ("D2Q9", (4, 7, 1), 4),
+                                          ("D2Q9", (260, 3, 1), 5)])
+def test_x_pair_tiles_small_lattices(lbm, lat, ext, tile):
+    """x-pair tiles on lattices narrower than a tile, one-cell extents and a
+    second tile holding a single pair column: random FP32 offsets against
+    the oracle from the same stored values."""
+    nx, ny, nz = ext
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
+    q = 19 if lat == "D3Q19" else 9
+    c, w = O.velocities(LAT[lat])
+    rho = rng.uniform(0.1, 2.0, size=(nz, ny, nx))
+    f0 = w[:, None, None, None] * rho[None] * rng.uniform(0.9, 1.1, size=(q, nz, ny, nx))
+    f0 = as_stored(lat, f0, "f32", 1.0)
+    L = lbm.Lattice(lat, nx, ny, nz, tau=0.8, G=-5.0, storage="f32", kernel="fused", tile=tile,
+                    rho_ref=1.0)
+    assert L.plan()[1] == tile
+    L.write_f(f0)
+    L.step(7)
+    fo = O.run(LAT[lat], f0, 7, 0.8, -5.0)
+    assert rel_err(L.read("f"), fo) < 1e-5, rel_err(L.read("f"), fo)
     L.close()
 
 
