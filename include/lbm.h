@@ -176,14 +176,15 @@ lbm_status lbm_read_budgets(lbm_ctx *ctx, double *budget, int32_t n);
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* Autotuner: time every fused-kernel tile that fits this lattice and storage,
- * each with the one-wave number of z chunks, half and double it (two
- * warm-up steps, then the best of two rounds of `steps` timed steps,
- * starting from the current state), and keep the fastest for later lbm_step
- * calls.  The
- * populations, budgets and step counter are restored afterwards, so the
- * call has no effect on results.  *best_tile and *best_ms (either may be
- * NULL) receive the chosen tile id and its time per step.  Errors: ESTATE
- * (not seeded), EINVAL (two-pass context, steps < 1), ENOMEM, ECUDA. */
+ * each with the planned number of z chunks (fewest staged planes per CTA
+ * slot when CTAs run in waves), half and double it, and the number that
+ * fills the resident CTA slots once (two warm-up steps, then the best of
+ * two rounds of `steps` timed steps, starting from the current state), and
+ * keep the fastest for later lbm_step calls.  The populations, budgets and
+ * step counter are restored afterwards, so the call has no effect on
+ * results.  *best_tile and *best_ms (either may be NULL) receive the chosen
+ * tile id and its time per step.  Errors: ESTATE (not seeded), EINVAL
+ * (two-pass context, steps < 1), ENOMEM, ECUDA. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *best_tile, double *best_ms);
 
 /* Launch plan of the step kernel: out = {kernel (lbm_kernel), tile id,

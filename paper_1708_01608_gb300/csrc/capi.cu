@@ -590,23 +590,34 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best_tile, double *b
     CK(cudaEventCreate(&e1));
     FusedPlan best{};
     float best_t = 1e30f;
-    for (int cand = 0; cand < 64 * 3; ++cand) {
-      // every tile, with the one-wave number of z chunks, half and double it
-      const int tile = 1 + cand / 3, variant = cand % 3;
+    for (int cand = 0; cand < 64 * 4; ++cand) {
+      // every tile, with the modelled number of z chunks, half and double
+      // it, and the number that fills the resident slots once
+      const int tile = 1 + cand / 4, variant = cand % 4;
       int bx, by, ns;
       if (!fused_tile_shape(c->lat, c->st, tile, &bx, &by, &ns)) continue;
-      FusedPlan p;
-      if (fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, 0, &p) != cudaSuccess) {
+      FusedPlan p, p1;
+      if (fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, 0, &p) != cudaSuccess ||
+          fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, -1, &p1) !=
+              cudaSuccess) {
         cudaGetLastError();
         continue;
       }
       if (variant > 0) {
-        const int nzc = variant == 1 ? std::max(1, p.nzc / 2) : p.nzc * 2;
-        if (nzc == p.nzc || nzc > c->v.NZ) continue;
-        if (fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, nzc, &p) != cudaSuccess) {
+        const int nzc = variant == 1 ? std::max(1, p.nzc / 2)
+                        : variant == 2 ? p.nzc * 2
+                                       : p1.nzc;
+        if (nzc > c->v.NZ) continue;
+        FusedPlan q;
+        if (fused_make_plan(c->lat, c->st, tile, c->v.NX, c->v.NY, c->v.NZ, nzc, &q) != cudaSuccess) {
           cudaGetLastError();
           continue;
         }
+        // skip chunkings an earlier variant of this tile already timed
+        const int n1 = std::max(1, p.nzc / 2), n2 = p.nzc * 2;
+        if (q.nzc == p.nzc || (variant >= 2 && q.nzc == n1) || (variant == 3 && q.nzc == n2))
+          continue;
+        p = q;
       }
       CKS(use_plan(c, p));
       CKS(lbm_step(c, 2));

@@ -67,8 +67,9 @@ struct FusedPlan {
 // storage.  *xc (may be NULL) receives the cells per thread along x.
 bool fused_tile_shape(int lat, int st, int tile, int *bx, int *by, int *nstage,
                       int *xc = nullptr);
-// Fill *plan for a lattice; nzc <= 0 picks the number of z chunks that
-// fills the kernel's resident CTA slots once (SMs x CTAs per SM).  Returns
+// Fill *plan for a lattice.  nzc > 0: that many z chunks; 0: the number
+// with the fewest staged planes per resident CTA slot when the CTAs run in
+// waves of SMs x CTAs per SM; -1: as many as fill those slots once.  Returns
 // cudaErrorInvalidValue when the tile does not fit or nx is not a multiple
 // of the 16-byte halo width.
 cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, int64_t NZ,

@@ -73,16 +73,31 @@ cudaError_t fused_make_plan(int lat, int st, int tile, int64_t NX, int64_t NY, i
   p->tiles_y = (int)((NY + by - 1) / by);
   const int ntiles = p->tiles_x * p->tiles_y;
   if (nzc <= 0) {
-    // one wave: as many z chunks as keep every resident slot busy (the
-    // kernel's occupancy: registers, shared memory and threads)
+    // resident CTA slots: SMs x the kernel's occupancy (registers, shared
+    // memory and threads)
     int per_sm = 0;
     if (fused_prepare(lat, st, *p, &per_sm) != cudaSuccess || per_sm < 1) {
       cudaGetLastError();
       per_sm = std::max(1, std::min(smem_sm / (p->smem + 1024), 2048 / p->threads));
     }
-    const int slots = nsm * per_sm;
-    nzc = std::max(1, slots / std::max(1, ntiles));
-    nzc = (int)std::min<int64_t>(nzc, std::max<int64_t>(1, NZ / 4));
+    // Time model: CTAs run in waves of `slots`, a chunk of zlen planes
+    // stages zlen + 2; pick the number of chunks (at least 4 planes each)
+    // with the fewest staged planes per slot, the smaller one on ties.
+    const int64_t slots = (int64_t)nsm * per_sm;
+    const int64_t max_nzc = std::max<int64_t>(1, NZ / 4);
+    int64_t best_cost = INT64_MAX;
+    if (nzc < 0)  // one wave: as many chunks as fill every slot once
+      best_cost = 0, nzc = (int)std::min<int64_t>(std::max<int64_t>(1, slots / ntiles), max_nzc);
+    for (int64_t c = 1; c <= max_nzc && best_cost > 0; ++c) {
+      const int64_t zl = (NZ + c - 1) / c;
+      const int64_t n = (NZ + zl - 1) / zl;  // chunks actually formed
+      const int64_t waves = (ntiles * n + slots - 1) / slots;
+      const int64_t cost = waves * (zl + 2);
+      if (cost < best_cost) {
+        best_cost = cost;
+        nzc = (int)n;
+      }
+    }
   }
   nzc = (int)std::min<int64_t>(std::max(nzc, 1), NZ);
   p->zlen = (int)((NZ + nzc - 1) / nzc);
