@@ -42,6 +42,10 @@ struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
 };
+struct PinBuf {  // pinned host memory
+  void *p = nullptr;
+  size_t bytes = 0;
+};
 
 }  // namespace
 
@@ -81,9 +85,39 @@ struct lbm_ctx {
   std::vector<int32_t> site_labels, prev_site_labels;
   bool have_prev = false;
   int64_t merge_events = 0;
+  // Pinned host memory for results read back after a call's one stream
+  // synchronisation: the status word, the site labels of the last labelling
+  // (copied to site_labels at that synchronisation) and a mailbox for the
+  // results of one call.  Pageable targets would make each copy a staged,
+  // serialising transfer.
+  PinBuf h_err, h_site, h_mail;
+  bool site_pending = false;
 };
 
 namespace {
+
+void hfree(PinBuf &b) {
+  if (b.p) cudaFreeHost(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// grow a pinned host buffer (the stream is drained first: no copy may still
+// target the old one)
+lbm_status halloc(lbm_ctx *c, PinBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.p && b.bytes >= bytes) return LBM_OK;
+  if (b.p) cudaStreamSynchronize(c->s);
+  hfree(b);
+  void *p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LBM_ENOMEM, "pinned host allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  b.p = p;
+  b.bytes = bytes;
+  return LBM_OK;
+}
 
 void dfree(lbm_ctx *c, DevBuf &b) {
   if (!b.p) return;
@@ -149,16 +183,23 @@ lbm_status check_sticky(lbm_ctx *c) {
 
 // Read and clear nothing: report the device status word after a sync.
 lbm_status sync_and_check(lbm_ctx *c) {
+  CKS(halloc(c, c->h_err, sizeof(int)));
+  int *herr = static_cast<int *>(c->h_err.p);
+  CK(cudaMemcpyAsync(herr, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
-  int err = 0;
-  CK(cudaMemcpy(&err, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  const int err = *herr;
+  if (c->site_pending) {
+    const int32_t *hs = static_cast<const int32_t *>(c->h_site.p);
+    c->site_labels.assign(hs, hs + c->sx.size());
+    c->site_pending = false;
+  }
   if (err & ERR_TMA_TIMEOUT) {
     c->sticky = LBM_ETIMEOUT;
     return fail(LBM_ETIMEOUT, "a step kernel gave up waiting for a TMA transfer");
   }
   if (err & ERR_NONFINITE) {
-    const int zero = 0;
-    CK(cudaMemcpy(c->d_err.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), c->s));
+    CK(cudaStreamSynchronize(c->s));
     return fail(LBM_ENUMERIC, "non-finite density found");
   }
   return LBM_OK;
@@ -331,6 +372,9 @@ void lbm_destroy(lbm_ctx *c) {
                     &c->d_count, &c->d_census, &c->d_film_state, &c->d_film_counts,
                     &c->d_film_rec};
   for (DevBuf *b : bufs) dfree(c, *b);
+  hfree(c->h_err);
+  hfree(c->h_site);
+  hfree(c->h_mail);
   delete c;
 }
 
@@ -416,6 +460,7 @@ lbm_status lbm_seed_bubbles(lbm_ctx *c, const lbm_bubble *b, int32_t n, double r
   c->merge_events = 0;
   c->film_state_clear = false;
   c->p_valid = c->labels_valid = false;
+  c->site_pending = false;
   c->site_labels.assign(n, -1);
   CK(cudaStreamSynchronize(c->s));  // host staging buffers go out of scope
   return LBM_OK;
@@ -731,9 +776,10 @@ static lbm_status enqueue_labels(lbm_ctx *c, bool want_totals) {
     CKS(dalloc(c, c->d_site_lab, sizeof(int32_t) * ns));
     CK(diag_gather_labels(lab, static_cast<const int32_t *>(c->d_cells.p), ns,
                           static_cast<int32_t *>(c->d_site_lab.p), c->s));
-    c->site_labels.resize(ns);
-    CK(cudaMemcpyAsync(c->site_labels.data(), c->d_site_lab.p, sizeof(int32_t) * ns,
+    CKS(halloc(c, c->h_site, sizeof(int32_t) * ns));
+    CK(cudaMemcpyAsync(c->h_site.p, c->d_site_lab.p, sizeof(int32_t) * ns,
                        cudaMemcpyDeviceToHost, c->s));
+    c->site_pending = true;  // copied to site_labels at the next synchronisation
   }
   c->labels_valid = true;
   return LBM_OK;
@@ -788,8 +834,9 @@ lbm_status lbm_film_probe(lbm_ctx *c, const int64_t *line, double rho_mid, lbm_f
   CK(diag_film_probe(c->v, static_cast<const double *>(c->d_rho.p),
                      static_cast<const double *>(c->d_p.p), wrap64(x0, c->v.NX), wrap64(y0, c->v.NY),
                      wrap64(z0, c->v.NZ), e, ep, line[4], rho_mid, tmp, c->s));
-  double h[6];
-  CK(cudaMemcpyAsync(h, tmp, sizeof(h), cudaMemcpyDeviceToHost, c->s));
+  CKS(halloc(c, c->h_mail, 6 * sizeof(double)));
+  const double *h = static_cast<const double *>(c->h_mail.p);
+  CK(cudaMemcpyAsync(c->h_mail.p, tmp, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
   CKS(sync_and_check(c));
   out->found = h[0] != 0.0;
   out->x1 = h[1];
@@ -844,12 +891,13 @@ lbm_status lbm_label_gas(lbm_ctx *c, int32_t *labels, int64_t *ncomp) {
   CKS(set_device(c));
   CKS(check_sticky(c));
   CKS(enqueue_labels(c, false));
-  unsigned long long nc = 0;
-  CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
+  CKS(halloc(c, c->h_mail, sizeof(unsigned long long)));
+  const auto *nc = static_cast<const unsigned long long *>(c->h_mail.p);
+  CK(cudaMemcpyAsync(c->h_mail.p, c->d_ncomp.p, sizeof(*nc), cudaMemcpyDeviceToHost, c->s));
   if (labels)
     CK(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost, c->s));
   CKS(sync_and_check(c));
-  if (ncomp) *ncomp = (int64_t)nc;
+  if (ncomp) *ncomp = (int64_t)*nc;
   count_merges(c);
   return LBM_OK;
 }
@@ -860,13 +908,17 @@ lbm_status lbm_diagnose(lbm_ctx *c, double totals[4], int32_t *labels, int64_t *
   CKS(set_device(c));
   CKS(check_sticky(c));
   CKS(enqueue_labels(c, totals != nullptr));
-  unsigned long long nc = 0;
-  CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
-  if (totals) CK(cudaMemcpyAsync(totals, c->d_tot.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  // mailbox: [ncomp][totals: 4 doubles]
+  CKS(halloc(c, c->h_mail, 5 * sizeof(double)));
+  auto *mail = static_cast<unsigned char *>(c->h_mail.p);
+  CK(cudaMemcpyAsync(mail, c->d_ncomp.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+  if (totals)
+    CK(cudaMemcpyAsync(mail + 8, c->d_tot.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
   if (labels)
     CK(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost, c->s));
   CKS(sync_and_check(c));
-  if (ncomp) *ncomp = (int64_t)nc;
+  if (totals) std::memcpy(totals, mail + 8, 4 * sizeof(double));
+  if (ncomp) *ncomp = (int64_t)*reinterpret_cast<const unsigned long long *>(mail);
   count_merges(c);
   return LBM_OK;
 }
@@ -885,33 +937,34 @@ lbm_status lbm_bubble_sizes(lbm_ctx *c, int64_t *roots, int64_t *sizes, int64_t 
   // One synchronisation in the common case: the list is written up to the
   // device capacity, which grows (and the list is redone) when a lattice has
   // more components than ever before.
-  unsigned long long nc = 0;
-  std::vector<int64_t> r, sz;
-  std::vector<unsigned long long> h((size_t)nb), cnt(1);
+  const unsigned long long *mail = nullptr;
+  const int64_t *r = nullptr, *sz = nullptr;
   int64_t n = 0;
   for (int pass = 0; pass < 2; ++pass) {
     const int64_t capdev = c->census_cap;
-    // [n_dev][hist: 64][roots: capdev][sizes: capdev]
-    CKS(dalloc(c, c->d_census, sizeof(int64_t) * (65 + 2 * (size_t)capdev)));
+    // device block and mailbox: [n_dev][hist: 64][roots: capdev][sizes: capdev];
+    // the mailbox has the labelling's component count after it
+    const size_t block = sizeof(int64_t) * (65 + 2 * (size_t)capdev);
+    CKS(dalloc(c, c->d_census, block));
+    CKS(halloc(c, c->h_mail, block + sizeof(unsigned long long)));
     auto *base = static_cast<unsigned long long *>(c->d_census.p);
     int64_t *d_roots = reinterpret_cast<int64_t *>(base + 65), *d_sizes = d_roots + capdev;
     CK(diag_bubble_sizes(c->v, static_cast<const int32_t *>(c->d_labels.p),
                          static_cast<int32_t *>(c->d_count.p), base, capdev, d_roots, d_sizes,
                          nb, base + 1, c->s));
-    r.resize((size_t)capdev);
-    sz.resize((size_t)capdev);
-    CK(cudaMemcpyAsync(&nc, c->d_ncomp.p, sizeof(nc), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(cnt.data(), base, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(h.data(), base + 1, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(r.data(), d_roots, sizeof(int64_t) * capdev, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(sz.data(), d_sizes, sizeof(int64_t) * capdev, cudaMemcpyDeviceToHost, c->s));
+    mail = static_cast<const unsigned long long *>(c->h_mail.p);
+    CK(cudaMemcpyAsync(c->h_mail.p, base, block, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(static_cast<unsigned char *>(c->h_mail.p) + block, c->d_ncomp.p,
+                       sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
     CKS(sync_and_check(c));
-    n = (int64_t)nc;
+    n = (int64_t)mail[block / sizeof(unsigned long long)];
+    r = reinterpret_cast<const int64_t *>(mail + 65);
+    sz = r + capdev;
     if (n <= capdev) break;
     c->census_cap = n;  // more components than the list holds: grow, redo
   }
   count_merges(c);
-  if ((int64_t)cnt[0] != n) return fail(LBM_ECUDA, "bubble census: component count mismatch");
+  if ((int64_t)mail[0] != n) return fail(LBM_ECUDA, "bubble census: component count mismatch");
   // canonical order: increasing root label
   std::vector<int64_t> order((size_t)n);
   for (int64_t q = 0; q < n; ++q) order[q] = q;
@@ -922,7 +975,7 @@ lbm_status lbm_bubble_sizes(lbm_ctx *c, int64_t *roots, int64_t *sizes, int64_t 
   }
   if (ncomp) *ncomp = n;
   if (hist)
-    for (int b = 0; b < nbins; ++b) hist[b] = (int64_t)h[b];
+    for (int b = 0; b < nbins; ++b) hist[b] = (int64_t)mail[1 + b];
   return LBM_OK;
 }
 
@@ -948,19 +1001,24 @@ lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
                      static_cast<uint8_t *>(c->d_film_state.p),
                      static_cast<unsigned long long *>(c->d_film_counts.p), cap, c->d_film_rec.p,
                      c->s));
-  unsigned long long cnt[4];
-  CK(cudaMemcpyAsync(cnt, c->d_film_counts.p, sizeof(cnt), cudaMemcpyDeviceToHost, c->s));
-  if (fired && cap > 0)  // up to cap records, copied with the counts (one synchronisation)
-    CK(cudaMemcpyAsync(fired, c->d_film_rec.p, sizeof(lbm_film_cell) * cap,
-                       cudaMemcpyDeviceToHost, c->s));
+  // mailbox: [counts: 4][up to cap records], one synchronisation
+  const size_t rec_bytes = fired ? sizeof(lbm_film_cell) * (size_t)cap : 0;
+  CKS(halloc(c, c->h_mail, 4 * sizeof(unsigned long long) + rec_bytes));
+  auto *mail = static_cast<unsigned char *>(c->h_mail.p);
+  CK(cudaMemcpyAsync(mail, c->d_film_counts.p, 4 * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, c->s));
+  if (rec_bytes)
+    CK(cudaMemcpyAsync(mail + 32, c->d_film_rec.p, rec_bytes, cudaMemcpyDeviceToHost, c->s));
   CKS(sync_and_check(c));
   count_merges(c);
+  const auto *cnt = reinterpret_cast<const unsigned long long *>(mail);
   out->film = (int64_t)cnt[0];
   out->midpoints = (int64_t)cnt[1];
   out->armed = (int64_t)cnt[2];
   out->fired = (int64_t)cnt[3];
   const int64_t nrec = std::min<int64_t>(out->fired, cap);
   if (fired && nrec > 0) {
+    std::memcpy(fired, mail + 32, sizeof(lbm_film_cell) * (size_t)nrec);
     std::sort(fired, fired + nrec, [](const lbm_film_cell &a, const lbm_film_cell &b) {
       return a.cell != b.cell ? a.cell < b.cell : a.axis < b.axis;
     });
@@ -991,8 +1049,11 @@ lbm_status lbm_totals(lbm_ctx *c, double out[4]) {
   else
     CK(diag_totals(c->v, lattice_ptr(c, c->cur), static_cast<double *>(c->d_part.p),
                    static_cast<double *>(c->d_tot.p), c->s));
-  CK(cudaMemcpyAsync(out, c->d_tot.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
-  return sync_and_check(c);
+  CKS(halloc(c, c->h_mail, 4 * sizeof(double)));
+  CK(cudaMemcpyAsync(c->h_mail.p, c->d_tot.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  CKS(sync_and_check(c));
+  std::memcpy(out, c->h_mail.p, 4 * sizeof(double));
+  return LBM_OK;
 }
 
 lbm_status lbm_read(lbm_ctx *c, int32_t field, double *dst, size_t bytes) {

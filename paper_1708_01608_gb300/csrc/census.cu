@@ -17,10 +17,14 @@ inline int grid_of(int64_t n) {
        k += (int64_t)gridDim.x * blockDim.x)
 
 // ---- bubble sizes -----------------------------------------------------------
+// Cells per root.  A warp reads 32 consecutive cells of a row, which inside
+// a bubble share one label: the lanes of equal labels add their number once,
+// so that a large bubble does not serialise on one counter.
 __global__ void k_size_count(int64_t N, const int32_t *labels, int32_t *count) {
   CENSUS_LOOP(k, N) {
     const int32_t l = labels[k];
-    if (l >= 0) atomicAdd(&count[l], 1);
+    const unsigned peers = __match_any_sync(__activemask(), l);
+    if (l >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[l], __popc(peers));
   }
 }
 

@@ -366,17 +366,20 @@ __global__ void __launch_bounds__(TPB) k_totals_final(const double *part, double
 }
 
 // ---- one pass for the diagnostic interval (FP32-arithmetic storages) -------
-// Per cell, the offsets g_i are summed with an error-free FP32 transformation
-// (TwoSum, Knuth TAOCP vol. 2, 4.2.2): the pair (hi, lo) holds sum g exactly
-// up to FP32 underflow, and hi + lo is added to a per-thread FP64
-// accumulator; threads and blocks are combined in FP64 in a fixed order, so
-// the mass (N rho_ref + sum of offsets) is an FP64 reduction that repeated
-// calls reproduce bit for bit.  Momentum (sum g c_i; the w_i rho_ref part
-// cancels) is reduced the same way.
+// The offsets g_i are summed with an error-free FP32 transformation (TwoSum,
+// Knuth TAOCP vol. 2, 4.2.2) into a per-thread pair (hi, lo): every addition
+// to hi is exact, its rounding error goes to lo.  Every SCAN_FLUSH cells
+// hi + lo is added to the thread's FP64 accumulator (FP64 is a narrow pipe
+// on this part: two FP64 operations per cell instead of sixteen); threads
+// and blocks are combined in FP64 in a fixed order, so the mass
+// (N rho_ref + sum of offsets) is an FP64 reduction that repeated calls
+// reproduce bit for bit.  Momentum (sum g c_i; the w_i rho_ref part cancels)
+// is reduced the same way.
 // The gas decision rho < threshold is taken in FP64, exactly as the FP64
 // moments of the decoded populations would take it, whenever the FP32
 // density is within 1e-5 of the threshold; elsewhere hi decides.
 constexpr int SCAN_BLOCKS = 1024;
+constexpr int SCAN_FLUSH = 8;
 __device__ __forceinline__ void two_sum(float &hi, float &lo, float x) {
   const float s = hi + x;
   const float bp = s - hi;
@@ -396,24 +399,27 @@ __global__ void __launch_bounds__(TPB) k_scan(const View v, const void *stored, 
   const T *f = static_cast<const T *>(stored);
   const float rho_ref = (float)v.rho_ref, thr_f = (float)thr;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+  int pending = 0;
   bool bad = false;
   for (int64_t k = blockIdx.x * (int64_t)TPB + threadIdx.x; k < N;
        k += (int64_t)SCAN_BLOCKS * TPB) {
     const Idx c = idx_of(k, v);
     const int64_t o = ((int64_t)c.z * v.NY + c.y) * v.px + c.x;
     float g[L::Q];
-    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    float cell = 0.0f;  // the cell's FP32 offset sum, for the gas decision
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       g[i] = S::load(f[i * pop + o]);
+      cell += g[i];
       two_sum(hi[0], lo[0], g[i]);
       if (L::cx(i) != 0) two_sum(hi[1], lo[1], L::cx(i) > 0 ? g[i] : -g[i]);
       if (L::cy(i) != 0) two_sum(hi[2], lo[2], L::cy(i) > 0 ? g[i] : -g[i]);
       if (L::cz(i) != 0) two_sum(hi[3], lo[3], L::cz(i) > 0 ? g[i] : -g[i]);
     }
-    if (!isfinite(hi[0])) bad = true;
+    if (!isfinite(cell)) bad = true;
     if (labels) {
-      const float r32 = rho_ref + hi[0];
+      const float r32 = rho_ref + cell;
       bool gas;
       if (fabsf(r32 - thr_f) > 1e-5f) {
         gas = r32 < thr_f;
@@ -425,9 +431,17 @@ __global__ void __launch_bounds__(TPB) k_scan(const View v, const void *stored, 
       }
       labels[k] = gas ? (int32_t)k : -1;
     }
+    if (++pending == SCAN_FLUSH) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += (double)hi[q] + (double)lo[q];
+      for (int q = 0; q < 4; ++q) {
+        acc[q] += (double)hi[q] + (double)lo[q];
+        hi[q] = lo[q] = 0.0f;
+      }
+      pending = 0;
+    }
   }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] += (double)hi[q] + (double)lo[q];
   if (bad && err) atomicOr(err, ERR_NONFINITE);
   if (!part) return;
 #pragma unroll

@@ -233,6 +233,10 @@ struct lbm_ensemble {
   int64_t launches = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // pinned host copies of the step counter and the domain states, so that
+  // an interval's two transfers are plain asynchronous copies
+  int64_t *h_step = nullptr;
+  EnsState *h_state = nullptr;
 };
 
 namespace {
@@ -382,12 +386,14 @@ lbm_status ens_interval(lbm_ensemble *E) {
   for (int d = 0; d < E->n; ++d)
     if (E->hstate[d].active) cells += (double)E->hdom[d].NX * E->hdom[d].NZ;
   const int64_t now = E->steps + E->diag_every;
-  ECK(cudaMemcpyAsync(E->d_step, &now, sizeof(now), cudaMemcpyHostToDevice, E->s));
+  *E->h_step = now;
+  ECK(cudaMemcpyAsync(E->d_step, E->h_step, sizeof(now), cudaMemcpyHostToDevice, E->s));
   ECKS(ensure_graph(E));
   ECK(cudaGraphLaunch(E->exec, E->s));
-  ECK(cudaMemcpyAsync(E->hstate.data(), E->d_state, sizeof(EnsState) * E->n,
-                      cudaMemcpyDeviceToHost, E->s));
+  ECK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(EnsState) * E->n, cudaMemcpyDeviceToHost,
+                      E->s));
   ECK(cudaStreamSynchronize(E->s));
+  std::copy(E->h_state, E->h_state + E->n, E->hstate.begin());
   E->steps = now;
   E->updates += cells * E->diag_every;
   int ncls = 0;
@@ -441,6 +447,13 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
     cudaGetLastError();
     lbm_ensemble_destroy(E);
     return efail(LBM_ECUDA, "ensemble: stream creation failed");
+  }
+  if (cudaMallocHost(reinterpret_cast<void **>(&E->h_step), sizeof(int64_t)) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void **>(&E->h_state), sizeof(EnsState) * (size_t)n) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    lbm_ensemble_destroy(E);
+    return efail(LBM_ENOMEM, "ensemble: pinned host allocation failed");
   }
   // arena layout
   std::vector<size_t> off(n);
@@ -594,6 +607,8 @@ void lbm_ensemble_destroy(lbm_ensemble *E) {
   }
   if (E->fork) cudaEventDestroy(E->fork);
   if (E->s) cudaStreamDestroy(E->s);
+  if (E->h_step) cudaFreeHost(E->h_step);
+  if (E->h_state) cudaFreeHost(E->h_state);
   cudaGetLastError();
   delete E;
 }

@@ -235,6 +235,8 @@ class Lattice:
             cfg.alloc, cfg.free = self._mem.alloc, self._mem.free
         cfg.stream = stream or None
         self.cfg = cfg
+        self._census_buf = (np.empty(4096, np.int64), np.empty(4096, np.int64))
+        self._film_buf = np.empty(0, dtype=FILM_CELL)
         self.q = 9 if cfg.lattice == D2Q9 else 19
         self.shape = (cfg.nz, cfg.ny, cfg.nx)
         self.n = cfg.nx * cfg.ny * cfg.nz
@@ -381,24 +383,35 @@ class Lattice:
     def bubble_sizes(self, nbins=32, cap=1 << 20):
         """Label the gas and measure its components (lbm_bubble_sizes):
         (roots, sizes) in increasing root order and the log2 size histogram."""
-        roots = np.zeros(max(cap, 1), dtype=np.int64)
-        sizes = np.zeros(max(cap, 1), dtype=np.int64)
+        # The output arrays are kept between calls (large allocations are
+        # costly at every diagnostic interval) and grown, with the call
+        # repeated, when the lattice has more components than they hold.
         hist = np.zeros(max(nbins, 1), dtype=np.int64)
         nc = C.c_int64(0)
-        _check(_lib.lbm_bubble_sizes(self._h, _ptr(roots), _ptr(sizes), int(cap), C.byref(nc),
-                                     _ptr(hist), int(nbins)))
-        n = min(int(nc.value), cap)
-        return roots[:n], sizes[:n], hist[:nbins]
+        while True:
+            buf = self._census_buf
+            room = min(int(cap), len(buf[0]))
+            _check(_lib.lbm_bubble_sizes(self._h, _ptr(buf[0]), _ptr(buf[1]), room, C.byref(nc),
+                                         _ptr(hist), int(nbins)))
+            n = int(nc.value)
+            if n <= room or room >= cap:
+                break
+            grow = min(int(cap), 2 * n)
+            self._census_buf = (np.empty(grow, np.int64), np.empty(grow, np.int64))
+        n = min(n, room)
+        return buf[0][:n].copy(), buf[1][:n].copy(), hist[:nbins]
 
     def film_cells(self, h_max=12, eps_arm=1e-3, cap=1 << 16):
         """The film test at every lattice point (lbm_film_cells): (counts
         dict, fired records as a FILM_CELL array in (cell, axis) order)."""
         out = FilmCensus()
-        rec = np.zeros(max(cap, 1), dtype=FILM_CELL)
+        if len(self._film_buf) < max(cap, 1):  # kept between calls, as for the census
+            self._film_buf = np.empty(max(cap, 1), dtype=FILM_CELL)
+        rec = self._film_buf
         _check(_lib.lbm_film_cells(self._h, int(h_max), float(eps_arm), C.byref(out), _ptr(rec),
                                    int(cap)))
         return (dict(film=out.film, midpoints=out.midpoints, armed=out.armed, fired=out.fired),
-                rec[:min(out.fired, cap)])
+                rec[:min(out.fired, cap)].copy())
 
     def totals(self):
         out = np.zeros(4)
