@@ -51,10 +51,11 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.8e6,
                           ("d3q19_foam_128", "f32", 5): 277.5e6,
                           ("d3q19_foam_128", "f32", 16): 277.35e6,
+                          ("d3q19_foam_128", "f32", 25): 277.57e6,
                           ("d3q19_foam_512", "f16", 14): 8 * 1270.09e6,
                           ("d3q19_foam_768", "f16", 14): 27 * 1270.09e6}
 # D3Q19 tile ids of the x-pair kernel (fused_step_kernel_x2)
-X_PAIR_TILES = range(14, 25)
+X_PAIR_TILES = range(14, 26)
 
 
 def peak_hbm():

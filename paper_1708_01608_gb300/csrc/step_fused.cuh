@@ -619,7 +619,8 @@ cudaError_t fused_launch_t(const FusedPlan &p, const StepArgs &a, const FusedMap
   X(21, 64, 16, 3)              \
   X(22, 32, 8, 4)               \
   X(23, 64, 8, 2)               \
-  X(24, 128, 4, 2)
+  X(24, 128, 4, 2)              \
+  X(25, 64, 7, 3)
 #define SCLBM_D2Q9_X2_TILES(X) \
   X(4, 256, 1, 4)              \
   X(5, 256, 1, 6)              \

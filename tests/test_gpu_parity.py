@@ -104,6 +104,8 @@ CASES = [
     ("D3Q19", (136, 12, 6), "f16", "fused", 19),
     ("D3Q19", (40, 28, 20), "f16", "fused", 20),
     ("D3Q19", (40, 28, 20), "bf16", "fused", 14),
+    ("D3Q19", (72, 16, 7), "f32", "fused", 25),
+    ("D3Q19", (136, 23, 9), "f16", "fused", 25),
     ("D2Q9", (300, 37, 1), "f32", "fused", 4),
     ("D2Q9", (132, 21, 1), "f32", "fused", 6),
     ("D2Q9", (304, 37, 1), "f16", "fused", 5),
