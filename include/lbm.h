@@ -319,6 +319,34 @@ typedef struct {
 lbm_status lbm_film_cells(lbm_ctx *ctx, int32_t h_max, double eps_arm, lbm_film_census *out,
                           lbm_film_cell *fired, int64_t cap);
 
+/* The same film test (same arming state, same census), reported per pair
+ * of bubbles that meet in a film: the criterion "at each lattice point" of
+ * a foam (Sec. 4) gives each pair's film disc and critical thickness, the
+ * two quantities of Fig. 3.  For a pair (gas labels label_a < label_b) and a
+ * lattice axis, the lines along the axis holding a film midpoint of the
+ * pair are its film's area in cells (a film of even thickness has two
+ * midpoints on a line).  The pair's film lies across the axis with the most
+ * lines (the lower axis on a tie); r_d = sqrt(lines / pi) in 3-D, lines / 2
+ * in 2-D; h_min is the thinnest liquid run there.  fired counts the pair's
+ * midpoints whose criterion fired in this call (any axis) and h_c is their
+ * mean thickness (0 when none fired).  pairs[q] for q < min(*npairs, cap),
+ * in increasing (label_a, label_b) order; *npairs (may be NULL) = all pairs.
+ * Use either this call or lbm_film_cells per diagnostic interval: each
+ * advances the arming state.  Synchronous.  Errors: EINVAL, ESTATE, ENOMEM,
+ * ECUDA. */
+typedef struct {
+  int32_t label_a, label_b; /* the two bubbles, label_a < label_b */
+  int32_t axis;             /* 0, 1, 2: the axis the film lies across */
+  int32_t h_min;            /* thinnest liquid run of the film along axis */
+  int64_t lines;            /* lattice lines along axis through the film */
+  int64_t midpoints;        /* film midpoints of the pair along axis */
+  int64_t fired;            /* midpoints of the pair that fired in this call */
+  double r_d;               /* film disc radius */
+  double h_c;               /* mean thickness of the fired midpoints */
+} lbm_film_pair;
+lbm_status lbm_film_pairs(lbm_ctx *ctx, int32_t h_max, double eps_arm, lbm_film_census *census,
+                          lbm_film_pair *pairs, int64_t cap, int64_t *npairs);
+
 /* FP64 totals: out[0] = sum rho, out[1..3] = sum j over all cells, with a
  * fixed-order block reduction (repeated calls give identical bits).  FP64
  * storage sums every population in FP64; the FP32-arithmetic storages sum

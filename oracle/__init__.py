@@ -80,6 +80,8 @@ def _L():
         _lib.orc_bubble_sizes.restype = i64
         _lib.orc_size_histogram.argtypes = [i64, P, C.c_int, P]
         _lib.orc_film_cells.argtypes = [C.c_int, i64, i64, i64, P, P, C.c_int, d, P, P, i64, P, P]
+        _lib.orc_film_midpoints.argtypes = [C.c_int, i64, i64, i64, P, P, C.c_int, d, P, P, i64,
+                                            P, P]
     return _lib
 
 
@@ -274,6 +276,64 @@ def film_cells(lat, labels, p, h_max, eps_arm, state, cap=1 << 16):
     nf = int(min(counts[3], cap))
     return (dict(film=int(counts[0]), midpoints=int(counts[1]), armed=int(counts[2]),
                  fired=int(counts[3])), rec[:nf], d2[:nf])
+
+
+def film_midpoints(lat, labels, p, h_max, eps_arm, state, cap=1 << 20):
+    """The film test of film_cells (the same arming update of ``state``)
+    returning every film midpoint: (counts dict as film_cells, records (k, 6)
+    int64 = cell, axis, label on the -axis side, label on the +axis side,
+    thickness, fired flag, in increasing (cell, axis) order)."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    p = _f64(p)
+    nz, ny, nx = lab.shape
+    assert state.dtype == np.uint8 and state.shape == lab.shape and state.flags.c_contiguous
+    counts = np.zeros(5, dtype=np.int64)
+    rec = np.zeros((cap, 6), dtype=np.int64)
+    _L().orc_film_midpoints(lat, nx, ny, nz, _p(lab), _p(p), int(h_max), float(eps_arm),
+                            _p(state), _p(counts), cap, _p(rec), None)
+    n = int(min(counts[4], cap))
+    return (dict(film=int(counts[0]), midpoints=int(counts[1]), armed=int(counts[2]),
+                 fired=int(counts[3])), rec[:n])
+
+
+def film_pairs(lat, shape, mids):
+    """Per bubble pair census of the film test in a foam (Sec. 4: the
+    criterion at each lattice point; Fig. 3's film disc radius R_d and
+    critical thickness h_c per pair of bubbles).  ``mids`` are the midpoint
+    records of film_midpoints on a lattice of ``shape`` = (nz, ny, nx).
+    For each unordered pair of labels meeting in a film, and each axis: the
+    lattice lines along the axis that hold a midpoint of the pair (a film of
+    even thickness has two midpoints on one line), the midpoints, the
+    thinnest run.  The pair's film lies across the axis with the most lines
+    (the lower axis on a tie); the lines are its disc's area in cells, so
+    R_d = sqrt(lines / pi) in 3-D and lines / 2 in 2-D (a film segment).
+    h_c = mean thickness of the pair's fired midpoints (any axis), 0 when none
+    fired.  Returns rows (label_a < label_b, axis, lines, midpoints, h_min,
+    r_d, fired, h_c) in increasing (label_a, label_b) order."""
+    nz, ny, nx = shape
+    dims = 2 if lat == D2Q9 else 3
+    groups = {}
+    for cell, a, lm, lp, t, fired in np.asarray(mids, dtype=np.int64).reshape(-1, 6).tolist():
+        x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+        line = (y, z) if a == 0 else ((x, z) if a == 1 else (x, y))
+        g = groups.setdefault((min(lm, lp), max(lm, lp)),
+                              dict(lines=[set() for _ in range(dims)], mid=[0] * dims,
+                                   hmin=[None] * dims, fired=0, tsum=0))
+        g["lines"][a].add(line)
+        g["mid"][a] += 1
+        g["hmin"][a] = t if g["hmin"][a] is None else min(g["hmin"][a], t)
+        if fired:
+            g["fired"] += 1
+            g["tsum"] += t
+    rows = []
+    for (la, lb) in sorted(groups):
+        g = groups[(la, lb)]
+        a = max(range(dims), key=lambda q: (len(g["lines"][q]), -q))
+        n = len(g["lines"][a])
+        r_d = float(np.sqrt(n / np.pi)) if dims == 3 else n / 2.0
+        h_c = g["tsum"] / g["fired"] if g["fired"] else 0.0
+        rows.append((la, lb, a, n, g["mid"][a], g["hmin"][a], r_d, g["fired"], h_c))
+    return rows
 
 
 def criterion_step(state, probe, eps_arm, h_max):

@@ -650,9 +650,13 @@ void orc_size_histogram(int64_t n, const int64_t *sizes, int nbins, int64_t *his
  * counts = {film (cell, axis) pairs, midpoints, armed after the update,
  * fired}; the fired records, in increasing (cell, axis) order, fill up to
  * cap entries of rec (cell, axis, L-, L+, t) and d2 (either may be NULL). */
-void orc_film_cells(int lat, int64_t nx, int64_t ny, int64_t nz, const int32_t *label,
-                    const double *p, int h_max, double eps_arm, uint8_t *state,
-                    int64_t *counts, int64_t cap, int64_t *rec, double *d2out) {
+/* One pass of the film test.  all_mid = 0: rec (5 columns) and d2out hold
+ * the fired (cell, axis) pairs.  all_mid = 1: rec (6 columns: cell, axis,
+ * label on the -axis side, label on the +axis side, thickness, fired) and
+ * d2out hold every film midpoint, and counts[4] their number. */
+static void film_pass(int lat, int64_t nx, int64_t ny, int64_t nz, const int32_t *label,
+                      const double *p, int h_max, double eps_arm, uint8_t *state,
+                      int64_t *counts, int64_t cap, int64_t *rec, double *d2out, int all_mid) {
   int dims = lat == ORC_D2Q9 ? 2 : 3;
   int64_t N = nx * ny * nz;
   int64_t nfilm = 0, nmid = 0, narmed = 0, nfired = 0;
@@ -692,16 +696,32 @@ void orc_film_cells(int lat, int64_t nx, int64_t ny, int64_t nz, const int32_t *
         state[k] = (uint8_t)(state[k] & ~bit);
         continue;
       }
-      ++nmid;
       int e[3] = {0, 0, 0};
       e[a] = 1;
       double d2 = p[nb(x, y, z, e[0], e[1], e[2], nx, ny, nz)] - 2.0 * p[k] +
                   p[nb(x, y, z, -e[0], -e[1], -e[2], nx, ny, nz)];
+      int fired = 0;
       if (d2 < -eps_arm) {
         state[k] = (uint8_t)(state[k] | bit);
       } else if ((state[k] & bit) && d2 >= 0.0) {
         state[k] = (uint8_t)(state[k] & ~bit);
-        if (nfired < cap) {
+        fired = 1;
+      }
+      if (all_mid && nmid < cap) {
+        if (rec) {
+          int64_t *r = rec + 6 * nmid;
+          r[0] = k;
+          r[1] = a;
+          r[2] = Lm;
+          r[3] = Lp;
+          r[4] = dp + dm - 1;
+          r[5] = fired;
+        }
+        if (d2out) d2out[nmid] = d2;
+      }
+      ++nmid;
+      if (fired) {
+        if (!all_mid && nfired < cap) {
           if (rec) {
             int64_t *r = rec + 5 * nfired;
             r[0] = k;
@@ -722,4 +742,20 @@ void orc_film_cells(int lat, int64_t nx, int64_t ny, int64_t nz, const int32_t *
   counts[1] = nmid;
   counts[2] = narmed;
   counts[3] = nfired;
+  if (all_mid) counts[4] = nmid;
+}
+
+void orc_film_cells(int lat, int64_t nx, int64_t ny, int64_t nz, const int32_t *label,
+                    const double *p, int h_max, double eps_arm, uint8_t *state,
+                    int64_t *counts, int64_t cap, int64_t *rec, double *d2out) {
+  film_pass(lat, nx, ny, nz, label, p, h_max, eps_arm, state, counts, cap, rec, d2out, 0);
+}
+
+/* The same pass recording every film midpoint: counts has 5 entries (film,
+ * midpoints, armed, fired, midpoint records), rec 6 columns per midpoint in
+ * increasing (cell, axis) order. */
+void orc_film_midpoints(int lat, int64_t nx, int64_t ny, int64_t nz, const int32_t *label,
+                        const double *p, int h_max, double eps_arm, uint8_t *state,
+                        int64_t *counts, int64_t cap, int64_t *rec, double *d2out) {
+  film_pass(lat, nx, ny, nz, label, p, h_max, eps_arm, state, counts, cap, rec, d2out, 1);
 }

@@ -76,9 +76,10 @@ struct lbm_ctx {
   // diagnostics
   DevBuf d_err, d_rho, d_p, d_tmp, d_j, d_u, d_labels, d_ncomp, d_part, d_tot, d_site_lab;
   // bubble census and per-point film test
-  DevBuf d_count, d_census, d_film_state, d_film_counts, d_film_rec;
+  DevBuf d_count, d_census, d_film_state, d_film_counts, d_film_rec, d_film_save;
   bool film_state_clear = false;  // d_film_state must be zeroed before use
   int64_t census_cap = 4096;       // device capacity of the census list (grows)
+  int64_t film_mid_cap = 1 << 16;  // device capacity of the midpoint records (grows)
   // d_rho / d_p hold the FP64 density and pressure of the current state;
   // d_labels its gas labels (cleared by stepping and by state writes)
   bool p_valid = false, labels_valid = false;
@@ -370,7 +371,7 @@ void lbm_destroy(lbm_ctx *c) {
                     &c->psi_scratch, &c->d_err, &c->d_rho, &c->d_p, &c->d_tmp, &c->d_j, &c->d_u,
                     &c->d_labels, &c->d_ncomp, &c->d_part, &c->d_tot, &c->d_site_lab,
                     &c->d_count, &c->d_census, &c->d_film_state, &c->d_film_counts,
-                    &c->d_film_rec};
+                    &c->d_film_rec, &c->d_film_save};
   for (DevBuf *b : bufs) dfree(c, *b);
   hfree(c->h_err);
   hfree(c->h_site);
@@ -979,11 +980,10 @@ lbm_status lbm_bubble_sizes(lbm_ctx *c, int64_t *roots, int64_t *sizes, int64_t 
   return LBM_OK;
 }
 
-lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_census *out,
-                          lbm_film_cell *fired, int64_t cap) {
-  if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
-  if (h_max < 1 || h_max > 1024 || !(eps_arm >= 0) || cap < 0)
-    return fail(LBM_EINVAL, "1 <= h_max <= 1024, eps_arm >= 0, cap >= 0");
+// shared set-up of the film test: labels, arming state, counters
+static lbm_status film_prepare(lbm_ctx *c, int32_t h_max, double eps_arm) {
+  if (h_max < 1 || h_max > 1024 || !(eps_arm >= 0))
+    return fail(LBM_EINVAL, "1 <= h_max <= 1024, eps_arm >= 0");
   if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
   CKS(set_device(c));
   CKS(check_sticky(c));
@@ -994,13 +994,21 @@ lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
     CK(cudaMemsetAsync(c->d_film_state.p, 0, (size_t)c->N, c->s));
     c->film_state_clear = true;
   }
-  CKS(dalloc(c, c->d_film_counts, 4 * sizeof(unsigned long long)));
+  CKS(dalloc(c, c->d_film_counts, 5 * sizeof(unsigned long long)));
+  return LBM_OK;
+}
+
+lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_census *out,
+                          lbm_film_cell *fired, int64_t cap) {
+  if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+  if (cap < 0) return fail(LBM_EINVAL, "cap >= 0");
+  CKS(film_prepare(c, h_max, eps_arm));
   CKS(dalloc(c, c->d_film_rec, film_record_bytes() * (size_t)std::max<int64_t>(cap, 1)));
   CK(diag_film_cells(c->v, static_cast<const int32_t *>(c->d_labels.p), lattice_ptr(c, c->cur),
                      c->cfg.G, c->cfg.rho0, h_max, eps_arm,
                      static_cast<uint8_t *>(c->d_film_state.p),
                      static_cast<unsigned long long *>(c->d_film_counts.p), cap, c->d_film_rec.p,
-                     c->s));
+                     false, c->s));
   // mailbox: [counts: 4][up to cap records], one synchronisation
   const size_t rec_bytes = fired ? sizeof(lbm_film_cell) * (size_t)cap : 0;
   CKS(halloc(c, c->h_mail, 4 * sizeof(unsigned long long) + rec_bytes));
@@ -1023,6 +1031,108 @@ lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
       return a.cell != b.cell ? a.cell < b.cell : a.axis < b.axis;
     });
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_film_pairs(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_census *census,
+                          lbm_film_pair *pairs, int64_t cap, int64_t *npairs) {
+  if (!c || !census) return fail(LBM_EINVAL, "NULL argument");
+  if (cap < 0 || (cap > 0 && !pairs)) return fail(LBM_EINVAL, "cap >= 0, pairs given when cap > 0");
+  CKS(film_prepare(c, h_max, eps_arm));
+  // every midpoint is recorded; when they outnumber the record buffer the
+  // arming state is put back and the pass redone with a larger buffer, so
+  // that one call advances the state once
+  CKS(dalloc(c, c->d_film_save, (size_t)c->N));
+  CK(cudaMemcpyAsync(c->d_film_save.p, c->d_film_state.p, (size_t)c->N,
+                     cudaMemcpyDeviceToDevice, c->s));
+  const auto *mail = static_cast<const unsigned long long *>(nullptr);
+  int64_t nmid = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t capdev = c->film_mid_cap;
+    const size_t rec_bytes = film_record_bytes() * (size_t)capdev;
+    CKS(dalloc(c, c->d_film_rec, rec_bytes));
+    CK(diag_film_cells(c->v, static_cast<const int32_t *>(c->d_labels.p), lattice_ptr(c, c->cur),
+                       c->cfg.G, c->cfg.rho0, h_max, eps_arm,
+                       static_cast<uint8_t *>(c->d_film_state.p),
+                       static_cast<unsigned long long *>(c->d_film_counts.p), capdev,
+                       c->d_film_rec.p, true, c->s));
+    // mailbox: [counts: 5, one padding word][records]
+    CKS(halloc(c, c->h_mail, 6 * sizeof(unsigned long long) + rec_bytes));
+    auto *m = static_cast<unsigned char *>(c->h_mail.p);
+    CK(cudaMemcpyAsync(m, c->d_film_counts.p, 5 * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(m + 48, c->d_film_rec.p, rec_bytes, cudaMemcpyDeviceToHost, c->s));
+    CKS(sync_and_check(c));
+    mail = reinterpret_cast<const unsigned long long *>(m);
+    nmid = (int64_t)mail[4];
+    if (nmid <= capdev) break;
+    c->film_mid_cap = nmid + nmid / 4;  // grow, restore the state, redo
+    CK(cudaMemcpyAsync(c->d_film_state.p, c->d_film_save.p, (size_t)c->N,
+                       cudaMemcpyDeviceToDevice, c->s));
+  }
+  census->film = (int64_t)mail[0];
+  census->midpoints = (int64_t)mail[1];
+  census->armed = (int64_t)mail[2];
+  census->fired = (int64_t)mail[3];
+  // per pair and axis: lines holding a midpoint, midpoints, thinnest run;
+  // per pair: fired midpoints and their summed thickness
+  const auto *rec = reinterpret_cast<const lbm_film_cell *>(reinterpret_cast<const unsigned char *>(mail) + 48);
+  const int dims = c->lat == D2Q9 ? 2 : 3;
+  const int64_t nx = c->cfg.nx, ny = c->cfg.ny;
+  struct Acc {
+    std::vector<int64_t> lines[3];
+    int64_t mid[3] = {0, 0, 0};
+    int32_t hmin[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
+    int64_t fired = 0;
+    double tsum = 0.0;
+  };
+  std::map<std::pair<int32_t, int32_t>, Acc> acc;
+  for (int64_t q = 0; q < nmid; ++q) {
+    const lbm_film_cell &r = rec[q];
+    const int a = r.axis & 0xff;
+    const bool fired = (r.axis >> 8) & 1;
+    Acc &g = acc[{std::min(r.label_minus, r.label_plus), std::max(r.label_minus, r.label_plus)}];
+    // the lattice line through the cell along axis a, as the cell's index
+    // with its a-coordinate removed (user coordinates x + nx (y + ny z))
+    const int64_t x = r.cell % nx, yz = r.cell / nx, y = yz % ny, z = yz / ny;
+    const int64_t line = a == 0 ? yz : (a == 1 ? x + nx * z : x + nx * y);
+    g.lines[a].push_back(line);
+    g.mid[a] += 1;
+    g.hmin[a] = std::min(g.hmin[a], r.thickness);
+    if (fired) {
+      g.fired += 1;
+      g.tsum += r.thickness;
+    }
+  }
+  int64_t n = 0;
+  for (auto &kv : acc) {
+    Acc &g = kv.second;
+    int best = 0;
+    int64_t best_lines = -1;
+    for (int a = 0; a < dims; ++a) {
+      std::sort(g.lines[a].begin(), g.lines[a].end());
+      const int64_t nl = std::unique(g.lines[a].begin(), g.lines[a].end()) - g.lines[a].begin();
+      if (nl > best_lines) {  // the lower axis on a tie
+        best_lines = nl;
+        best = a;
+      }
+    }
+    if (n < cap) {
+      lbm_film_pair &o = pairs[n];
+      o.label_a = kv.first.first;
+      o.label_b = kv.first.second;
+      o.axis = best;
+      o.h_min = g.hmin[best];
+      o.lines = best_lines;
+      o.midpoints = g.mid[best];
+      o.fired = g.fired;
+      constexpr double kPi = 3.14159265358979323846;
+      o.r_d = dims == 3 ? std::sqrt((double)best_lines / kPi) : 0.5 * (double)best_lines;
+      o.h_c = g.fired ? g.tsum / (double)g.fired : 0.0;
+    }
+    ++n;
+  }
+  if (npairs) *npairs = n;
   return LBM_OK;
 }
 

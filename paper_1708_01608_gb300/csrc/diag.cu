@@ -551,12 +551,14 @@ using FilmRec = lbm_film_cell;  // written as the C ABI hands it out
 // each side (at most h_max cells), classify film / midpoint, and update the
 // arming bit of (cell, axis) as the two-bubble criterion does.  The FP64
 // pressure of a midpoint and its two neighbours along the axis is computed
-// from their populations (the bits diag_moments would store).
+// from their populations (the bits diag_moments would store).  Records: the
+// fired (cell, axis) pairs (slot counts[3]); with all_mid, every midpoint
+// instead (slot counts[4], axis | fired << 8).
 template <int LAT, int ST>
 __global__ void __launch_bounds__(TPB)
     k_film_cells(const View v, const int32_t *labels, const void *stored, double G, double rho0,
                  int h_max, double eps_arm, uint8_t *state, unsigned long long *counts,
-                 int64_t cap, FilmRec *rec) {
+                 int64_t cap, FilmRec *rec, int all_mid) {
   __shared__ unsigned long long sh[4];
   if (threadIdx.x < 4) sh[threadIdx.x] = 0;
   __syncthreads();
@@ -625,21 +627,35 @@ __global__ void __launch_bounds__(TPB)
       }
       ++nmid;
       const double d2 = p_at(1) - 2.0 * p_at(0) + p_at(-1);
+      bool fired = false;
       if (d2 < -eps_arm) {
         st = (uint8_t)(st | bit);
       } else if ((st & bit) && d2 >= 0.0) {
         st = (uint8_t)(st & ~bit);
-        const unsigned long long q = atomicAdd(&counts[3], 1ull);
-        if ((int64_t)q < cap) {
-          FilmRec r;
-          r.cell = k;
-          r.axis = ua;
-          r.label_minus = Lm;
-          r.label_plus = Lp;
-          r.thickness = dp + dm - 1;
-          r.d2p = d2;
-          rec[q] = r;
-        }
+        fired = true;
+      }
+      unsigned long long q = ~0ull;
+      if (all_mid) {
+        // one atomic per warp for the midpoints recorded together
+        const unsigned am = __activemask();
+        const int lane = (int)(threadIdx.x & 31), leader = __ffs(am) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&counts[4], (unsigned long long)__popc(am));
+        base = __shfl_sync(am, base, leader);
+        q = base + (unsigned long long)__popc(am & ((1u << lane) - 1u));
+        if (fired) atomicAdd(&counts[3], 1ull);
+      } else if (fired) {
+        q = atomicAdd(&counts[3], 1ull);
+      }
+      if ((int64_t)q < cap && q != ~0ull) {
+        FilmRec r;
+        r.cell = k;
+        r.axis = all_mid ? (ua | (fired ? 0x100 : 0)) : ua;
+        r.label_minus = Lm;
+        r.label_plus = Lp;
+        r.thickness = dp + dm - 1;
+        r.d2p = d2;
+        rec[q] = r;
       }
     }
     state[k] = st;
@@ -856,13 +872,13 @@ size_t film_record_bytes() { return sizeof(FilmRec); }
 cudaError_t diag_film_cells(const View &v, const int32_t *labels, const void *stored, double G,
                             double rho0, int h_max, double eps_arm, uint8_t *state,
                             unsigned long long *counts, int64_t cap, void *records,
-                            cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 4, s);
+                            bool all_mid, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 5, s);
   if (e != cudaSuccess) return e;
   dispatch(v, [&](auto L, auto S) {
     k_film_cells<decltype(L)::value, decltype(S)::value><<<nblocks(ncells(v)), TPB, 0, s>>>(
         v, labels, stored, G, rho0, h_max, eps_arm, state, counts, cap,
-        static_cast<FilmRec *>(records));
+        static_cast<FilmRec *>(records), all_mid ? 1 : 0);
   });
   return cudaGetLastError();
 }

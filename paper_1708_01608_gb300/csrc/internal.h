@@ -174,12 +174,14 @@ cudaError_t diag_bubble_sizes(const View &v, const int32_t *labels, int32_t *cou
                               int64_t *sizes, int nbins, unsigned long long *hist,
                               cudaStream_t s);
 // film test at every lattice point on the stored populations (FP64 pressure
-// of the midpoints computed on demand): counts[4] = {film, midpoints, armed,
-// fired}; fired records (film_record_bytes() each, unordered) up to cap
+// of the midpoints computed on demand): counts[5] = {film, midpoints, armed,
+// fired, midpoint records}; records (film_record_bytes() each, unordered)
+// up to cap: the fired (cell, axis) pairs, or with all_mid every midpoint
+// (axis | fired << 8)
 size_t film_record_bytes();
 cudaError_t diag_film_cells(const View &v, const int32_t *labels, const void *stored, double G,
                             double rho0, int h_max, double eps_arm, uint8_t *state,
                             unsigned long long *counts, int64_t cap, void *records,
-                            cudaStream_t s);
+                            bool all_mid, cudaStream_t s);
 
 }  // namespace sclbm

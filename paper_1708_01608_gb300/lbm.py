@@ -75,6 +75,10 @@ class FilmCensus(C.Structure):
 FILM_CELL = np.dtype([("cell", np.int64), ("axis", np.int32), ("label_minus", np.int32),
                       ("label_plus", np.int32), ("thickness", np.int32), ("d2p", np.float64)],
                      align=True)
+# lbm_film_pair
+FILM_PAIR = np.dtype([("label_a", np.int32), ("label_b", np.int32), ("axis", np.int32),
+                      ("h_min", np.int32), ("lines", np.int64), ("midpoints", np.int64),
+                      ("fired", np.int64), ("r_d", np.float64), ("h_c", np.float64)], align=True)
 
 
 class Domain(C.Structure):
@@ -120,6 +124,7 @@ def _load():
         "lbm_site_labels": (i32, [P_, P_, i32, C.POINTER(i64)]),
         "lbm_bubble_sizes": (i32, [P_, P_, P_, i64, C.POINTER(i64), P_, i32]),
         "lbm_film_cells": (i32, [P_, i32, d, C.POINTER(FilmCensus), P_, i64]),
+        "lbm_film_pairs": (i32, [P_, i32, d, C.POINTER(FilmCensus), P_, i64, C.POINTER(i64)]),
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
         "lbm_write_f": (i32, [P_, P_, sz]),
@@ -148,7 +153,7 @@ EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites"
            "lbm_autotune", "lbm_plan_info",
            "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose", "lbm_film_probe",
            "lbm_run_until_rupture",
-           "lbm_site_labels", "lbm_bubble_sizes", "lbm_film_cells",
+           "lbm_site_labels", "lbm_bubble_sizes", "lbm_film_cells", "lbm_film_pairs",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_last_error",
            "lbm_version", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_run",
            "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f")
@@ -412,6 +417,17 @@ class Lattice:
                                    int(cap)))
         return (dict(film=out.film, midpoints=out.midpoints, armed=out.armed, fired=out.fired),
                 rec[:min(out.fired, cap)].copy())
+
+    def film_pairs(self, h_max=12, eps_arm=1e-3, cap=1 << 14):
+        """The film test reported per pair of bubbles (lbm_film_pairs):
+        (counts dict, FILM_PAIR array in (label_a, label_b) order)."""
+        out = FilmCensus()
+        pairs = np.empty(max(cap, 1), dtype=FILM_PAIR)
+        n = C.c_int64(0)
+        _check(_lib.lbm_film_pairs(self._h, int(h_max), float(eps_arm), C.byref(out), _ptr(pairs),
+                                   int(cap), C.byref(n)))
+        return (dict(film=out.film, midpoints=out.midpoints, armed=out.armed, fired=out.fired),
+                pairs[:min(int(n.value), cap)].copy())
 
     def totals(self):
         out = np.zeros(4)

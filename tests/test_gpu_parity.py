@@ -649,6 +649,63 @@ def test_film_cells_3d_match_oracle(lbm):
     L.close()
 
 
+def _pairs_oracle(lat, f, G, h_max, eps_arm, state):
+    rho = O.moments(lat, f)[0]
+    lab, _ = O.label_gas(lat, rho, 1.0)
+    _, p = O.eos(rho, G)
+    counts, mids = O.film_midpoints(lat, lab, p, h_max, eps_arm, state)
+    return counts, O.film_pairs(lat, lab.shape, mids)
+
+
+def _same_pairs(got, ref):
+    (cg, pg), (co, po) = got, ref
+    assert cg == co, (cg, co)
+    assert len(pg) == len(po), (pg, po)
+    for g, o in zip(pg, po):
+        assert (g["label_a"], g["label_b"], g["axis"], g["lines"], g["midpoints"], g["h_min"],
+                g["fired"]) == (o[0], o[1], o[2], o[3], o[4], o[5], o[7]), (g, o)
+        assert g["r_d"] == pytest.approx(o[6], rel=1e-12) and g["h_c"] == pytest.approx(o[8], rel=1e-12)
+
+
+def test_film_pairs_two_disks_match_oracle(lbm):
+    """The two-disk film per pair: one pair, its film segment across x, at
+    2800 steps (armed) and 160 steps later (fired), as the oracle gives it."""
+    L, W, f0 = _two_disks(lbm)
+    f1 = O.run(O.D2Q9, f0, 2800, W["tau"], W["G"])
+    L.write_f(f1)
+    state = np.zeros((1, 128, 128), dtype=np.uint8)
+    a1 = L.film_pairs(12, 1e-3)
+    _same_pairs(a1, _pairs_oracle(O.D2Q9, f1, W["G"], 12, 1e-3, state))
+    assert len(a1[1]) == 1 and a1[1][0]["axis"] == 0 and a1[0]["armed"] > 0
+    L.step(160)
+    f2 = O.run(O.D2Q9, f1, 160, W["tau"], W["G"])
+    a2 = L.film_pairs(12, 1e-3)
+    _same_pairs(a2, _pairs_oracle(O.D2Q9, f2, W["G"], 12, 1e-3, state))
+    assert a2[1][0]["fired"] > 0 and a2[1][0]["h_c"] > 0
+    L.close()
+
+
+def test_film_pairs_3d_row_of_spheres_match_oracle(lbm):
+    """Four spheres of radius 7 in a row along x, 3 cells apart (through the
+    periodic wrap too): four films, each across x; three calls 20 steps
+    apart on each side (FP64)."""
+    nx, ny, nz = 68, 24, 24
+    bub = np.array([[8.0 + 17 * k, 12, 12, 7.0] for k in range(4)])
+    f = oracle_init("D3Q19", nx, ny, nz, bub, 2.0, 0.15, 2.0, 1e-3, 8)
+    L = lbm.Lattice("D3Q19", nx, ny, nz, tau=1.0, G=-5.0, storage="f64")
+    L.write_f(f)
+    state = np.zeros((nz, ny, nx), dtype=np.uint8)
+    for call in range(3):
+        got = L.film_pairs(12, 1e-3)
+        ref = _pairs_oracle(O.D3Q19, f, -5.0, 12, 1e-3, state)
+        _same_pairs(got, ref)
+        if call == 0:
+            assert len(got[1]) == 4 and (got[1]["axis"] == 0).all() and (got[1]["lines"] > 10).all()
+        L.step(20)
+        f = O.run(O.D3Q19, f, 20, 1.0, -5.0)
+    L.close()
+
+
 def test_bubble_sizes_many_components(lbm):
     """More components than the census list first holds: 32 x 32 x 48 with a
     gas cell at every even (x, y, z) is 6144 isolated cells, and six gas rows

@@ -679,3 +679,67 @@ def test_film_cells_3d_along_z():
     assert (st[10] == 4).all() and st.sum() == 4 * nx * ny
     c, r, _ = O.film_cells(O.D3Q19, lab, 0.01 * zs ** 2, 12, 1e-3, st)
     assert c["fired"] == nx * ny and (r[:, 1] == 2).all() and (r[:, 0] // (nx * ny) == 10).all()
+
+
+# ------------------------------------------------------- film pairs (per pair)
+def test_film_pairs_disc_between_two_gas_cylinders():
+    """Two gas cylinders of radius 4 stacked in z with a 5-cell liquid layer
+    between them: the film is the disc of (x, y) lines inside the cylinders,
+    across z only, thinnest run 5; R_d = sqrt(lines / pi).  Armed, then
+    fired on every line with h_c = 5."""
+    nx, ny, nz = 16, 16, 30
+    xx, yy = np.meshgrid(np.arange(nx), np.arange(ny))
+    disc = (xx - 7.5) ** 2 + (yy - 7.5) ** 2 <= 16.0
+    lines = int(disc.sum())
+    rho = np.full((nz, ny, nx), 2.0)
+    rho[2:8][:, disc] = 0.2
+    rho[13:19][:, disc] = 0.2
+    lab, n = O.label_gas(O.D3Q19, rho, 1.0)
+    assert n == 2
+    zs = np.arange(nz, dtype=float)[:, None, None] * np.ones((1, ny, nx))
+    st = np.zeros(lab.shape, dtype=np.uint8)
+    c, mids = O.film_midpoints(O.D3Q19, lab, -0.01 * zs ** 2, 12, 1e-3, st)
+    assert c["midpoints"] == lines == len(mids)
+    rows = O.film_pairs(O.D3Q19, lab.shape, mids)
+    la, lb = sorted({int(v) for v in lab.ravel() if v >= 0})
+    assert len(rows) == 1
+    assert rows[0][:6] == (la, lb, 2, lines, lines, 5)
+    assert rows[0][6] == pytest.approx(np.sqrt(lines / np.pi)) and rows[0][7:] == (0, 0.0)
+    c2, mids2 = O.film_midpoints(O.D3Q19, lab, 0.01 * zs ** 2, 12, 1e-3, st)
+    rows2 = O.film_pairs(O.D3Q19, lab.shape, mids2)
+    assert c2["fired"] == lines and rows2[0][7] == lines and rows2[0][8] == 5.0
+
+
+@pytest.mark.parametrize("t", [3, 4])
+def test_film_pairs_2d_slab_counts_lines_not_midpoints(t):
+    """A 2-D slab film across every row: an even thickness has two midpoints
+    per row, but the film segment still has one line per row: lines = ny,
+    R_d = ny / 2, midpoints = ny or 2 ny."""
+    nx, ny = 48, 6
+    lab, n = _slab_labels(nx, ny, 4, 12, t)
+    st = np.zeros(lab.shape, dtype=np.uint8)
+    c, mids = O.film_midpoints(O.D2Q9, lab, np.zeros(lab.shape), 12, 1e-3, st)
+    rows = O.film_pairs(O.D2Q9, lab.shape, mids)
+    per_row = 1 if t % 2 else 2
+    assert rows == [(4, 12 + t, 0, ny, per_row * ny, t, ny / 2.0, 0, 0.0)]
+    assert c["midpoints"] == per_row * ny
+
+
+def test_film_pairs_three_bubbles_two_films():
+    """Gas blocks A | B | C along x: a 3-cell film A-B over rows 0..9 and a
+    5-cell film B-C over rows 0..3 (C is 4 rows tall): two pairs, each with
+    its own lines and thickness, in increasing label order; the midpoint
+    totals add up to the census."""
+    nx, ny = 60, 16
+    rho = np.full((1, ny, nx), 2.0)
+    rho[0, 0:10, 4:12] = 0.2      # A
+    rho[0, 0:10, 15:25] = 0.2     # B (3 liquid cells after A)
+    rho[0, 0:4, 30:38] = 0.2      # C (5 liquid cells after B)
+    lab, n = O.label_gas(O.D2Q9, rho, 1.0)
+    assert n == 3
+    st = np.zeros(lab.shape, dtype=np.uint8)
+    c, mids = O.film_midpoints(O.D2Q9, lab, np.zeros(lab.shape), 12, 1e-3, st)
+    rows = O.film_pairs(O.D2Q9, lab.shape, mids)
+    A, B, Cc = 4, 15, 30
+    assert [r[:6] for r in rows] == [(A, B, 0, 10, 10, 3), (B, Cc, 0, 4, 4, 5)]
+    assert sum(r[4] for r in rows) == c["midpoints"] == len(mids)
