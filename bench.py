@@ -428,6 +428,11 @@ def run_ensemble(args):
             "seconds": dt, "updates": st["updates"], "launches": st["launches"],
             "fired": len(fired), "merged": sum(r["merged"] for r in res),
             "h_c_vs_R": [[round(a, 2), round(b, 3), round(c, 1), s] for a, b, c, s in fired]}
+    if len(fired) >= 3:
+        # the functional forms of Fig. 3 fitted to the fired domains (R_b = disk radius)
+        from paper_1708_01608_gb300.sweep import fit_fig3
+        line["fig3_fit"] = fit_fig3([a for a, _, _, _ in fired], [c for _, _, c, _ in fired],
+                                    [b for _, b, _, _ in fired])
     E.close()
     if args.single:
         upd, t_single = 0.0, 0.0

@@ -74,3 +74,20 @@ def test_site_sampler_reports_overfull(lbm):
     with pytest.raises(lbm.LBMError) as e:
         lbm.sample_sites(16, 16, 1, 50, 3.0, 3.0, 8.0, 0.0, 1, max_tries=10000)
     assert e.value.status == lbm.ESTATE
+
+
+def test_fig3_fit_recovers_exact_forms():
+    """Rows generated exactly from the two functional forms of Fig. 3 give
+    back their coefficients (R^2 = 1)."""
+    from paper_1708_01608_gb300.sweep import fit_fig3
+    R_b = np.array([8.0, 11.0, 15.0, 21.0, 30.0, 42.0, 60.0])
+    R_d = 2.088 * np.log(R_b) + 0.114
+    h_c = 0.002 * R_d ** 2 - 0.003 * R_d + 0.035
+    f = fit_fig3(R_b, R_d, h_c)
+    q, l = f["h_c_vs_R_d"], f["R_d_vs_ln_R_b"]
+    assert (q["a"], q["b"], q["c"]) == pytest.approx((0.002, -0.003, 0.035), abs=1e-9)
+    assert (l["alpha"], l["beta"]) == pytest.approx((2.088, 0.114), abs=1e-9)
+    assert q["r2"] == pytest.approx(1.0) and l["r2"] == pytest.approx(1.0)
+    assert f["corr_h_c_R_d"] > 0.99 and f["n"] == 7
+    with pytest.raises(ValueError):
+        fit_fig3(R_b[:2], R_d[:2], h_c[:2])
