@@ -170,6 +170,19 @@ lbm_status lbm_inject(lbm_ctx *ctx, const double *rate, const double *budget,
 /* Copy the remaining FP64 budgets (n = number of sites) to host. */
 lbm_status lbm_read_budgets(lbm_ctx *ctx, double *budget, int32_t n);
 
+/* Where the blowing agent goes.  mode 0 (default): w_i dm into the site
+ * cell's post-collision populations inside the step.  mode 1: spread over
+ * the site's bubble, the gas component holding the site cell at the start
+ * of each lbm_step call: after every step, the dm of the bubble's sites
+ * (taken in increasing site order from their FP64 budgets) is divided
+ * evenly over the bubble's cells, each getting w_i dm / n on its
+ * post-streaming populations; a site whose cell is liquid deposits at that
+ * cell.  In mode 1 lbm_step labels the gas of its starting state and
+ * synchronises once to read the sites' labels.  Mode 1 needs FP64 or FP32
+ * storage (a deposit per cell is below a 16-bit offset's resolution).
+ * Errors: EINVAL. */
+lbm_status lbm_set_injection_mode(lbm_ctx *ctx, int32_t mode);
+
 /* Advance nsteps time steps (asynchronous on the context stream).  Errors:
  * ESTATE (not seeded), EINVAL (nsteps < 0), ECUDA, or a sticky ETIMEOUT from
  * an earlier step. */

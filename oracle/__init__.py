@@ -278,6 +278,52 @@ def film_cells(lat, labels, p, h_max, eps_arm, state, cap=1 << 16):
                  fired=int(counts[3])), rec[:nf], d2[:nf])
 
 
+def run_spread(lat, f, steps, tau, G, sites, rate, budget, relabel_every, threshold=1.0):
+    """Blowing agent spread over each site's bubble (a reading of Sec. 3:
+    gas is added to each bubble every step until the agent is used up).
+    Every ``relabel_every`` steps (from the first) the gas is labelled and
+    each site takes the label of its cell.  Each step is the plain step of
+    ``run`` without injection, followed by the deposits: for every bubble
+    holding sites, its sites in increasing order take dm = min(rate, budget)
+    from their budgets (``budget`` is updated in place) and the total D is
+    spread evenly over the bubble's n cells, each population f_i of each of
+    its cells gaining w_i D / n; a site whose cell is liquid adds w_i dm to
+    its cell.  ``sites`` are linear cell indices.  Returns the populations."""
+    f = _f64(f)
+    _, w = velocities(lat)
+    Q = len(w)
+    sites = np.asarray(sites, dtype=np.int64)
+    for t in range(steps):
+        if t % relabel_every == 0:
+            lab, _ = label_gas(lat, moments(lat, f)[0], threshold)
+            lab_flat = lab.ravel()
+            site_lab = lab_flat[sites]
+            sizes = {}
+            for root, size in zip(*bubble_sizes(lab)):
+                sizes[int(root)] = int(size)
+        f = run(lat, f, 1, tau, G)
+        flat = f.reshape(Q, -1)
+        groups = {}
+        for s in range(len(sites)):
+            key = int(site_lab[s]) if site_lab[s] >= 0 else -1 - int(sites[s])
+            groups.setdefault(key, []).append(s)
+        for key, members in groups.items():
+            total = 0.0
+            for s in members:
+                d = min(rate[s], budget[s])
+                budget[s] -= d
+                total += d
+            if key >= 0:
+                per_cell = total / sizes[key]
+                cells = np.nonzero(lab_flat == key)[0]
+                for i in range(Q):
+                    flat[i, cells] += w[i] * per_cell
+            else:
+                for i in range(Q):
+                    flat[i, -1 - key] += w[i] * total
+    return f
+
+
 def film_midpoints(lat, labels, p, h_max, eps_arm, state, cap=1 << 20):
     """The film test of film_cells (the same arming update of ``state``)
     returning every film midpoint: (counts dict as film_cells, records (k, 6)

@@ -80,6 +80,10 @@ struct lbm_ctx {
   bool film_state_clear = false;  // d_film_state must be zeroed before use
   int64_t census_cap = 4096;       // device capacity of the census list (grows)
   int64_t film_mid_cap = 1 << 16;  // device capacity of the midpoint records (grows)
+  // injection mode: 0 at the site cell (inside the step kernels), 1 spread
+  // over the site's bubble (inject.cu)
+  int inj_mode = 0;
+  DevBuf d_spread_groups, d_spread_sites, d_spread_count, d_dep;
   // d_rho / d_p hold the FP64 density and pressure of the current state;
   // d_labels its gas labels (cleared by stepping and by state writes)
   bool p_valid = false, labels_valid = false;
@@ -371,7 +375,8 @@ void lbm_destroy(lbm_ctx *c) {
                     &c->psi_scratch, &c->d_err, &c->d_rho, &c->d_p, &c->d_tmp, &c->d_j, &c->d_u,
                     &c->d_labels, &c->d_ncomp, &c->d_part, &c->d_tot, &c->d_site_lab,
                     &c->d_count, &c->d_census, &c->d_film_state, &c->d_film_counts,
-                    &c->d_film_rec, &c->d_film_save};
+                    &c->d_film_rec, &c->d_film_save, &c->d_spread_groups,
+                    &c->d_spread_sites, &c->d_spread_count, &c->d_dep};
   for (DevBuf *b : bufs) dfree(c, *b);
   hfree(c->h_err);
   hfree(c->h_site);
@@ -511,6 +516,8 @@ lbm_status lbm_read_budgets(lbm_ctx *c, double *budget, int32_t n) {
   return sync_and_check(c);
 }
 
+static lbm_status ensure_labels(lbm_ctx *c);
+
 lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
@@ -546,6 +553,42 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.inv_rho0_f = (float)(1.0 / c->cfg.rho0);
   a.rho_ref_f = (float)c->cfg.rho_ref;
   const size_t pop_bytes = (size_t)c->v.px * c->v.NY * c->v.NZ * storage_bytes(c->st);
+  // spread mode: the bubbles of the sites are those of the state at the
+  // start of this call (one synchronisation to read the site labels)
+  const bool spread = c->inj_mode == 1 && c->ninj > 0 && nsteps > 0;
+  int ngroups = 0;
+  if (spread) {
+    a.nsites = 0;  // the step kernels deposit nothing
+    CKS(ensure_labels(c));
+    CKS(dalloc(c, c->d_spread_count, sizeof(int32_t) * c->N));
+    CK(inject_component_sizes(c->v, static_cast<const int32_t *>(c->d_labels.p),
+                              static_cast<int32_t *>(c->d_spread_count.p), c->s));
+    CKS(sync_and_check(c));  // site labels on the host
+    // groups: one per bubble holding sites, one per liquid site cell; sites
+    // in increasing order within a group
+    std::map<int64_t, std::vector<int32_t>> by;
+    for (int32_t q = 0; q < c->ninj; ++q) {
+      const int32_t lab = c->site_labels[q];
+      const int64_t cell = (int64_t)c->sx[q] + c->v.NX * ((int64_t)c->sy[q] + c->v.NY * c->sz[q]);
+      by[lab >= 0 ? (int64_t)lab : -1 - cell].push_back(q);
+    }
+    std::vector<int4> groups;
+    std::vector<int32_t> gsites;
+    for (auto &kv : by) {
+      const int first = (int)gsites.size();
+      gsites.insert(gsites.end(), kv.second.begin(), kv.second.end());
+      const bool bubble = kv.first >= 0;
+      groups.push_back(make_int4(bubble ? (int)kv.first : -1, first, (int)gsites.size(),
+                                 bubble ? 0 : (int)(-1 - kv.first)));
+    }
+    ngroups = (int)groups.size();
+    CKS(upload(c, c->d_spread_groups, groups));
+    CKS(upload(c, c->d_spread_sites, gsites));
+    CKS(dalloc(c, c->d_dep, sizeof(double) * c->N));
+    CK(cudaMemsetAsync(c->d_dep.p, 0, sizeof(double) * c->N, c->s));
+    CK(cudaStreamSynchronize(c->s));  // the host vectors go out of scope
+  }
+  const int32_t *spread_labels = static_cast<const int32_t *>(c->d_labels.p);
   for (int64_t t = 0; t < nsteps; ++t) {
     a.fin = lattice_ptr(c, c->cur);
     a.fout = lattice_ptr(c, 1 - c->cur);
@@ -555,6 +598,13 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
       e = fused_launch(c->lat, c->st, c->plan, a, c->cur == 0 ? c->tmA : c->tmB, c->s);
     else
       e = twopass_launch(c->lat, c->st, a, c->psi_scratch.p, c->s);
+    if (e == cudaSuccess && spread)
+      e = inject_spread(c->v, ngroups, static_cast<const int4 *>(c->d_spread_groups.p),
+                        static_cast<const int32_t *>(c->d_spread_sites.p),
+                        static_cast<const double *>(c->d_rate.p),
+                        static_cast<double *>(c->d_budget.p),
+                        static_cast<const int32_t *>(c->d_spread_count.p),
+                        static_cast<double *>(c->d_dep.p), spread_labels, a.fout, c->s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->sticky = LBM_ECUDA;
@@ -568,6 +618,15 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
 }
 
 int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+lbm_status lbm_set_injection_mode(lbm_ctx *c, int32_t mode) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (mode != 0 && mode != 1) return fail(LBM_EINVAL, "mode must be 0 (site cell) or 1 (bubble)");
+  if (mode == 1 && c->st != LBM_F64 && c->st != LBM_F32)
+    return fail(LBM_EINVAL, "spread injection needs FP64 or FP32 storage");
+  c->inj_mode = mode;
+  return LBM_OK;
+}
 
 lbm_status lbm_plan_info(const lbm_ctx *c, int32_t out[6]) {
   if (!c || !out) return fail(LBM_EINVAL, "NULL argument");

@@ -178,6 +178,15 @@ cudaError_t diag_bubble_sizes(const View &v, const int32_t *labels, int32_t *cou
 // fired, midpoint records}; records (film_record_bytes() each, unordered)
 // up to cap: the fired (cell, axis) pairs, or with all_mid every midpoint
 // (axis | fired << 8)
+// blowing agent spread over each site's bubble (inject.cu): cells per gas
+// root; then, after a step, take dm from the grouped sites (groups[g] =
+// {bubble label or -1, first, end into gsites, cell of a liquid group}) and
+// add w_i dm / n to the bubble's cells (dep: N doubles, per label)
+cudaError_t inject_component_sizes(const View &v, const int32_t *labels, int32_t *count,
+                                   cudaStream_t s);
+cudaError_t inject_spread(const View &v, int ngroups, const int4 *groups, const int32_t *gsites,
+                          const double *rate, double *budget, const int32_t *count, double *dep,
+                          const int32_t *labels, void *lattice, cudaStream_t s);
 size_t film_record_bytes();
 cudaError_t diag_film_cells(const View &v, const int32_t *labels, const void *stored, double G,
                             double rho0, int h_max, double eps_arm, uint8_t *state,

@@ -125,6 +125,7 @@ def _load():
         "lbm_bubble_sizes": (i32, [P_, P_, P_, i64, C.POINTER(i64), P_, i32]),
         "lbm_film_cells": (i32, [P_, i32, d, C.POINTER(FilmCensus), P_, i64]),
         "lbm_film_pairs": (i32, [P_, i32, d, C.POINTER(FilmCensus), P_, i64, C.POINTER(i64)]),
+        "lbm_set_injection_mode": (i32, [P_, i32]),
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
         "lbm_write_f": (i32, [P_, P_, sz]),
@@ -149,7 +150,8 @@ _lib = _load()
 
 # every symbol the header declares (checked by the CPU tests)
 EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites",
-           "lbm_seed_bubbles", "lbm_inject", "lbm_read_budgets", "lbm_step", "lbm_step_count",
+           "lbm_seed_bubbles", "lbm_inject", "lbm_set_injection_mode", "lbm_read_budgets",
+           "lbm_step", "lbm_step_count",
            "lbm_autotune", "lbm_plan_info",
            "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose", "lbm_film_probe",
            "lbm_run_until_rupture",
@@ -286,6 +288,11 @@ class Lattice:
         _check(_lib.lbm_inject(self._h, _ptr(r) if len(r) else None,
                                _ptr(b) if len(b) else None, len(r)))
         self._ninj = len(r)
+
+    def set_injection_mode(self, mode):
+        """"site" (the site cell, default) or "bubble" (spread over the site's
+        bubble after every step; lbm_set_injection_mode)."""
+        _check(_lib.lbm_set_injection_mode(self._h, {"site": 0, "bubble": 1}[mode]))
 
     def read_budgets(self):
         out = np.empty(getattr(self, "_ninj", 0))

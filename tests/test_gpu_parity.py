@@ -706,6 +706,50 @@ def test_film_pairs_3d_row_of_spheres_match_oracle(lbm):
     L.close()
 
 
+@pytest.mark.parametrize("lat,storage", [("D2Q9", "f64"), ("D3Q19", "f64"), ("D3Q19", "f32")])
+def test_spread_injection_matches_oracle(lbm, lat, storage):
+    """Blowing agent spread over each site's bubble (two sites in one bubble,
+    one in the liquid), 50 steps in calls of 10 (the bubbles are relabelled
+    at the start of each call): populations and FP64 budgets as the oracle's
+    run_spread relabelling every 10 steps."""
+    if lat == "D2Q9":
+        nx, ny, nz = 64, 48, 1
+        bub = [[20, 20, 0, 8.0], [44, 30, 0, 7.0]]
+        cells = [20 + nx * 20, 22 + nx * 21, 5 + nx * 40]
+    else:
+        nx, ny, nz = 32, 28, 24
+        bub = [[10, 10, 10, 6.0], [22, 18, 14, 5.0]]
+        cells = [10 + nx * (10 + ny * 10), 11 + nx * (10 + ny * 10), 2 + nx * (25 + ny * 3)]
+    rate = np.array([1e-3, 5e-4, 2e-4])
+    budget = np.array([1.0, 0.004, 1.0])
+    f0 = as_stored(lat, oracle_init(lat, nx, ny, nz, bub, 2.0, 0.15, 2.0, 1e-3, 5), storage, 2.0)
+    L = lbm.Lattice(lat, nx, ny, nz, tau=0.9, G=-5.0, storage=storage, rho_ref=2.0)
+    # sites at the chosen cells (one point bubble each registers the site)
+    xs = [c % nx for c in cells]
+    ys = [(c // nx) % ny for c in cells]
+    zs = [c // (nx * ny) for c in cells]
+    sb = np.array([[x, y, z, 0.0] for x, y, z in zip(xs, ys, zs)], dtype=float)
+    L.seed_bubbles(sb, 2.0, 2.0, 2.0, 0.0, 1)
+    L.write_f(f0)
+    L.inject(rate, budget)
+    L.set_injection_mode("bubble")
+    for _ in range(5):
+        L.step(10)
+    ob = budget.copy()
+    fo = O.run_spread(LAT[lat], f0, 50, 0.9, -5.0, np.array(cells), rate, ob, 10)
+    assert np.abs(L.read_budgets() - ob).max() < 1e-15
+    assert rel_err(L.read("f"), fo) < (1e-12 if storage == "f64" else 1e-5), rel_err(L.read("f"), fo)
+    L.close()
+
+
+def test_spread_injection_needs_32_or_64_bit_storage(lbm):
+    L = lbm.Lattice("D3Q19", 16, 16, 16, storage="f16")
+    with pytest.raises(lbm.LBMError) as e:
+        L.set_injection_mode("bubble")
+    assert e.value.status == lbm.EINVAL
+    L.close()
+
+
 def test_bubble_sizes_many_components(lbm):
     """More components than the census list first holds: 32 x 32 x 48 with a
     gas cell at every even (x, y, z) is 6144 isolated cells, and six gas rows

@@ -743,3 +743,58 @@ def test_film_pairs_three_bubbles_two_films():
     A, B, Cc = 4, 15, 30
     assert [r[:6] for r in rows] == [(A, B, 0, 10, 10, 3), (B, Cc, 0, 4, 4, 5)]
     assert sum(r[4] for r in rows) == c["midpoints"] == len(mids)
+
+
+# ---------------------------------------------- injection spread over a bubble
+def _disk_state(nx=48, ny=40, r=8.0, seed=3):
+    f, rho = O.init(O.D2Q9, nx, ny, 1, np.array([[20.0, 20.0, 0.0, r]]), 2.0, 0.15, 2.0, 1e-3,
+                    seed)
+    return f, rho
+
+
+def test_spread_injection_deposit_is_uniform_over_the_bubble():
+    """One step with two sites in the disk and one in the liquid, against
+    the same step without injection: every cell of the disk (as labelled at
+    the start) gains w_i (dm1 + dm2) / n on each population, the liquid site
+    cell gains w_i dm3, nothing else changes; budgets drop by the dm taken
+    (the second disk site's budget runs out)."""
+    f, rho = _disk_state()
+    nx = 48
+    lab, n = O.label_gas(O.D2Q9, rho, 1.0)
+    assert n == 1
+    root = int(lab.ravel()[20 + nx * 20])
+    ncell = int((lab == root).sum())
+    sites = np.array([20 + nx * 20, 22 + nx * 21, 40 + nx * 5])
+    rate = np.array([1e-3, 2e-3, 5e-4])
+    budget = np.array([1.0, 1.5e-3, 1.0])
+    g = O.run_spread(O.D2Q9, f, 1, 1.0, -5.0, sites, rate, budget, 1)
+    h = O.run(O.D2Q9, f, 1, 1.0, -5.0)
+    _, w = O.velocities(O.D2Q9)
+    diff = (g - h).reshape(9, -1)
+    D = 1e-3 + 1.5e-3
+    in_bub = lab.ravel() == root
+    assert np.allclose(diff[:, in_bub], w[:, None] * D / ncell, rtol=0, atol=1e-15)
+    assert np.allclose(diff[:, 40 + nx * 5], w * 5e-4, rtol=0, atol=1e-15)
+    other = ~in_bub
+    other[40 + nx * 5] = False
+    assert np.abs(diff[:, other]).max() == 0.0
+    assert np.allclose(budget, [1.0 - 1e-3, 0.0, 1.0 - 5e-4], rtol=0, atol=1e-15)
+    # zero momentum (sum_i c_i w_i = 0), up to the rounding of g - h (|f| ~ 0.2)
+    c, _ = O.velocities(O.D2Q9)
+    assert np.abs(c.T @ diff).max() < 1e-16
+
+
+def test_spread_injection_mass_ledger_with_relabelling():
+    """Over 30 steps relabelled every 10 (G = -5 dynamics conserve mass), the
+    total mass grows by exactly the agent taken."""
+    f, _ = _disk_state()
+    sites = np.array([20 + 48 * 20, 3 + 48 * 3])
+    rate = np.array([1e-3, 2e-4])
+    budget = np.array([0.02, 1.0])
+    m0 = O.totals(O.D2Q9, f)[0]
+    g = O.run_spread(O.D2Q9, f, 30, 1.0, -5.0, sites, rate, budget, 10)
+    taken = (0.02 - budget[0]) + (1.0 - budget[1])
+    assert taken == pytest.approx(0.02 + 30 * 2e-4, abs=1e-15)
+    # FP64 totals of a mass ~3800 carry ~1e-11 of rounding; a lost or doubled
+    # deposit would be off by >= 2e-4
+    assert O.totals(O.D2Q9, g)[0] - m0 == pytest.approx(taken, abs=1e-9)
