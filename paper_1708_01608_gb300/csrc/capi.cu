@@ -557,6 +557,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
   // start of this call (one synchronisation to read the site labels)
   const bool spread = c->inj_mode == 1 && c->ninj > 0 && nsteps > 0;
   int ngroups = 0;
+  bool any_bubble = false;
   if (spread) {
     a.nsites = 0;  // the step kernels deposit nothing
     CKS(ensure_labels(c));
@@ -578,6 +579,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
       const int first = (int)gsites.size();
       gsites.insert(gsites.end(), kv.second.begin(), kv.second.end());
       const bool bubble = kv.first >= 0;
+      any_bubble |= bubble;
       groups.push_back(make_int4(bubble ? (int)kv.first : -1, first, (int)gsites.size(),
                                  bubble ? 0 : (int)(-1 - kv.first)));
     }
@@ -604,7 +606,8 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
                         static_cast<const double *>(c->d_rate.p),
                         static_cast<double *>(c->d_budget.p),
                         static_cast<const int32_t *>(c->d_spread_count.p),
-                        static_cast<double *>(c->d_dep.p), spread_labels, a.fout, c->s);
+                        static_cast<double *>(c->d_dep.p), spread_labels, any_bubble, a.fout,
+                        c->s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->sticky = LBM_ECUDA;

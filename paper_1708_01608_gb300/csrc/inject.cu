@@ -118,13 +118,16 @@ cudaError_t inject_component_sizes(const View &v, const int32_t *labels, int32_t
 
 cudaError_t inject_spread(const View &v, int ngroups, const int4 *groups, const int32_t *gsites,
                           const double *rate, double *budget, const int32_t *count, double *dep,
-                          const int32_t *labels, void *lattice, cudaStream_t s) {
+                          const int32_t *labels, bool any_bubble, void *lattice, cudaStream_t s) {
   return dispatch_spread(v, [&](auto L, auto S) {
     constexpr int LAT = decltype(L)::value, ST = decltype(S)::value;
     if (ngroups > 0)
       k_spread_take<LAT, ST><<<(ngroups + 127) / 128, 128, 0, s>>>(v, ngroups, groups, gsites,
                                                                   rate, budget, count, dep, lattice);
-    k_spread_apply<LAT, ST><<<grid_for(v.NX * v.NY * v.NZ), TPB, 0, s>>>(v, labels, dep, lattice);
+    // the pass over the cells only when a site lies in a bubble
+    if (any_bubble)
+      k_spread_apply<LAT, ST><<<grid_for(v.NX * v.NY * v.NZ), TPB, 0, s>>>(v, labels, dep,
+                                                                            lattice);
   });
 }
 

@@ -186,7 +186,7 @@ cudaError_t inject_component_sizes(const View &v, const int32_t *labels, int32_t
                                    cudaStream_t s);
 cudaError_t inject_spread(const View &v, int ngroups, const int4 *groups, const int32_t *gsites,
                           const double *rate, double *budget, const int32_t *count, double *dep,
-                          const int32_t *labels, void *lattice, cudaStream_t s);
+                          const int32_t *labels, bool any_bubble, void *lattice, cudaStream_t s);
 size_t film_record_bytes();
 cudaError_t diag_film_cells(const View &v, const int32_t *labels, const void *stored, double G,
                             double rho0, int h_max, double eps_arm, uint8_t *state,
