@@ -28,7 +28,20 @@ from helpers import lbm_mod
 pytestmark = pytest.mark.gpu
 
 FORMS = ["f32", "f16", "bf16"]
+# storage form and kernel: the default tile (one cell per thread) and the
+# x-pair kernel's tile (two cells per thread), which the autotuner picks for
+# the 16-bit forms at scale; results of the latter are keyed "<form>_x2"
+VARIANTS = [("f32", 0), ("f16", 0), ("bf16", 0), ("f32", "x2"), ("f16", "x2")]
+X2_TILE = {"D2Q9": 4, "D3Q19": 14}
 RESULTS = {}
+
+
+def _tile(lat, t):
+    return X2_TILE[lat] if t == "x2" else 0
+
+
+def _key(st, t):
+    return st + ("_x2" if t == "x2" else "")
 
 
 @pytest.fixture(scope="module")
@@ -58,17 +71,19 @@ def test_flat_interface_coexistence(lbm):
     fo = O.run(O.D2Q9, f0, 20000, 1.0, -5.0)
     ref = _coexistence(O.moments(O.D2Q9, fo)[0][0, 0])
     rows = {}
-    for st in FORMS + ["f64"]:
+    for st, t in VARIANTS + [("f64", 0)]:
         L = lbm.Lattice("D2Q9", n, 1, 1, tau=1.0, G=-5.0, storage=st, rho_ref=1.0,
-                        kernel="two_pass" if st == "f64" else "auto")
+                        kernel="two_pass" if st == "f64" else ("fused" if t else "auto"),
+                        tile=_tile("D2Q9", t))
         L.write_f(f0)
         L.step(20000)
         got = _coexistence(L.read("rho")[0, 0])
         err = [abs(g / r - 1) for g, r in zip(got, ref)]
-        rows[st] = dict(rho_g=got[0], rho_l=got[1], rel_err_g=err[0], rel_err_l=err[1])
-        print(st, rows[st])
+        k = _key(st, t)
+        rows[k] = dict(rho_g=got[0], rho_l=got[1], rel_err_g=err[0], rel_err_l=err[1])
+        print(k, rows[k])
         bound = {"f64": 1e-10, "f32": 1e-4, "f16": 1e-2, "bf16": 5e-2}[st]
-        assert max(err) < bound, (st, rows[st])
+        assert max(err) < bound, (k, rows[k])
         L.close()
     RESULTS["coexistence"] = dict(oracle=dict(rho_g=ref[0], rho_l=ref[1]), **rows)
 
@@ -104,20 +119,22 @@ def test_laplace_surface_tension(lbm):
                        for f0 in starts])
     assert ref is not None
     rows = {}
-    for st in FORMS:
+    for st, t in VARIANTS:
         rhos = []
         for f0 in starts:
-            L = lbm.Lattice("D2Q9", n, n, 1, tau=1.0, G=-5.0, storage=st, rho_ref=1.0)
+            L = lbm.Lattice("D2Q9", n, n, 1, tau=1.0, G=-5.0, storage=st, rho_ref=1.0,
+                            kernel="fused" if t else "auto", tile=_tile("D2Q9", t))
             L.write_f(f0)
             L.step(3000)
             rhos.append(L.read("rho"))
             L.close()
         sg, Rm = sigma_of(rhos)
-        rows[st] = dict(sigma=sg, R_m=Rm, rel_err=None if sg is None else abs(sg / ref - 1))
-        print(st, rows[st])
+        k = _key(st, t)
+        rows[k] = dict(sigma=sg, R_m=Rm, rel_err=None if sg is None else abs(sg / ref - 1))
+        print(k, rows[k])
     RESULTS["laplace_sigma"] = dict(oracle=ref, **rows)
-    for st, bound in (("f32", 1e-3), ("f16", 3e-2)):
-        assert rows[st]["sigma"] is not None and rows[st]["rel_err"] < bound, (st, rows[st])
+    for k, bound in (("f32", 1e-3), ("f16", 3e-2), ("f32_x2", 1e-3), ("f16_x2", 3e-2)):
+        assert rows[k]["sigma"] is not None and rows[k]["rel_err"] < bound, (k, rows[k])
 
 
 def test_density_field_error_3d(lbm):
@@ -129,14 +146,16 @@ def test_density_field_error_3d(lbm):
     f0, _ = O.init(O.D3Q19, n, n, n, bub, 2.0, 0.15, 2.0, 1e-3, 7)
     ref = O.moments(O.D3Q19, O.run(O.D3Q19, f0, 200, 0.8, -5.0))[0]
     rows = {}
-    for st in FORMS:
-        L = lbm.Lattice("D3Q19", n, n, n, tau=0.8, G=-5.0, storage=st, rho_ref=2.0)
+    for st, t in VARIANTS:
+        L = lbm.Lattice("D3Q19", n, n, n, tau=0.8, G=-5.0, storage=st, rho_ref=2.0,
+                        kernel="fused" if t else "auto", tile=_tile("D3Q19", t))
         L.write_f(f0)
         L.step(200)
         d = L.read("rho") - ref
-        rows[st] = dict(max_abs=float(np.abs(d).max()), rms=float(np.sqrt((d ** 2).mean())))
-        print(st, rows[st])
-        assert rows[st]["max_abs"] < {"f32": 1e-5, "f16": 1e-2, "bf16": 5e-2}[st], (st, rows[st])
+        k = _key(st, t)
+        rows[k] = dict(max_abs=float(np.abs(d).max()), rms=float(np.sqrt((d ** 2).mean())))
+        print(k, rows[k])
+        assert rows[k]["max_abs"] < {"f32": 1e-5, "f16": 1e-2, "bf16": 5e-2}[st], (k, rows[k])
         L.close()
     RESULTS["density_64cube_200steps"] = rows
 
@@ -152,16 +171,18 @@ def test_two_disk_h_c(lbm):
                               5000, 20)
     assert ref["fired"]
     rows = {}
-    for st in FORMS:
-        L = lbm.Lattice("D2Q9", 128, 128, 1, tau=W["tau"], G=W["G"], storage=st, rho_ref=2.0)
+    for st, t in VARIANTS:
+        L = lbm.Lattice("D2Q9", 128, 128, 1, tau=W["tau"], G=W["G"], storage=st, rho_ref=2.0,
+                        kernel="fused" if t else "auto", tile=_tile("D2Q9", t))
         L.write_f(f0)
         r = L.run_until_rupture(line, 1.075, 1e-3, 20, 5000)
-        rows[st] = dict(fired=r["fired"], merged=r["merged"], step=r["steps"], h_c=r["h_c"],
-                        h_probe=r["h_probe"],
-                        rel_err=abs(r["h_c"] / ref["h_c"] - 1) if r["fired"] else None)
-        print(st, rows[st])
+        k = _key(st, t)
+        rows[k] = dict(fired=r["fired"], merged=r["merged"], step=r["steps"], h_c=r["h_c"],
+                       h_probe=r["h_probe"],
+                       rel_err=abs(r["h_c"] / ref["h_c"] - 1) if r["fired"] else None)
+        print(k, rows[k])
         L.close()
     RESULTS["two_disk_h_c"] = dict(oracle=dict(step=ref["step"], h_c=ref["h_c"],
                                                h_probe=ref["h_probe"]), **rows)
-    for st in ("f32", "f16"):
-        assert rows[st]["fired"] and rows[st]["rel_err"] < 0.01, (st, rows[st])
+    for k in ("f32", "f16", "f32_x2", "f16_x2"):
+        assert rows[k]["fired"] and rows[k]["rel_err"] < 0.01, (k, rows[k])
