@@ -208,9 +208,10 @@ def diagnostics(L):
     L.bubble_sizes(CENSUS_BINS)                 # bubble census + size histogram
 
 
-# kernels of one diagnostic interval: scan + final, union + compress, site
-# gather, moments (pressure), film test, census count + list
-DIAG_LAUNCHES = 9
+# kernels of one diagnostic interval (FP32 storage): scan + final (totals and
+# gas flags), union + compress (labels), site gather, film test (pressure of
+# its midpoints computed in place), census count + list
+DIAG_LAUNCHES = 8
 
 
 def cpu_baseline(seconds_target=15.0):

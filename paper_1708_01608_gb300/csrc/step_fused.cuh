@@ -549,8 +549,10 @@ __global__ void __launch_bounds__(BX *BY, BX *BY <= 256 ? 3 : 1)
   const MarchArgs m = march_args_of(tm, a, tiles_x, tiles_y, zlen, BX, BY);
   fused_barriers_init<LAT, ST, BX, BY, NS>(m);
   // Programmatic dependent launch: the shared-memory set-up above overlaps
-  // the previous step's tail; nothing in global memory is read or written
-  // before that step has completed and its writes are visible.
+  // the previous step's tail.  Before the wait only the launch's own
+  // read-only inputs are read (the injection buckets); the lattices and the
+  // site budgets are touched only after the previous step has completed
+  // and its writes are visible.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   uint32_t kb = 0;
