@@ -202,10 +202,9 @@ def make_lattice(lbm, kernel="auto"):
 
 def diagnostics(L):
     """The diagnostic interval through the C ABI (labels computed once)."""
-    L.diagnose(want_labels=False)               # FP64 totals + gas labels in one pass
-    L.site_labels()                             # per-site labels, merge events
-    L.film_cells(FILM_H_MAX, FILM_EPS_ARM, FILM_CAP)  # FP64 pressure, film test per point
-    L.bubble_sizes(CENSUS_BINS)                 # bubble census + size histogram
+    # FP64 totals + gas labels in one pass, site labels and merge events, the
+    # film test at every lattice point, the bubble census: one call, one sync
+    L.diagnostic_interval(FILM_H_MAX, FILM_EPS_ARM, FILM_CAP, CENSUS_BINS)
 
 
 # kernels of one diagnostic interval (FP32 storage): scan + final (totals and
@@ -342,9 +341,7 @@ def run_ours(args, world, rank, local):
     sizes = torch.empty(1 << 16, dtype=torch.int64, pin_memory=True).numpy()
     hist = np.zeros(CENSUS_BINS, dtype=np.int64)
     import ctypes as C
-    nc = C.c_int64(0)
-    tot = np.zeros(4)
-    census = lbm.FilmCensus()
+    rep = lbm.IntervalReport()
     vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
     barrier(world)
     torch.cuda.synchronize()
@@ -352,17 +349,17 @@ def run_ours(args, world, rank, local):
     for _ in range(args.steps):
         L.inject(rate_h, budget_pin)                      # H2D: rates and budgets
         L.step(INNER)
-        lib = lbm.lib()
-        lbm._check(lib.lbm_diagnose(L.handle, vp(tot), vp(labels), C.byref(nc)))
-        lbm._check(lib.lbm_film_cells(L.handle, FILM_H_MAX, FILM_EPS_ARM, C.byref(census),
-                                      vp(rec), FILM_CAP))
-        lbm._check(lib.lbm_bubble_sizes(L.handle, vp(roots), vp(sizes), len(roots), C.byref(nc),
-                                        vp(hist), CENSUS_BINS))  # D2H: totals, labels, census
+        # D2H: totals, labels, film census and fired cells, bubble census
+        lbm._check(lbm.lib().lbm_diagnostic_interval(
+            L.handle, FILM_H_MAX, FILM_EPS_ARM, vp(labels), vp(rec), FILM_CAP, vp(roots),
+            vp(sizes), len(roots), vp(hist), CENSUS_BINS, C.byref(rep)))
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
     h2d = rate_h.nbytes + budget_pin.nbytes
-    d2h = (labels.nbytes + tot.nbytes + 8 + 32 + lbm.FILM_CELL.itemsize * min(census.fired, FILM_CAP)
-           + 16 * min(nc.value, len(roots)) + hist.nbytes + 8)
+    # the results handed out per step: labels, totals, component count, film
+    # counts and fired cells, census entries and histogram
+    d2h = (labels.nbytes + 32 + 8 + 32 + lbm.FILM_CELL.itemsize * int(rep.nfired)
+           + 16 * int(rep.nsizes) + hist.nbytes)
 
     units = CELLS * INNER * args.steps  # per rank
     value = job_value(units, world, ms / 1e3)

@@ -360,6 +360,29 @@ typedef struct {
 lbm_status lbm_film_pairs(lbm_ctx *ctx, int32_t h_max, double eps_arm, lbm_film_census *census,
                           lbm_film_pair *pairs, int64_t cap, int64_t *npairs);
 
+/* One diagnostic interval in one call and one synchronisation: the FP64
+ * totals and gas labels of the current state (lbm_diagnose; labels[N] to
+ * host when labels is not NULL), the site
+ * labels and merge events (read afterwards with lbm_site_labels), the film
+ * test at every lattice point (lbm_film_cells: fired[q] for q < nfired, in
+ * (cell, axis) order) and the bubble census (lbm_bubble_sizes: roots[q],
+ * sizes[q] for q < nsizes in increasing root order, hist[nbins]).  Results
+ * are those of the separate calls on the same state; any output array may
+ * be NULL (its cap is then ignored).  Errors: EINVAL, ESTATE, ENOMEM,
+ * ECUDA. */
+typedef struct {
+  double totals[4];      /* as lbm_totals */
+  int64_t ncomp;         /* gas components */
+  int64_t merge_events;  /* cumulative, as lbm_site_labels */
+  lbm_film_census film;  /* as lbm_film_cells */
+  int64_t nfired;        /* fired records written */
+  int64_t nsizes;        /* census entries written */
+} lbm_interval_report;
+lbm_status lbm_diagnostic_interval(lbm_ctx *ctx, int32_t h_max, double eps_arm, int32_t *labels,
+                                   lbm_film_cell *fired, int64_t fired_cap, int64_t *roots,
+                                   int64_t *sizes, int64_t sizes_cap, int64_t *hist,
+                                   int32_t nbins, lbm_interval_report *out);
+
 /* FP64 totals: out[0] = sum rho, out[1..3] = sum j over all cells, with a
  * fixed-order block reduction (repeated calls give identical bits).  FP64
  * storage sums every population in FP64; the FP32-arithmetic storages sum

@@ -1198,6 +1198,109 @@ lbm_status lbm_film_pairs(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
   return LBM_OK;
 }
 
+lbm_status lbm_diagnostic_interval(lbm_ctx *c, int32_t h_max, double eps_arm, int32_t *labels,
+                                   lbm_film_cell *fired, int64_t fired_cap, int64_t *roots,
+                                   int64_t *sizes, int64_t sizes_cap, int64_t *hist,
+                                   int32_t nbins, lbm_interval_report *out) {
+  if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+  if (fired_cap < 0 || sizes_cap < 0 || nbins < 0 || nbins > 63 || (hist && nbins < 1))
+    return fail(LBM_EINVAL, "caps >= 0 and 1 <= nbins <= 63 when hist is given");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  CKS(set_device(c));
+  CKS(check_sticky(c));
+  const int nb = std::max(nbins, 1);
+  // everything of the interval on the stream: FP64 totals and labels (one
+  // pass), site labels, the film test, the census
+  CKS(enqueue_labels(c, true));
+  CKS(film_prepare(c, h_max, eps_arm));  // arming state and counters (labels are current)
+  CKS(dalloc(c, c->d_film_rec, film_record_bytes() * (size_t)std::max<int64_t>(fired_cap, 1)));
+  CK(diag_film_cells(c->v, static_cast<const int32_t *>(c->d_labels.p), lattice_ptr(c, c->cur),
+                     c->cfg.G, c->cfg.rho0, h_max, eps_arm,
+                     static_cast<uint8_t *>(c->d_film_state.p),
+                     static_cast<unsigned long long *>(c->d_film_counts.p), fired_cap,
+                     c->d_film_rec.p, false, c->s));
+  CKS(dalloc(c, c->d_count, sizeof(int32_t) * c->N));
+  // mailbox: [ncomp][totals 4][film counts 5][census block][fired records]
+  const size_t rec_bytes = fired ? sizeof(lbm_film_cell) * (size_t)fired_cap : 0;
+  const unsigned long long *census = nullptr;
+  unsigned char *mail = nullptr;
+  int64_t n = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t capdev = c->census_cap;
+    const size_t block = sizeof(int64_t) * (65 + 2 * (size_t)capdev);
+    CKS(dalloc(c, c->d_census, block));
+    auto *base = static_cast<unsigned long long *>(c->d_census.p);
+    int64_t *d_roots = reinterpret_cast<int64_t *>(base + 65), *d_sizes = d_roots + capdev;
+    CK(diag_bubble_sizes(c->v, static_cast<const int32_t *>(c->d_labels.p),
+                         static_cast<int32_t *>(c->d_count.p), base, capdev, d_roots, d_sizes,
+                         nb, base + 1, c->s));
+    CKS(halloc(c, c->h_mail, 80 + block + rec_bytes));
+    mail = static_cast<unsigned char *>(c->h_mail.p);
+    if (pass == 0) {
+      CK(cudaMemcpyAsync(mail, c->d_ncomp.p, 8, cudaMemcpyDeviceToHost, c->s));
+      CK(cudaMemcpyAsync(mail + 8, c->d_tot.p, 32, cudaMemcpyDeviceToHost, c->s));
+      CK(cudaMemcpyAsync(mail + 40, c->d_film_counts.p, 40, cudaMemcpyDeviceToHost, c->s));
+      if (labels)
+        CK(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost,
+                           c->s));
+      if (rec_bytes)
+        CK(cudaMemcpyAsync(mail + 80 + block, c->d_film_rec.p, rec_bytes, cudaMemcpyDeviceToHost,
+                           c->s));
+    }
+    CK(cudaMemcpyAsync(mail + 80, base, block, cudaMemcpyDeviceToHost, c->s));
+    CKS(sync_and_check(c));
+    census = reinterpret_cast<const unsigned long long *>(mail + 80);
+    n = (int64_t)census[0];
+    if (n <= capdev) break;
+    // more components than the census list holds: grow and redo the census
+    // only; the other results stay where they are in the mailbox
+    std::vector<unsigned char> keep(80);
+    std::memcpy(keep.data(), mail, 80);
+    std::vector<unsigned char> keep_rec(rec_bytes);
+    if (rec_bytes) std::memcpy(keep_rec.data(), mail + 80 + block, rec_bytes);
+    c->census_cap = n;
+    const size_t block2 = sizeof(int64_t) * (65 + 2 * (size_t)n);
+    CKS(halloc(c, c->h_mail, 80 + block2 + rec_bytes));
+    mail = static_cast<unsigned char *>(c->h_mail.p);
+    std::memcpy(mail, keep.data(), 80);
+    if (rec_bytes) std::memcpy(mail + 80 + block2, keep_rec.data(), rec_bytes);
+  }
+  count_merges(c);
+  const auto *w64 = reinterpret_cast<const unsigned long long *>(mail);
+  out->ncomp = (int64_t)w64[0];
+  std::memcpy(out->totals, mail + 8, 32);
+  out->film.film = (int64_t)w64[5];
+  out->film.midpoints = (int64_t)w64[6];
+  out->film.armed = (int64_t)w64[7];
+  out->film.fired = (int64_t)w64[8];
+  out->merge_events = c->merge_events;
+  if (n != out->ncomp) return fail(LBM_ECUDA, "interval: component count mismatch");
+  // census entries in increasing root order
+  const int64_t capdev = c->census_cap;
+  const auto *r = reinterpret_cast<const int64_t *>(census + 65);
+  const int64_t *sz = r + capdev;
+  std::vector<int64_t> order((size_t)n);
+  for (int64_t q = 0; q < n; ++q) order[q] = q;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return r[a] < r[b]; });
+  out->nsizes = std::min(n, sizes_cap);
+  for (int64_t q = 0; q < out->nsizes; ++q) {
+    if (roots) roots[q] = r[order[q]];
+    if (sizes) sizes[q] = sz[order[q]];
+  }
+  if (hist)
+    for (int b = 0; b < nbins; ++b) hist[b] = (int64_t)census[1 + b];
+  // fired film records in (cell, axis) order
+  const size_t block = sizeof(int64_t) * (65 + 2 * (size_t)capdev);
+  out->nfired = fired ? std::min<int64_t>(out->film.fired, fired_cap) : 0;
+  if (out->nfired > 0) {
+    std::memcpy(fired, mail + 80 + block, sizeof(lbm_film_cell) * (size_t)out->nfired);
+    std::sort(fired, fired + out->nfired, [](const lbm_film_cell &a, const lbm_film_cell &b) {
+      return a.cell != b.cell ? a.cell < b.cell : a.axis < b.axis;
+    });
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_site_labels(lbm_ctx *c, int32_t *site_labels, int32_t n, int64_t *merge_events) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (site_labels) {

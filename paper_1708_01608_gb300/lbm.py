@@ -71,6 +71,11 @@ class FilmCensus(C.Structure):
                 ("fired", C.c_int64)]
 
 
+class IntervalReport(C.Structure):
+    _fields_ = [("totals", C.c_double * 4), ("ncomp", C.c_int64), ("merge_events", C.c_int64),
+                ("film", FilmCensus), ("nfired", C.c_int64), ("nsizes", C.c_int64)]
+
+
 # lbm_film_cell as a numpy record
 FILM_CELL = np.dtype([("cell", np.int64), ("axis", np.int32), ("label_minus", np.int32),
                       ("label_plus", np.int32), ("thickness", np.int32), ("d2p", np.float64)],
@@ -126,6 +131,8 @@ def _load():
         "lbm_film_cells": (i32, [P_, i32, d, C.POINTER(FilmCensus), P_, i64]),
         "lbm_film_pairs": (i32, [P_, i32, d, C.POINTER(FilmCensus), P_, i64, C.POINTER(i64)]),
         "lbm_set_injection_mode": (i32, [P_, i32]),
+        "lbm_diagnostic_interval": (i32, [P_, i32, d, P_, P_, i64, P_, P_, i64, P_, i32,
+                                          C.POINTER(IntervalReport)]),
         "lbm_totals": (i32, [P_, P_]),
         "lbm_read": (i32, [P_, i32, P_, sz]),
         "lbm_write_f": (i32, [P_, P_, sz]),
@@ -156,6 +163,7 @@ EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites"
            "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose", "lbm_film_probe",
            "lbm_run_until_rupture",
            "lbm_site_labels", "lbm_bubble_sizes", "lbm_film_cells", "lbm_film_pairs",
+           "lbm_diagnostic_interval",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_last_error",
            "lbm_version", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_run",
            "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f")
@@ -424,6 +432,36 @@ class Lattice:
                                    int(cap)))
         return (dict(film=out.film, midpoints=out.midpoints, armed=out.armed, fired=out.fired),
                 rec[:min(out.fired, cap)].copy())
+
+    def diagnostic_interval(self, h_max=12, eps_arm=1e-3, fired_cap=4096, nbins=32,
+                            want_labels=False):
+        """Totals, labels, site labels, the film test and the bubble census of
+        the current state in one call (lbm_diagnostic_interval): dict with
+        totals, ncomp, merge_events, film (counts), fired (FILM_CELL records),
+        roots, sizes, hist, and labels (shape of the lattice) if asked."""
+        lab = np.empty(self.shape, dtype=np.int32) if want_labels else None
+        if len(self._film_buf) < max(fired_cap, 1):
+            self._film_buf = np.empty(max(fired_cap, 1), dtype=FILM_CELL)
+        roots, sizes = self._census_buf
+        hist = np.zeros(max(nbins, 1), dtype=np.int64)
+        rep = IntervalReport()
+        _check(_lib.lbm_diagnostic_interval(self._h, int(h_max), float(eps_arm),
+                                            _ptr(lab) if want_labels else None,
+                                            _ptr(self._film_buf), int(fired_cap), _ptr(roots),
+                                            _ptr(sizes), len(roots), _ptr(hist), int(nbins),
+                                            C.byref(rep)))
+        n = int(rep.ncomp)
+        if n > len(roots):
+            # more components than the kept arrays hold: the census alone,
+            # again on the same labels (the film test is not repeated)
+            roots, sizes, _ = self.bubble_sizes(nbins, cap=n)
+        else:
+            roots, sizes = roots[:n].copy(), sizes[:n].copy()
+        f = rep.film
+        return dict(totals=np.array(rep.totals[:]), ncomp=n, merge_events=int(rep.merge_events),
+                    film=dict(film=f.film, midpoints=f.midpoints, armed=f.armed, fired=f.fired),
+                    fired=self._film_buf[:int(rep.nfired)].copy(), roots=roots, sizes=sizes,
+                    hist=hist[:nbins], labels=lab)
 
     def film_pairs(self, h_max=12, eps_arm=1e-3, cap=1 << 14):
         """The film test reported per pair of bubbles (lbm_film_pairs):

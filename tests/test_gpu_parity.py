@@ -750,6 +750,41 @@ def test_spread_injection_needs_32_or_64_bit_storage(lbm):
     L.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_diagnostic_interval_equals_separate_calls(lbm, storage):
+    """lbm_diagnostic_interval (one synchronisation) against lbm_diagnose,
+    lbm_site_labels, lbm_film_cells and lbm_bubble_sizes called one by one
+    on a twin lattice in the same state: identical totals, labels, site
+    labels, merge events, film census and fired cells, bubble census; three
+    intervals 30 steps apart while two spheres' film drains."""
+    bub = np.array([[13.5, 20, 20, 10.0], [36.5, 20, 20, 10.0], [24, 6, 30, 4.0]])
+    f = as_stored("D3Q19", oracle_init("D3Q19", 48, 40, 40, bub, 2.0, 0.15, 2.0, 1e-3, 6),
+                  storage, 2.0)
+    twins = []
+    for _ in range(2):
+        L = lbm.Lattice("D3Q19", 48, 40, 40, tau=1.0, G=-5.0, storage=storage, rho_ref=2.0)
+        L.seed_bubbles(bub, 2.0, 0.15, 2.0, 1e-3, 6)  # registers the three sites
+        L.write_f(f)
+        twins.append(L)
+    A, B = twins
+    for call in range(3):
+        ra = A.diagnostic_interval(12, 1e-3, 4096, 16, want_labels=True)
+        tb, lab_b, nb = B.diagnose(want_labels=True)
+        cb, recb = B.film_cells(12, 1e-3, 4096)
+        rb, sb, hb = B.bubble_sizes(16)
+        site_b, ev_b = B.site_labels()
+        site_a, ev_a = A.site_labels()
+        assert (ra["totals"] == tb).all() and ra["ncomp"] == nb and (ra["labels"] == lab_b).all()
+        assert (site_a == site_b).all() and ra["merge_events"] == ev_a == ev_b
+        assert ra["film"] == cb and (ra["fired"] == recb).all()
+        assert (ra["roots"] == rb).all() and (ra["sizes"] == sb).all() and (ra["hist"] == hb).all()
+        assert ra["film"]["midpoints"] > 0 and ra["ncomp"] >= 2
+        A.step(30)
+        B.step(30)
+    A.close()
+    B.close()
+
+
 def test_bubble_sizes_many_components(lbm):
     """More components than the census list first holds: 32 x 32 x 48 with a
     gas cell at every even (x, y, z) is 6144 isolated cells, and six gas rows
