@@ -52,8 +52,16 @@ NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.8e6,
                           ("d3q19_foam_128", "f32", 5): 277.5e6,
                           ("d3q19_foam_128", "f32", 16): 277.35e6,
                           ("d3q19_foam_128", "f32", 25): 277.57e6,
+                          ("d3q19_foam_128", "f64", 6): 626.2e6,
                           ("d3q19_foam_512", "f16", 14): 8 * 1270.09e6,
                           ("d3q19_foam_768", "f16", 14): 27 * 1270.09e6}
+# FP64 storage: the step kernel is bound by the FP64 pipe, not by HBM.  FP64
+# operations per lattice update of its D3Q19 kernel, DADD + DMUL + 2 DFMA as
+# ncu counts them on the 128^3 case (146 + 71 + 2 x 332), and the FP64 peak
+# from the unit counts: 2 DFMA per SM and cycle x 152 SMs x 2 FLOP x 2.07 GHz.
+FP64_FLOP_PER_UPDATE = 881
+FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+STORAGE_NAME = {"f32": "FP32", "f64": "FP64", "f16": "FP16-offset", "bf16": "BF16-offset"}
 # D3Q19 tile ids of the x-pair kernel (fused_step_kernel_x2)
 X_PAIR_TILES = range(14, 26)
 
@@ -366,6 +374,19 @@ def run_ours(args, world, rank, local):
     e2e_val = job_value(units, world, e2e_s)
     peak, src = peak_hbm()
     achieved = B_ALG * CELLS / (step_kernel_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC_PER_LAUNCH.get((W["name"], W["storage"], plan[1]))
+    kname = "fused_step_kernel_x2" if plan[1] in X_PAIR_TILES else "fused_step_kernel"
+    if W["storage"] == "f64":
+        tflops = FP64_FLOP_PER_UPDATE * CELLS / (step_kernel_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived from unit counts and the 2.07 GHz clock",
+                    "traffic": traffic, "kernel": kname, "flop_per_update": FP64_FLOP_PER_UPDATE,
+                    "bytes_per_update": B_ALG, "kernel_ms": step_kernel_ms}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": src, "traffic": traffic,
+                    "kernel": kname, "bytes_per_update": B_ALG, "kernel_ms": step_kernel_ms}
     launches_per_step = INNER + DIAG_LAUNCHES
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -384,12 +405,7 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": src,
-                         "traffic": NCU_TRAFFIC_PER_LAUNCH.get((W["name"], W["storage"], plan[1])),
-                         "kernel": "fused_step_kernel_x2" if plan[1] in X_PAIR_TILES
-                                   else "fused_step_kernel", "bytes_per_update": B_ALG,
-                         "kernel_ms": step_kernel_ms},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -518,8 +534,8 @@ def main():
             return
         if args.workload == "foam512":
             W = dict(WL.FOAM_512)
-            METRIC = ("D3Q19 Shan-Chen MLUPS (512^3 foam, 1000 bubbles, diagnostics every "
-                      "100 steps)")
+            METRIC = ("D3Q19 Shan-Chen MLUPS (512^3 foam, FP32 storage, 1000 bubbles, "
+                      "diagnostics every 100 steps)")
         else:
             W = dict(WL.FOAM_768)
             METRIC = ("D3Q19 Shan-Chen MLUPS (768^3 full foam, FP16-offset storage, 4096 sites "
@@ -528,6 +544,8 @@ def main():
         CELLS = W["nx"] * W["ny"] * W["nz"]
         args.no_cpu_baseline = True
     if args.storage:
+        # the metric names the storage form measured
+        METRIC = METRIC.replace(STORAGE_NAME[W["storage"]], STORAGE_NAME[args.storage])
         W = dict(W, storage=args.storage)
     B_ALG = 2 * Q * {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[W["storage"]]
     try:
