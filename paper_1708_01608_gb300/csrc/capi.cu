@@ -314,6 +314,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
   }
   c->v.px = (c->v.NX + 7) / 8 * 8;
   c->v.rho_ref = cfg->rho_ref;
+  view_prepare(c->v);
   c->N = c->v.NX * c->v.NY * c->v.NZ;
   c->kernel = cfg->kernel == LBM_KERNEL_TWO_PASS ? LBM_KERNEL_TWO_PASS : LBM_KERNEL_FUSED;
   c->lat_bytes = (size_t)c->Q * c->v.px * c->v.NY * c->v.NZ * storage_bytes(c->st);

@@ -20,19 +20,31 @@ struct Idx {
 // Lattices hold fewer than 2^31 cells (lbm_create), so cell indices and
 // their decomposition use 32-bit arithmetic: a 64-bit division is a long
 // emulated sequence on the GPU, partly on the narrow FP64 pipe.
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f, uint32_t d) {
+  if (f.m == 0) return n / d;  // a view that was not prepared
+  const uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
 __device__ __forceinline__ Idx idx_of(int64_t k, const View &v) {
   Idx c;
   const uint32_t kk = (uint32_t)k, nx = (uint32_t)v.NX, ny = (uint32_t)v.NY;
-  const uint32_t r = kk / nx;
+  const uint32_t r = fdiv(kk, v.fx, nx);
   c.x = (int)(kk - r * nx);
-  const uint32_t zq = r / ny;
+  const uint32_t zq = fdiv(r, v.fy, ny);
   c.y = (int)(r - zq * ny);
   c.z = (int)zq;
   return c;
 }
+// periodic wrap: one add or subtract for a neighbour's coordinate, the
+// remainder only for coordinates further out
 __device__ __forceinline__ int wr(int a, int n) {
-  int r = a % n;
-  return r < 0 ? r + n : r;
+  if (a >= n) a -= n;
+  else if (a < 0) a += n;
+  if ((unsigned)a >= (unsigned)n) {
+    a %= n;
+    if (a < 0) a += n;
+  }
+  return a;
 }
 __device__ __forceinline__ int64_t lin(int x, int y, int z, const View &v) {
   return (int64_t)(((uint32_t)z * (uint32_t)v.NY + (uint32_t)y) * (uint32_t)v.NX + (uint32_t)x);
@@ -584,7 +596,20 @@ __global__ void __launch_bounds__(TPB)
         if ((unsigned)q >= (unsigned)n_a) q = ((q % n_a) + n_a) % n_a;
         return q;
       };
+      // the cell s steps along the axis: the cell's own index plus s strides,
+      // one period added or removed at the seam (|s| <= h_max < n_a; axes no
+      // longer than h_max take the general wrap)
+      const int stride = va == 0 ? 1 : (va == 1 ? (int)v.NX : (int)(v.NX * v.NY));
+      const int period = n_a * stride;
+      const bool short_axis = n_a <= h_max;
       auto cell_at = [&](int s) -> int64_t {
+        if (!short_axis) {
+          const int q = c_a + s;
+          int idx = (int)k + s * stride;
+          if (q >= n_a) idx -= period;
+          else if (q < 0) idx += period;
+          return idx;
+        }
         const int q = wrap_a(c_a + s);
         const int xx = va == 0 ? q : x, yy = va == 1 ? q : y, zz = va == 2 ? q : z;
         return lin(xx, yy, zz, v);
@@ -599,17 +624,20 @@ __global__ void __launch_bounds__(TPB)
       int32_t Lp = -1, Lm = -1;
       int dp = 0, dm = 0;
       if (liquid) {
-        // first gas cell within h_max along +e (then -e), four loads in flight
+        // first gas cell within h_max along +e (then -e): the labels of a
+        // whole walk of FILM_CHUNK cells are loaded at once, so that a cell
+        // with no gas near it waits for one round trip per direction
+        constexpr int FILM_CHUNK = 12;
         auto first_gas = [&](int sign, int32_t &lab_out) -> int {
-          for (int s0 = 1; s0 <= h_max; s0 += 4) {
-            int32_t l4[4];
+          for (int s0 = 1; s0 <= h_max; s0 += FILM_CHUNK) {
+            int32_t lq[FILM_CHUNK];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              l4[q] = s0 + q <= h_max ? labels[cell_at(sign * (s0 + q))] : -1;
+            for (int q = 0; q < FILM_CHUNK; ++q)
+              lq[q] = s0 + q <= h_max ? labels[cell_at(sign * (s0 + q))] : -1;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (l4[q] >= 0) {
-                lab_out = l4[q];
+            for (int q = 0; q < FILM_CHUNK; ++q)
+              if (lq[q] >= 0) {
+                lab_out = lq[q];
                 return s0 + q;
               }
           }

@@ -568,6 +568,7 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
     const lbm_domain &s = dom[d];
     const EnsDomain &D = E->hdom[d];
     View v{D2Q9, ST_F32, D.NX, 1, D.NZ, D.px, s.rho_ref};
+    view_prepare(v);
     double hb[16];
     for (int b = 0; b < s.nbubbles; ++b) {
       hb[4 * b + 0] = s.bubbles[b].x;
@@ -687,6 +688,7 @@ lbm_status lbm_ensemble_read_f(lbm_ensemble *E, int32_t d, double *host, size_t 
   const int64_t its = s.active ? E->steps : s.step;
   const float *lat = (its & 1) ? D.latB : D.latA;
   View v{D2Q9, ST_F32, D.NX, 1, D.NZ, D.px, D.rho_ref};
+  view_prepare(v);
   void *p;
   ECKS(ealloc(E, N * sizeof(double), &p));
   double *tmp = static_cast<double *>(p);

@@ -116,11 +116,35 @@ int fused_x2_smem_bf16(int lat, int tile);
 cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi_scratch, cudaStream_t s);
 
 // ---- diagnostics / state kernels (diag.cu) --------------------------------
+// n / d for every 32-bit n with one multiply-high and two shifts: division
+// by an invariant integer (Granlund and Montgomery, PLDI 1994, Fig. 4.1).
+// The kernels' runtime 32-bit divisions otherwise run as a sequence on the
+// FP64 pipe, which is narrow on this part.  m = 0: not prepared.
+struct FastDiv {
+  uint32_t m = 0;
+  int s1 = 0, s2 = 0;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  int l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  // d < 2^31, so 2^32 (2^l - d) < 2^63 and m < 2^32
+  f.m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l - f.s1;
+  return f;
+}
+
 struct View {
   int lat, st;
   int64_t NX, NY, NZ, px;
   double rho_ref;
+  FastDiv fx, fy;  // division by NX and by NY (view_prepare)
 };
+inline void view_prepare(View &v) {
+  v.fx = make_fastdiv((uint32_t)v.NX);
+  v.fy = make_fastdiv((uint32_t)v.NY);
+}
 // initial density field (doubles, N) from bubbles (view coordinates, x y z r)
 cudaError_t diag_init_rho(const View &v, const double *bub, int32_t nb, double rho_l,
                           double rho_g, double width, double noise_amp, uint64_t seed,
