@@ -20,11 +20,6 @@ struct Idx {
 // Lattices hold fewer than 2^31 cells (lbm_create), so cell indices and
 // their decomposition use 32-bit arithmetic: a 64-bit division is a long
 // emulated sequence on the GPU, partly on the narrow FP64 pipe.
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f, uint32_t d) {
-  if (f.m == 0) return n / d;  // a view that was not prepared
-  const uint32_t t = __umulhi(f.m, n);
-  return (t + ((n - t) >> f.s1)) >> f.s2;
-}
 __device__ __forceinline__ Idx idx_of(int64_t k, const View &v) {
   Idx c;
   const uint32_t kk = (uint32_t)k, nx = (uint32_t)v.NX, ny = (uint32_t)v.NY;

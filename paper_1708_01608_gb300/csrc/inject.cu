@@ -69,8 +69,11 @@ __global__ void __launch_bounds__(TPB)
     if (lab < 0) continue;
     const double d = dep[lab];
     if (d == 0.0) continue;
-    const int64_t x = k % v.NX, yz = k / v.NX, y = yz % v.NY, z = yz / v.NY;
-    const int64_t o = (z * v.NY + y) * v.px + x;
+    // cell coordinates with the view's invariant-integer divisors
+    const uint32_t kk = (uint32_t)k, nx = (uint32_t)v.NX, ny = (uint32_t)v.NY;
+    const uint32_t yz = fdiv(kk, v.fx, nx), z = fdiv(yz, v.fy, ny);
+    const int64_t x = kk - yz * nx, y = yz - z * ny;
+    const int64_t o = ((int64_t)z * v.NY + y) * v.px + x;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) add_w<ST>(lat, pop, i * pop + o, L::w(i), d);
   }

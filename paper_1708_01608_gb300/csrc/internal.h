@@ -145,6 +145,13 @@ inline void view_prepare(View &v) {
   v.fx = make_fastdiv((uint32_t)v.NX);
   v.fy = make_fastdiv((uint32_t)v.NY);
 }
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f, uint32_t d) {
+  if (f.m == 0) return n / d;  // a view that was not prepared
+  const uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+#endif
 // initial density field (doubles, N) from bubbles (view coordinates, x y z r)
 cudaError_t diag_init_rho(const View &v, const double *bub, int32_t nb, double rho_l,
                           double rho_g, double width, double noise_amp, uint64_t seed,
