@@ -13,7 +13,7 @@ configuration: with 1e-3 initial noise the FP64 oracle's own h_c moves by
 up to 10 % between noise seeds, so any perturbation of that size (storage
 rounding included) shifts it as much; without noise it is a well-conditioned
 function of the configuration.  The measured values are printed (pytest -s)
-and written to gpurun_out/precision_study.json when that directory exists.
+and written as JSON to the path in PRECISION_STUDY_OUT when it is set.
 """
 import json
 import math
@@ -52,9 +52,9 @@ def lbm():
 
 
 def teardown_module(module):
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out) and RESULTS:
-        with open(os.path.join(out, "precision_study.json"), "w") as fh:
+    out = os.environ.get("PRECISION_STUDY_OUT")
+    if out and RESULTS:
+        with open(out, "w") as fh:
             json.dump(RESULTS, fh, indent=1, sort_keys=True)
 
 
