@@ -59,6 +59,22 @@ def test_null_arguments(lbm):
     assert "NULL" in L.lbm_last_error().decode()
 
 
+def test_null_arguments_of_diagnostics_and_modes(lbm):
+    """The film pair census, the one-call interval, the injection mode and
+    the ensemble's calls reject a missing context before any device work."""
+    L = lbm.lib()
+    census = lbm.FilmCensus()
+    n = C.c_int64(0)
+    assert L.lbm_film_pairs(None, 12, 1e-3, C.byref(census), None, 0, C.byref(n)) == lbm.EINVAL
+    rep = lbm.IntervalReport()
+    assert L.lbm_diagnostic_interval(None, 12, 1e-3, None, None, 0, None, None, 0, None, 0,
+                                     C.byref(rep)) == lbm.EINVAL
+    assert L.lbm_set_injection_mode(None, 1) == lbm.EINVAL
+    assert L.lbm_film_cells(None, 12, 1e-3, C.byref(census), None, 0) == lbm.EINVAL
+    assert L.lbm_bubble_sizes(None, None, None, 0, None, None, 0) == lbm.EINVAL
+    assert L.lbm_ensemble_run(None, 10, None) == lbm.EINVAL
+
+
 @pytest.mark.parametrize("args", [
     (128, 128, 128, 64, 3.0, 3.0, 12.0, 0.0, 1),
     (64, 64, 64, 30, 4.0, 12.0, 0.0, 4.0, 2),
