@@ -175,6 +175,36 @@ def max_over_ranks(world, x):
     return float(t.item())
 
 
+def sum_over_ranks(world, x):
+    """The sum of x over the ranks: every rank gets it."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def gather_lists(world, items):
+    """The concatenation of every rank's list, on every rank."""
+    if world == 1:
+        return list(items)
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, list(items))
+    return [x for part in out for x in part]
+
+
+def ensemble_shard(domains, world, rank):
+    """The domains of one rank: sorted by cells (largest first, ties by
+    index) and dealt round-robin, so that every rank gets a like share of
+    the cells; the ranks' shards are disjoint and cover all domains."""
+    order = sorted(range(len(domains)), key=lambda d: (-domains[d]["nx"] * domains[d]["ny"], d))
+    return [domains[d] for d in order[rank::world]]
+
+
 def job_value(units_per_rank, world, seconds):
     """Whole-job throughput in millions of units per second: every rank
     processes units_per_rank (independent replicas), the job takes the
@@ -413,34 +443,49 @@ def run_ours(args, world, rank, local):
     L.close()
 
 
-def run_ensemble(args):
+def run_ensemble(args, world=1, rank=0, local=0):
     """The batched two-bubble sweep (256 uneven D2Q9 domains) run until every
-    criterion fired or 20000 steps; MLUPS over all domain updates."""
+    criterion fired or 20000 steps; MLUPS over all domain updates.  With N
+    ranks the domains are sharded over the GPUs (independent problems, no
+    exchange): the job's time is the slowest rank's, its updates the sum."""
     import torch
     from paper_1708_01608_gb300 import build_lib
     from paper_1708_01608_gb300 import workloads as WL
-    build_lib.build()
+    if rank == 0 or not build_lib.up_to_date():
+        build_lib.build()
+    barrier(world)
     from paper_1708_01608_gb300 import lbm
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(local)
     R = WL.ENSEMBLE_256
-    doms = WL.ensemble_domains(R)
+    all_doms = WL.ensemble_domains(R)
+    doms = ensemble_shard(all_doms, world, rank)
     E = lbm.Ensemble(doms, eps_arm=R["eps_arm"], diag_every=R["diag_every"], h_max=R["h_max"])
+    barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     E.run(R["steps"])
-    dt = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    dt = max_over_ranks(world, time.perf_counter() - t0)
+    barrier(world)
     st = E.stats()
     res = E.results()
-    fired = [(d["R"], r["h_c"], r["r_d"], r["steps"]) for d, r in zip(doms, res) if r["fired"]]
+    updates = sum_over_ranks(world, st["updates"])
+    fired = gather_lists(world, [(d["R"], r["h_c"], r["r_d"], r["steps"])
+                                 for d, r in zip(doms, res) if r["fired"]])
+    fired.sort()
+    merged = int(sum_over_ranks(world, sum(r["merged"] for r in res)))
+    launches = int(sum_over_ranks(world, st["launches"]))
+    steps = int(max_over_ranks(world, st["steps"]))
     line = {"metric": "batched D2Q9 ensemble MLUPS (256 two-bubble domains, run to the rupture "
                       "criterion or 20000 steps)",
-            "value": st["updates"] / dt / 1e6, "unit": UNIT, "n_gpus": 1, "steps": st["steps"],
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": R["name"], "domains": len(doms),
-                       "cells": int(sum(d["nx"] * d["ny"] for d in doms)),
-                       "diag_every": R["diag_every"], "eps_arm": R["eps_arm"], "h_max": R["h_max"]},
-            "seconds": dt, "updates": st["updates"], "launches": st["launches"],
-            "fired": len(fired), "merged": sum(r["merged"] for r in res),
+            "value": updates / dt / 1e6, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": R["name"], "domains": len(all_doms),
+                       "cells": int(sum(d["nx"] * d["ny"] for d in all_doms)),
+                       "diag_every": R["diag_every"], "eps_arm": R["eps_arm"], "h_max": R["h_max"],
+                       "parallelism": f"domains sharded over {world} GPU(s)"},
+            "seconds": dt, "updates": updates, "launches": launches,
+            "fired": len(fired), "merged": merged,
             "h_c_vs_R": [[round(a, 2), round(b, 3), round(c, 1), s] for a, b, c, s in fired]}
     if len(fired) >= 3:
         # the functional forms of Fig. 3 fitted to the fired domains (R_b = disk radius)
@@ -448,7 +493,9 @@ def run_ensemble(args):
         line["fig3_fit"] = fit_fig3([a for a, _, _, _ in fired], [c for _, _, c, _ in fired],
                                     [b for _, b, _, _ in fired])
     E.close()
-    if args.single:
+    if rank != 0:
+        return
+    if args.single and world == 1:
         upd, t_single = 0.0, 0.0
         for dm in doms:
             L = lbm.Lattice("D2Q9", dm["nx"], dm["ny"], 1, tau=dm["tau"], G=dm["G"],
@@ -530,7 +577,12 @@ def main():
         global W, METRIC, INNER, CELLS, B_ALG
         from paper_1708_01608_gb300 import workloads as WL
         if args.workload == "ensemble256":
-            run_ensemble(args)
+            try:
+                run_ensemble(args, world, rank, local)
+            finally:
+                if world > 1:
+                    import torch.distributed as dist
+                    dist.destroy_process_group()
             return
         if args.workload == "foam512":
             W = dict(WL.FOAM_512)

@@ -34,6 +34,9 @@ def _rank_main(rank, world, port, out):
         bench.barrier(w)
         t = bench.max_over_ranks(w, 1.5 + rank)   # rank 1 is the slow one
         rate = bench.job_value(1e6, w, t)
+        # the sharded ensemble's host logic: summed updates, gathered rows
+        total = bench.sum_over_ranks(w, 10.0 * (rank + 1))
+        rows = bench.gather_lists(w, [(rank, k) for k in range(rank + 1)])
         # the reference arm: rank 0 alone runs and prints
         buf = io.StringIO()
 
@@ -43,7 +46,7 @@ def _rank_main(rank, world, port, out):
         bench.CELLS = 16 ** 3
         with redirect_stdout(buf):
             bench.run_reference(A, w, r)
-        out.put((r, t, rate, buf.getvalue()))
+        out.put((r, t, rate, buf.getvalue(), total, rows))
     finally:
         dist.destroy_process_group()
 
@@ -60,7 +63,26 @@ def test_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, t0, v0, o0), (r1, t1, v1, o1) = res
+    (r0, t0, v0, o0, s0, g0), (r1, t1, v1, o1, s1, g1) = res
+    assert s0 == s1 == 30.0                        # sum over ranks
+    assert g0 == g1 == [(0, 0), (1, 0), (1, 1)]    # every rank's rows, rank order
     assert t0 == t1 == 2.5                         # max over ranks
     assert v0 == v1 == pytest.approx(2e6 / 2.5 / 1e6)  # both replicas' units / slowest time
     assert '"impl": "reference"' in o0 and o1 == ""   # rank 0 prints, rank 1 does no work
+
+
+def test_ensemble_shards_cover_the_domains_once():
+    """The ensemble's domains over N ranks: disjoint shards that together
+    are all domains, each with a like share of the cells."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1708_01608_gb300.workloads import ENSEMBLE_256, ensemble_domains
+    doms = ensemble_domains(ENSEMBLE_256)
+    total = sum(d["nx"] * d["ny"] for d in doms)
+    for world in (1, 2, 4, 8):
+        shards = [bench.ensemble_shard(doms, world, r) for r in range(world)]
+        seen = sorted(id(d) for sh in shards for d in sh)
+        assert seen == sorted(id(d) for d in doms)
+        cells = [sum(d["nx"] * d["ny"] for d in sh) for sh in shards]
+        assert sum(cells) == total
+        assert max(cells) - min(cells) <= max(d["nx"] * d["ny"] for d in doms)
