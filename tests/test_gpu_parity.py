@@ -303,14 +303,16 @@ def test_conservation_fp32_full_foam_128(lbm):
     L.close()
 
 
-def test_full_size_sampled_cells_fp32(lbm):
-    """128^3 FP32, bench launch plan: one step checked cell by cell."""
+@pytest.mark.parametrize("tile", [0, 25])
+def test_full_size_sampled_cells_fp32(lbm, tile):
+    """128^3 FP32 foam, one step checked cell by cell: the default plan and
+    the x-pair tile 25 the bench's autotuner picks at this size."""
     from paper_1708_01608_gb300.workloads import FOAM_128 as W
     s = W["sites"]
     bub = lbm.sample_sites(128, 128, 128, s["n"], s["r_min"], s["r_max"], s["min_spacing"],
                            s["min_gap"], W["seed"])
     L = lbm.Lattice("D3Q19", 128, 128, 128, tau=W["tau"], G=W["G"], storage="f32",
-                    rho_ref=W["rho_ref"])
+                    rho_ref=W["rho_ref"], kernel="fused" if tile else "auto", tile=tile)
     L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
     f_init = oracle_init("D3Q19", 128, 128, 128, bub, W["rho_l"], W["rho_g"], W["width"],
                          W["noise"], W["seed"])
@@ -326,6 +328,35 @@ def test_full_size_sampled_cells_fp32(lbm):
     got = f1[:, cells].T
     assert rel_err(got, ref) < 1e-5
     L.close()
+
+
+@pytest.mark.parametrize("n,period,storage,tile", [(512, 64, "f16", 14), (512, 64, "f32", 16),
+                                                   (768, 128, "f16", 14)])
+def test_full_size_periodic_state(lbm, n, period, storage, tile):
+    """The 512^3 and 768^3 workloads' sizes in the x-pair plans the bench's
+    autotuner picks for them (tile 14 for FP16, 16 for FP32; z chunks from
+    the wave model): a state periodic with period p (one bubble per p^3
+    block, no noise) stays periodic, so after 5 steps every block of the
+    density is bit-identical to every other (every CTA, tile seam and z
+    chunk of the launch computes the same update), and the first block
+    matches the FP64 oracle run on one period from the same stored state."""
+    k, c, r = n // period, period / 2, 10.0
+    bub = np.array([[c + period * i, c + period * j, c + period * l, r]
+                    for i in range(k) for j in range(k) for l in range(k)])
+    L = lbm.Lattice("D3Q19", n, n, n, tau=0.8, G=-5.0, storage=storage, rho_ref=2.0,
+                    kernel="fused", tile=tile)
+    L.seed_bubbles(bub, 2.0, 0.15, 2.0, 0.0, 1)
+    assert L.plan()[1] == tile and L.plan()[4] > 1
+    L.step(5)
+    rho = L.read("rho")
+    L.close()
+    blocks = rho.reshape(k, period, k, period, k, period)
+    first = blocks[0, :, 0, :, 0, :]
+    assert (blocks == first[None, :, None, :, None, :]).all()
+    f0 = as_stored("D3Q19", oracle_init("D3Q19", period, period, period, [[c, c, c, r]], 2.0,
+                                        0.15, 2.0, 0.0, 1), storage, 2.0)
+    ro = O.moments(O.D3Q19, O.run(O.D3Q19, f0, 5, 0.8, -5.0))[0]
+    assert rel_err(first, ro) < TOL[storage], rel_err(first, ro)
 
 
 def test_deterministic_bits(lbm):
