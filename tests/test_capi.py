@@ -40,7 +40,10 @@ def test_version(lbm):
 
 @pytest.mark.parametrize("kw", [
     dict(lattice="D2Q9", nz=2), dict(nx=0), dict(tau=0.5), dict(tau=float("nan")),
-    dict(rho0=0.0), dict(storage=7), dict(kernel=9), dict(lattice=5)])
+    dict(rho0=0.0), dict(storage=7), dict(kernel=9), dict(lattice=5),
+    # size limits: an extent above 2^20; padded cells (x rounded up to 8) at 2^31
+    dict(nx=2**20 + 8, ny=1, nz=1), dict(nx=1024, ny=1024, nz=2048),
+    dict(nx=1020, ny=1024, nz=2048)])
 def test_create_rejects_bad_config_without_gpu(lbm, kw):
     args = dict(lattice="D3Q19", nx=8, ny=8, nz=8, torch_memory=False)
     args.update(kw)

@@ -359,6 +359,37 @@ def test_full_size_periodic_state(lbm, n, period, storage, tile):
     assert rel_err(first, ro) < TOL[storage], rel_err(first, ro)
 
 
+@pytest.mark.parametrize("lat,storage,ext,period,r", [
+    ("D2Q9", "f32", (2**20, 32, 1), (1024, 32, 1), 8.0),   # largest x extent
+    ("D3Q19", "f16", (8, 8, 2**20), (8, 8, 1024), 3.0),    # largest z extent
+    ("D2Q9", "f16", (46336, 46336, 1), (2896, 2896, 1), 20.0),  # 2^31 - 458752 cells
+])
+def test_maximum_sizes(lbm, lat, storage, ext, period, r):
+    """Extents at the limits lbm_create accepts (2^20 along an axis; padded
+    cells just below 2^31, where the kernels' 32-bit cell offsets end): a
+    state periodic with one bubble per block stays periodic bit for bit over
+    5 steps, and its first block matches the FP64 oracle run on one block."""
+    k = [e // q for e, q in zip(ext, period)]
+    cen = [q / 2 if q > 1 else 0.0 for q in period]
+    bub = np.array([[cen[0] + period[0] * i, cen[1] + period[1] * j, cen[2] + period[2] * l, r]
+                    for i in range(k[0]) for j in range(k[1]) for l in range(k[2])])
+    L = lbm.Lattice(lat, *ext, tau=0.8, G=-5.0, storage=storage, rho_ref=2.0)
+    L.seed_bubbles(bub, 2.0, 0.15, 2.0, 0.0, 1)
+    L.step(5)
+    rho = L.read("rho")
+    L.close()
+    nx, ny, nz = ext
+    px_, py_, pz_ = period
+    blocks = rho.reshape(k[2], pz_, k[1], py_, k[0], px_)
+    first = blocks[0, :, 0, :, 0, :]
+    assert (blocks == first[None, :, None, :, None, :]).all()
+    del blocks, rho
+    f0 = as_stored(lat, oracle_init(lat, px_, py_, pz_, [[cen[0], cen[1], cen[2], r]], 2.0, 0.15,
+                                    2.0, 0.0, 1), storage, 2.0)
+    ro = O.moments(LAT[lat], O.run(LAT[lat], f0, 5, 0.8, -5.0))[0]
+    assert rel_err(first, ro) < TOL[storage], rel_err(first, ro)
+
+
 def test_deterministic_bits(lbm):
     out = []
     for _ in range(2):
