@@ -53,6 +53,7 @@ NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.8e6,
                           ("d3q19_foam_128", "f32", 16): 277.35e6,
                           ("d3q19_foam_128", "f32", 25): 277.57e6,
                           ("d3q19_foam_128", "f64", 6): 626.2e6,
+                          ("d3q19_foam_512", "f32", 16): 8 * 2534.04e6,
                           ("d3q19_foam_512", "f16", 14): 8 * 1270.09e6,
                           ("d3q19_foam_768", "f16", 14): 27 * 1270.09e6}
 # FP64 storage: the step kernel is bound by the FP64 pipe, not by HBM.  FP64
