@@ -2,11 +2,13 @@
 
 Each mutation below is a plausible slip in sc_oracle.c (a coefficient, a
 sign, an index, a weight, the tau factor, the streaming direction, the
-injection, the minimum image, the RNG, the site spacing, the film probe).
-The test compiles a mutated copy into a temporary directory and runs
-tests/test_oracle_pins.py against it; every mutant must fail at least one
-pin.  The unmutated copy must pass.  Mutations live only in the temporary
-copies: the oracle's source is never written.
+injection, the minimum image, the RNG, the site spacing, the film probe)
+or in the oracle's Python layer (the spread injection, the per-pair film
+census, the rupture criterion).  The test builds a mutated copy in a
+temporary directory and runs tests/test_oracle_pins.py against it; every
+mutant must fail at least one pin.  The unmutated copy must pass.
+Mutations live only in the temporary copies: the oracle's source is never
+written.
 """
 import concurrent.futures as cf
 import os
@@ -69,6 +71,26 @@ MUTATIONS = [
     ("} else if ((state[k] & bit) && d2 >= 0.0) {", "} else if (d2 >= 0.0) {"),
 ]
 
+# the same for the oracle's Python layer (oracle/__init__.py): the blowing
+# agent spread over a bubble, the per-pair film census, the rupture criterion
+PY_MUTATIONS = [
+    ("per_cell = total / sizes[key]", "per_cell = total"),
+    ("flat[i, cells] += w[i] * per_cell", "flat[i, cells] += per_cell / Q"),
+    ("                d = min(rate[s], budget[s])\n", "                d = rate[s]\n"),
+    ("flat[i, -1 - key] += w[i] * total", "flat[i, -1 - key] += w[i] * total / Q"),
+    ("r_d = float(np.sqrt(n / np.pi)) if dims == 3 else n / 2.0",
+     "r_d = float(np.sqrt(n / np.pi)) if dims == 3 else float(n)"),
+    ("r_d = float(np.sqrt(n / np.pi)) if dims == 3 else n / 2.0",
+     "r_d = float(np.sqrt(n)) if dims == 3 else n / 2.0"),
+    ("key=lambda q: (len(g[\"lines\"][q]), -q))", "key=lambda q: (g[\"mid\"][q], -q))"),
+    ("h_c = g[\"tsum\"] / g[\"fired\"] if g[\"fired\"] else 0.0",
+     "h_c = g[\"tsum\"] if g[\"fired\"] else 0.0"),
+    ("else min(g[\"hmin\"][a], t)", "else max(g[\"hmin\"][a], t)"),
+    ("h_c = h0 + (h - h0) * (-d0 / (d - d0))", "h_c = h"),
+    ("    if h > h_max:\n        armed = False\n", "    if h > h_max:\n        pass\n"),
+    ("    elif d < -eps_arm:\n", "    elif d < 0.0:\n"),
+]
+
 
 def _compile(tmp, name, text):
     d = os.path.join(tmp, name)
@@ -87,6 +109,49 @@ def _pins(lib):
                         "test_oracle_pins.py"), "-x", "-q", "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     return r.returncode, r.stdout[-400:]
+
+
+def _py_tree(tmp, name, text):
+    """A copy of the oracle package with a mutated __init__.py beside a copy of
+    the pins (their conftest puts the copy's root first on sys.path)."""
+    d = os.path.join(tmp, name)
+    os.makedirs(os.path.join(d, "oracle"))
+    with open(os.path.join(d, "oracle", "__init__.py"), "w") as fh:
+        fh.write(text)
+    shutil.copy(O.SRC, os.path.join(d, "oracle", "sc_oracle.c"))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
+    for f in ("conftest.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(d, "tests", f))
+    return d
+
+
+def _py_pins(args):
+    root, lib = args
+    env = dict(os.environ, SC_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(root, "tests",
+                        "test_oracle_pins.py"), "-x", "-q", "-p", "no:cacheprovider"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=900)
+    return r.returncode, r.stdout[-400:]
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc needed")
+def test_planted_mistakes_in_the_python_layer_fail_the_pins(tmp_path):
+    init = os.path.join(os.path.dirname(O.SRC), "__init__.py")
+    with open(init) as fh:
+        orig = fh.read()
+    with open(O.SRC) as fh:
+        lib = _compile(str(tmp_path), "lib", fh.read())
+    jobs = {"unmutated": (_py_tree(str(tmp_path), "unmutated", orig), lib)}
+    for k, (a, b) in enumerate(PY_MUTATIONS):
+        assert orig.count(a) == 1, a
+        jobs[f"p{k:02d}: {a[:60]}"] = (_py_tree(str(tmp_path), f"p{k:02d}", orig.replace(a, b)),
+                                       lib)
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
+        res = dict(zip(jobs, ex.map(_py_pins, jobs.values())))
+    rc, out = res.pop("unmutated")
+    assert rc == 0, out
+    survivors = [name for name, (rc, _) in res.items() if rc == 0]
+    assert not survivors, survivors
 
 
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc needed")

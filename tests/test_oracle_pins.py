@@ -745,6 +745,47 @@ def test_film_pairs_three_bubbles_two_films():
     assert sum(r[4] for r in rows) == c["midpoints"] == len(mids)
 
 
+def test_film_pairs_h_min_is_the_thinnest_line():
+    """Gas blocks A and B over rows 0..9 with a film along x whose thickness
+    alternates 3 (even rows) and 5 (odd rows): one film line per row,
+    h_min = 3 (not the thickest run, 5); R_d = 10 / 2."""
+    nx, ny = 40, 30
+    rho = np.full((1, ny, nx), 2.0)
+    rho[0, 0:10, 4:12] = 0.2                       # A
+    for y in range(10):
+        rho[0, y, 12 + (3 if y % 2 == 0 else 5):25] = 0.2   # B, a comb on its left side
+    lab, n = O.label_gas(O.D2Q9, rho, 1.0)
+    assert n == 2
+    st = np.zeros(lab.shape, dtype=np.uint8)
+    c, mids = O.film_midpoints(O.D2Q9, lab, np.zeros(lab.shape), 12, 1e-3, st)
+    rows = O.film_pairs(O.D2Q9, lab.shape, mids)
+    assert rows == [(4, 15, 0, 10, 10, 3, 5.0, 0, 0.0)]
+
+
+def test_film_pairs_axis_with_most_lines_not_most_midpoints():
+    """Gas block A (x 0..9, rows 0..9) and an L-shaped B: an arm right of A
+    over rows 0..2 leaves an even 4-cell film along x (3 lines, 6
+    midpoints); an arm above A over columns 6..9 leaves an odd 3-cell film
+    along y (4 lines, 4 midpoints); a connector far to the right joins the
+    arms (none of B's other runs comes within 12 cells of A).  The film
+    lies across the axis with the most lines, y:
+    (A, B, axis 1, 4 lines, 4 midpoints, h_min 3, R_d 2)."""
+    nx, ny = 48, 30
+    rho = np.full((1, ny, nx), 2.0)
+    rho[0, 0:10, 0:10] = 0.2      # A
+    rho[0, 0:3, 14:31] = 0.2      # B: arm right of A (liquid x 10..13)
+    rho[0, 0:17, 26:31] = 0.2     # B: connector
+    rho[0, 13:17, 6:31] = 0.2     # B: arm above A (liquid rows 10..12 over x 6..9)
+    lab, n = O.label_gas(O.D2Q9, rho, 1.0)
+    assert n == 2
+    st = np.zeros(lab.shape, dtype=np.uint8)
+    c, mids = O.film_midpoints(O.D2Q9, lab, np.zeros(lab.shape), 12, 1e-3, st)
+    by_axis = [int((np.asarray(mids)[:, 1] == a).sum()) for a in (0, 1)]
+    assert by_axis == [6, 4]
+    rows = O.film_pairs(O.D2Q9, lab.shape, mids)
+    assert rows == [(0, 14, 1, 4, 4, 3, 2.0, 0, 0.0)]
+
+
 # ---------------------------------------------- injection spread over a bubble
 def _disk_state(nx=48, ny=40, r=8.0, seed=3):
     f, rho = O.init(O.D2Q9, nx, ny, 1, np.array([[20.0, 20.0, 0.0, r]]), 2.0, 0.15, 2.0, 1e-3,
