@@ -768,6 +768,44 @@ def test_film_pairs_3d_row_of_spheres_match_oracle(lbm):
     L.close()
 
 
+def _comb_pair():
+    """Gas blocks A, B over rows 0..9; the film along x is 3 cells thick on
+    even rows and 5 on odd rows."""
+    rho = np.full((1, 30, 40), 2.0)
+    rho[0, 0:10, 4:12] = 0.2
+    for y in range(10):
+        rho[0, y, 12 + (3 if y % 2 == 0 else 5):25] = 0.2
+    return rho
+
+
+def _l_pair():
+    """Block A and an L-shaped B: a 4-cell film along x over 3 rows and a
+    3-cell film along y over 4 columns."""
+    rho = np.full((1, 30, 48), 2.0)
+    rho[0, 0:10, 0:10] = 0.2
+    rho[0, 0:3, 14:31] = 0.2
+    rho[0, 0:17, 26:31] = 0.2
+    rho[0, 13:17, 6:31] = 0.2
+    return rho
+
+
+@pytest.mark.parametrize("geometry,axis,h_min", [(_comb_pair, 0, 3), (_l_pair, 1, 3)])
+def test_film_pairs_constructed_geometries_match_oracle(lbm, geometry, axis, h_min):
+    """A film of alternating thickness, and a pair whose film crosses both
+    axes, as states at rest (f_i = w_i rho): the GPU's per-pair census equals
+    the oracle's (the thinnest line; the axis with the most lines)."""
+    rho = geometry()
+    _, w = O.velocities(O.D2Q9)
+    f = w[:, None, None, None] * rho[None]
+    nz, ny, nx = rho.shape
+    L = lbm.Lattice("D2Q9", nx, ny, 1, tau=1.0, G=-5.0, storage="f64")
+    L.write_f(f)
+    got = L.film_pairs(12, 1e-3)
+    L.close()
+    _same_pairs(got, _pairs_oracle(O.D2Q9, f, -5.0, 12, 1e-3, np.zeros((1, ny, nx), np.uint8)))
+    assert len(got[1]) == 1 and got[1][0]["axis"] == axis and got[1][0]["h_min"] == h_min
+
+
 @pytest.mark.parametrize("lat,storage", [("D2Q9", "f64"), ("D3Q19", "f64"), ("D3Q19", "f32")])
 def test_spread_injection_matches_oracle(lbm, lat, storage):
     """Blowing agent spread over each site's bubble (two sites in one bubble,
