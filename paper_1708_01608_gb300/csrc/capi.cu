@@ -1029,6 +1029,7 @@ lbm_status lbm_bubble_sizes(lbm_ctx *c, int64_t *roots, int64_t *sizes, int64_t 
   }
   count_merges(c);
   if ((int64_t)mail[0] != n) return fail(LBM_ECUDA, "bubble census: component count mismatch");
+  if (n > c->census_cap) return fail(LBM_ECUDA, "bubble census: list overflow after regrowth");
   // canonical order: increasing root label
   std::vector<int64_t> order((size_t)n);
   for (int64_t q = 0; q < n; ++q) order[q] = q;
@@ -1109,9 +1110,9 @@ lbm_status lbm_film_pairs(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
   CK(cudaMemcpyAsync(c->d_film_save.p, c->d_film_state.p, (size_t)c->N,
                      cudaMemcpyDeviceToDevice, c->s));
   const auto *mail = static_cast<const unsigned long long *>(nullptr);
-  int64_t nmid = 0;
+  int64_t nmid = 0, capdev = 0;
   for (int pass = 0; pass < 2; ++pass) {
-    const int64_t capdev = c->film_mid_cap;
+    capdev = c->film_mid_cap;
     const size_t rec_bytes = film_record_bytes() * (size_t)capdev;
     CKS(dalloc(c, c->d_film_rec, rec_bytes));
     CK(diag_film_cells(c->v, static_cast<const int32_t *>(c->d_labels.p), lattice_ptr(c, c->cur),
@@ -1133,6 +1134,9 @@ lbm_status lbm_film_pairs(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
     CK(cudaMemcpyAsync(c->d_film_state.p, c->d_film_save.p, (size_t)c->N,
                        cudaMemcpyDeviceToDevice, c->s));
   }
+  // the redo sees the same state, so its midpoints fit; a count that still
+  // exceeds the records read back is an error, never an over-read
+  if (nmid > capdev) return fail(LBM_ECUDA, "film pairs: midpoint records overflow after regrowth");
   census->film = (int64_t)mail[0];
   census->midpoints = (int64_t)mail[1];
   census->armed = (int64_t)mail[2];
@@ -1278,6 +1282,7 @@ lbm_status lbm_diagnostic_interval(lbm_ctx *c, int32_t h_max, double eps_arm, in
   if (n != out->ncomp) return fail(LBM_ECUDA, "interval: component count mismatch");
   // census entries in increasing root order
   const int64_t capdev = c->census_cap;
+  if (n > capdev) return fail(LBM_ECUDA, "interval: census list overflow after regrowth");
   const auto *r = reinterpret_cast<const int64_t *>(census + 65);
   const int64_t *sz = r + capdev;
   std::vector<int64_t> order((size_t)n);

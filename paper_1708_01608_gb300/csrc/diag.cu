@@ -92,31 +92,87 @@ __device__ __forceinline__ float min_image_f(float d, float n) {
   if (d > 0.5f * n) d -= n;
   return d;
 }
-__global__ void k_init_rho(const View v, const double *bub, int32_t nb, double rho_l,
-                           double rho_g, double width, double amp, uint64_t key, double *rho) {
-  const int64_t N = v.NX * v.NY * v.NZ;
+// signed FP32 distance from the point (px, py, pz) to bubble b's surface
+__device__ __forceinline__ float bubble_dist_f(float px, float py, float pz, const double *b,
+                                               float nxf, float nyf, float nzf) {
+  const float dx = min_image_f(px - (float)b[0], nxf);
+  const float dy = min_image_f(py - (float)b[1], nyf);
+  const float dz = min_image_f(pz - (float)b[2], nzf);
+  return sqrtf(dx * dx + dy * dy + dz * dz) - (float)b[3];
+}
+
+// One block per brick of cells (8 x 8 x 8; 16 x 16 in the D2Q9 view).  The
+// block first keeps the bubbles that can matter to any of its cells.  With
+// c the brick's centre, h its half-diagonal and d_c the smallest signed
+// distance from c, every cell x of the brick has a bubble within d_c + h,
+// and a bubble b within that of x has d_c(b) <= d_x(b) + h <= d_c + 2h
+// (the periodic distance is a metric).  The margin covers the FP32 errors
+// and the 1e-3 window of the FP64 re-evaluation, so each cell meets the
+// same bubbles as in a scan of all of them.  A brick with more candidates
+// than the list holds scans all bubbles.
+constexpr int INIT_CAND = 1024;
+__global__ void __launch_bounds__(TPB) k_init_rho(const View v, int bx, int by, int bz,
+                                                  const double *bub, int32_t nb, double rho_l,
+                                                  double rho_g, double width, double amp,
+                                                  uint64_t key, double *rho) {
+  __shared__ int cand[INIT_CAND];
+  __shared__ int ncand;
+  __shared__ float wmin[TPB / 32];
+  const int NX = (int)v.NX, NY = (int)v.NY, NZ = (int)v.NZ;
+  const int nbx = (NX + bx - 1) / bx, nby = (NY + by - 1) / by;
+  const int ix = (int)(blockIdx.x % (unsigned)nbx);
+  const int r1 = (int)(blockIdx.x / (unsigned)nbx);
+  const int iy = r1 % nby, iz = r1 / nby;
+  const int x0 = ix * bx, y0 = iy * by, z0 = iz * bz;
+  const int ex = min(bx, NX - x0), ey = min(by, NY - y0), ez = min(bz, NZ - z0);
   const float nxf = (float)v.NX, nyf = (float)v.NY, nzf = (float)v.NZ;
-  GRID_LOOP(k, N) {
-    const Idx c = idx_of(k, v);
+  bool use_all = true;
+  if (nb > 0) {
+    const float cx = (float)x0 + 0.5f * (float)(ex - 1);
+    const float cy = (float)y0 + 0.5f * (float)(ey - 1);
+    const float cz = (float)z0 + 0.5f * (float)(ez - 1);
+    const float h = 0.5f * sqrtf((float)((ex - 1) * (ex - 1) + (ey - 1) * (ey - 1) +
+                                         (ez - 1) * (ez - 1)));
+    float m = INFINITY;
+    for (int b = threadIdx.x; b < nb; b += TPB)
+      m = fminf(m, bubble_dist_f(cx, cy, cz, bub + 4 * b, nxf, nyf, nzf));
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = m;
+    if (threadIdx.x == 0) ncand = 0;
+    __syncthreads();
+    float dc = wmin[0];
+    for (int w = 1; w < TPB / 32; ++w) dc = fminf(dc, wmin[w]);
+    const float t0 = dc + 2.0f * h;
+    for (int b = threadIdx.x; b < nb; b += TPB) {
+      const float d = bubble_dist_f(cx, cy, cz, bub + 4 * b, nxf, nyf, nzf);
+      if (d - t0 <= 0.05f + 1e-6f * (fabsf(d) + fabsf((float)bub[4 * b + 3]) + fabsf(t0))) {
+        const int q = atomicAdd(&ncand, 1);
+        if (q < INIT_CAND) cand[q] = b;
+      }
+    }
+    __syncthreads();
+    use_all = ncand > INIT_CAND;
+  }
+  const int nc = use_all ? nb : ncand;
+  const int cells = ex * ey * ez;
+  for (int t = threadIdx.x; t < cells; t += TPB) {
+    const int x = x0 + t % ex, y = y0 + (t / ex) % ey, z = z0 + t / (ex * ey);
+    const int64_t k = ((int64_t)z * NY + y) * NX + x;
     double r = rho_l;
     if (nb > 0) {
       float s32 = INFINITY;
-      for (int b = 0; b < nb; ++b) {
-        const float dx = min_image_f((float)c.x - (float)bub[4 * b + 0], nxf);
-        const float dy = min_image_f((float)c.y - (float)bub[4 * b + 1], nyf);
-        const float dz = min_image_f((float)c.z - (float)bub[4 * b + 2], nzf);
-        const float d = sqrtf(dx * dx + dy * dy + dz * dz) - (float)bub[4 * b + 3];
-        s32 = fminf(s32, d);
+      for (int j = 0; j < nc; ++j) {
+        const int b = use_all ? j : cand[j];
+        s32 = fminf(s32, bubble_dist_f((float)x, (float)y, (float)z, bub + 4 * b, nxf, nyf, nzf));
       }
       double s = INFINITY;
-      for (int b = 0; b < nb; ++b) {
-        const float dxf = min_image_f((float)c.x - (float)bub[4 * b + 0], nxf);
-        const float dyf = min_image_f((float)c.y - (float)bub[4 * b + 1], nyf);
-        const float dzf = min_image_f((float)c.z - (float)bub[4 * b + 2], nzf);
-        if (sqrtf(dxf * dxf + dyf * dyf + dzf * dzf) - (float)bub[4 * b + 3] > s32 + 1e-3f) continue;
-        const double dx = min_image((double)c.x - bub[4 * b + 0], (double)v.NX);
-        const double dy = min_image((double)c.y - bub[4 * b + 1], (double)v.NY);
-        const double dz = min_image((double)c.z - bub[4 * b + 2], (double)v.NZ);
+      for (int j = 0; j < nc; ++j) {
+        const int b = use_all ? j : cand[j];
+        if (bubble_dist_f((float)x, (float)y, (float)z, bub + 4 * b, nxf, nyf, nzf) > s32 + 1e-3f)
+          continue;
+        const double dx = min_image((double)x - bub[4 * b + 0], (double)v.NX);
+        const double dy = min_image((double)y - bub[4 * b + 1], (double)v.NY);
+        const double dz = min_image((double)z - bub[4 * b + 2], (double)v.NZ);
         const double d =
             __dadd_rn(sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz))),
                       -bub[4 * b + 3]);
@@ -751,8 +807,11 @@ static int64_t ncells(const View &v) { return v.NX * v.NY * v.NZ; }
 cudaError_t diag_init_rho(const View &v, const double *bub, int32_t nb, double rho_l,
                           double rho_g, double width, double noise_amp, uint64_t seed,
                           double *rho, cudaStream_t s) {
-  k_init_rho<<<nblocks(ncells(v)), TPB, 0, s>>>(v, bub, nb, rho_l, rho_g, width, noise_amp,
-                                                seed ^ 0x6E6F697365000000ull, rho);
+  // bricks of 8 x 8 x 8 cells, 16 x 16 in the D2Q9 view (NY == 1)
+  const int bx = v.NY == 1 ? 16 : 8, by = v.NY == 1 ? 1 : 8, bz = v.NY == 1 ? 16 : 8;
+  const int64_t nbricks = ((v.NX + bx - 1) / bx) * ((v.NY + by - 1) / by) * ((v.NZ + bz - 1) / bz);
+  k_init_rho<<<(unsigned)nbricks, TPB, 0, s>>>(v, bx, by, bz, bub, nb, rho_l, rho_g, width,
+                                               noise_amp, seed ^ 0x6E6F697365000000ull, rho);
   return cudaGetLastError();
 }
 
