@@ -411,6 +411,44 @@ def test_maximum_sizes(lbm, lat, storage, ext, period, r):
     assert rel_err(first, ro) < TOL[storage], rel_err(first, ro)
 
 
+@pytest.mark.parametrize("lat,ext,storage", [("D3Q19", (24, 20, 18), "f32"),
+                                             ("D3Q19", (24, 20, 18), "f64"),
+                                             ("D2Q9", (40, 30, 1), "f16")])
+def test_empty_and_uniform_states(lbm, lat, ext, storage):
+    """No bubbles (uniform liquid) and no liquid (uniform gas).  Zero steps
+    change nothing, an empty site list is accepted, and a uniform state stays
+    uniform bit for bit.  Uniform liquid has no gas component, an empty
+    census and no film.  Uniform gas is one component holding every cell
+    (root 0, wrapping along every axis) with no film.  Labels and census
+    equal the oracle's on the same density."""
+    nx, ny, nz = ext
+    N = nx * ny * nz
+    for rho_u, ncomp in ((2.0, 0), (0.15, 1)):
+        L = lbm.Lattice(lat, nx, ny, nz, tau=0.9, G=-5.0, storage=storage, rho_ref=2.0)
+        L.seed_bubbles(None, rho_u, rho_u, 2.0, 0.0, 0)
+        f0 = L.read("f")
+        L.step(0)
+        assert L.steps == 0 and (L.read("f") == f0).all()
+        L.inject([], [])
+        L.step(10)
+        rho = L.read("rho")
+        assert (rho == rho.flat[0]).all()
+        rep = L.diagnostic_interval(12, 1e-3, want_labels=True)
+        lab_o, n_o = O.label_gas(LAT[lat], rho, 1.0)
+        roots_o, sizes_o = O.bubble_sizes(lab_o)
+        assert rep["ncomp"] == n_o == ncomp
+        assert (rep["labels"] == lab_o).all()
+        assert list(rep["roots"]) == list(roots_o) and list(rep["sizes"]) == list(sizes_o)
+        assert rep["film"] == dict(film=0, midpoints=0, armed=0, fired=0)
+        assert rep["hist"].sum() == ncomp
+        if ncomp:
+            assert list(rep["sizes"]) == [N] and list(rep["roots"]) == [0]
+            assert rep["hist"][int(np.log2(N))] == 1
+        counts, pairs = L.film_pairs(12, 1e-3)
+        assert counts["film"] == 0 and len(pairs) == 0
+        L.close()
+
+
 def test_deterministic_bits(lbm):
     out = []
     for _ in range(2):
