@@ -764,6 +764,9 @@ struct FieldAcc {
   }
   __device__ double rho(int64_t x, int64_t y, int64_t z) const { return rho_f[at(x, y, z)]; }
   __device__ double p(int64_t x, int64_t y, int64_t z) const { return p_f[at(x, y, z)]; }
+  __device__ bool below(int64_t x, int64_t y, int64_t z, double mid) const {
+    return rho(x, y, z) < mid;
+  }
 };
 __global__ void k_film_probe(const View v, const double *rho, const double *p, int64_t x0,
                              int64_t y0, int64_t z0, int ex, int ey, int ez, int px_, int py_,
@@ -894,7 +897,7 @@ cudaError_t diag_line_d2(const View &v, const double *p, int64_t x0, int64_t y0,
 cudaError_t diag_film_probe(const View &v, const double *rho, const double *p, int64_t x0,
                             int64_t y0, int64_t z0, const int e[3], const int ep[3], int64_t len,
                             double mid, double *out, cudaStream_t s) {
-  k_film_probe<<<1, 128, 0, s>>>(v, rho, p, x0, y0, z0, e[0], e[1], e[2], ep[0], ep[1], ep[2],
+  k_film_probe<<<1, 256, 0, s>>>(v, rho, p, x0, y0, z0, e[0], e[1], e[2], ep[0], ep[1], ep[2],
                                  len, mid, out);
   return cudaGetLastError();
 }

@@ -113,6 +113,25 @@ struct PopAcc {
       r += __dadd_rn(__dmul_rn(Lattice<D2Q9>::w(i), D->rho_ref), (double)lat[i * D->popstride + o]);
     return r;
   }
+  // rho < mid as the FP64 sum above decides it.  The FP32 sum of the same
+  // eighteen terms (w_i rho_ref and g_i) is within 20 u sum|terms| of the
+  // exact value (u = 2^-24, Higham's bound for recursive summation with the
+  // rounded products), so a value outside a band of 4e-6 sum|terms| around
+  // mid is decided in FP32 and only the rest is summed again in FP64.
+  __device__ bool below(int64_t x, int64_t y, int64_t z, double mid) const {
+    const int64_t o = off(x, z);
+    float r = 0.0f, s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float t = (float)Lattice<D2Q9>::w(i) * D->rho_ref_f, g = lat[i * D->popstride + o];
+      r += t + g;
+      s += fabsf(t) + fabsf(g);
+    }
+    const double d = (double)r - mid, band = 4e-6 * (double)s;
+    if (d < -band) return true;
+    if (d > band) return false;
+    return rho(x, y, z) < mid;
+  }
   __device__ double p(int64_t x, int64_t y, int64_t z) const {
     const double r = rho(x, y, z);
     const double s = D->rho0 * (1.0 - exp(-r / D->rho0));
@@ -359,7 +378,7 @@ lbm_status enqueue_interval(lbm_ensemble *E) {
     ECK(cudaEventRecord(E->join[c], E->side[c]));
     ECK(cudaStreamWaitEvent(E->s, E->join[c], 0));
   }
-  k_ens_probe<<<E->n, 128, 0, E->s>>>(E->d_dom, E->d_state, E->n, 0, E->d_step, E->eps_arm,
+  k_ens_probe<<<E->n, 256, 0, E->s>>>(E->d_dom, E->d_state, E->n, 0, E->d_step, E->eps_arm,
                                        E->h_max);
   ECK(cudaGetLastError());
   return LBM_OK;
