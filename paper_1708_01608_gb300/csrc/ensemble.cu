@@ -49,7 +49,7 @@ constexpr int CLASS_BX[NCLASS] = {256, 128, 64};
 template <int BX, int NS>
 __global__ void __launch_bounds__(BX)
     ens_step_kernel(const EnsDomain *doms, const FusedMaps *mapsA, const FusedMaps *mapsB,
-                    const int4 *items, const int *count, int parity) {
+                    const int4 *items, const int *count, const EnsState *st, int parity) {
   if ((int)blockIdx.x >= *count) return;
   const int4 it = items[blockIdx.x];
   const EnsDomain &D = doms[it.x];
@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(BX)
   // the domain record are never written by a step, the lattices are read
   // and written only after the previous step has completed
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // a domain whose criterion was settled by a probe earlier in the same
+  // launch of intervals keeps the state it had there (uniform over the CTA)
+  if (!st[it.x].active) return;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   uint32_t kb = 0;
   fused_march<D2Q9, ST_F32, BX, 1, NS>(m, [&](int i) { return out + i * ps; }, kb);
@@ -182,7 +185,8 @@ cudaError_t ens_prepare_t() {
 }
 template <int BX, int NS>
 cudaError_t ens_launch_t(int grid, const EnsDomain *doms, const FusedMaps *a, const FusedMaps *b,
-                  const int4 *items, const int *count, int parity, cudaStream_t s) {
+                  const int4 *items, const int *count, const EnsState *st, int parity,
+                  cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)BX);
@@ -193,7 +197,7 @@ cudaError_t ens_launch_t(int grid, const EnsDomain *doms, const FusedMaps *a, co
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, ens_step_kernel<BX, NS>, doms, a, b, items, count, parity);
+  return cudaLaunchKernelEx(&cfg, ens_step_kernel<BX, NS>, doms, a, b, items, count, st, parity);
 }
 // class -> (BX, NS) of the D2Q9 fused tile table
 cudaError_t ens_prepare(int cls) {
@@ -204,12 +208,12 @@ cudaError_t ens_prepare(int cls) {
   }
 }
 cudaError_t ens_launch(int cls, int grid, const EnsDomain *doms, const FusedMaps *a,
-                       const FusedMaps *b, const int4 *items, const int *count, int parity,
-                       cudaStream_t s) {
+                       const FusedMaps *b, const int4 *items, const int *count,
+                       const EnsState *st, int parity, cudaStream_t s) {
   switch (cls) {
-    case 0: return ens_launch_t<256, 4>(grid, doms, a, b, items, count, parity, s);
-    case 1: return ens_launch_t<128, 4>(grid, doms, a, b, items, count, parity, s);
-    default: return ens_launch_t<64, 6>(grid, doms, a, b, items, count, parity, s);
+    case 0: return ens_launch_t<256, 4>(grid, doms, a, b, items, count, st, parity, s);
+    case 1: return ens_launch_t<128, 4>(grid, doms, a, b, items, count, st, parity, s);
+    default: return ens_launch_t<64, 6>(grid, doms, a, b, items, count, st, parity, s);
   }
 }
 int class_tile_id(int cls) { return cls == 0 ? 1 : (cls == 1 ? 2 : 3); }
@@ -250,10 +254,12 @@ struct lbm_ensemble {
   int64_t steps = 0;
   double updates = 0;  // lattice updates performed
   int64_t launches = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  // pinned host copies of the step counter and the domain states, so that
-  // an interval's two transfers are plain asynchronous copies
+  // captured launches of one interval and of ENS_BATCH intervals
+  cudaGraph_t graph = nullptr, graph_b = nullptr;
+  cudaGraphExec_t exec = nullptr, exec_b = nullptr;
+  // pinned host copies of the step counters (one per interval of a launch)
+  // and the domain states, so that a launch's two transfers are plain
+  // asynchronous copies
   int64_t *h_step = nullptr;
   EnsState *h_state = nullptr;
 };
@@ -307,6 +313,12 @@ void efree_all(lbm_ensemble *E) {
 // items.  Every chunk also stages the two rows around it, so long chunks
 // are cheaper while there are enough of them to fill the GPU.
 constexpr int ENS_ZLEN_MAX = 16, ENS_ZLEN_MIN = 2;
+// With few domains left, a launch covers ENS_BATCH intervals: the host's
+// per-interval round trip (graph launch, state copy, synchronisation) then
+// comes once per ENS_BATCH probes.  A domain settled by one of the probes
+// is skipped by the later steps of the launch, so it keeps the state of its
+// settling probe, as with one interval per launch.
+constexpr int ENS_BATCH = 10, ENS_BATCH_ACTIVE = 32;
 
 int chunk_len(int ny, int zmax) {
   int zlen = std::min(ny, zmax);
@@ -361,12 +373,15 @@ int choose_zlen(const lbm_ensemble *E) {
 void drop_graph(lbm_ensemble *E) {
   if (E->exec) cudaGraphExecDestroy(E->exec);
   if (E->graph) cudaGraphDestroy(E->graph);
-  E->exec = nullptr;
-  E->graph = nullptr;
+  if (E->exec_b) cudaGraphExecDestroy(E->exec_b);
+  if (E->graph_b) cudaGraphDestroy(E->graph_b);
+  E->exec = E->exec_b = nullptr;
+  E->graph = E->graph_b = nullptr;
 }
 
-// one diagnostic interval: diag_every steps of every class, then the probe
-lbm_status enqueue_interval(lbm_ensemble *E) {
+// one diagnostic interval (the k-th of a launch): diag_every steps of every
+// class, then the probe, which stamps settled domains with step counter k
+lbm_status enqueue_interval(lbm_ensemble *E, int k) {
   // fork: one chain of diag_every steps per tile class, joined before the probe
   ECK(cudaEventRecord(E->fork, E->s));
   for (int c = 0; c < NCLASS; ++c) {
@@ -374,20 +389,23 @@ lbm_status enqueue_interval(lbm_ensemble *E) {
     ECK(cudaStreamWaitEvent(E->side[c], E->fork, 0));
     for (int t = 0; t < E->diag_every; ++t)
       ECK(ens_launch(c, E->max_items[c], E->d_dom, E->d_mapsA, E->d_mapsB, E->d_items[c],
-                     E->d_count[c], t & 1, E->side[c]));
+                     E->d_count[c], E->d_state, t & 1, E->side[c]));
     ECK(cudaEventRecord(E->join[c], E->side[c]));
     ECK(cudaStreamWaitEvent(E->s, E->join[c], 0));
   }
-  k_ens_probe<<<E->n, 256, 0, E->s>>>(E->d_dom, E->d_state, E->n, 0, E->d_step, E->eps_arm,
+  k_ens_probe<<<E->n, 256, 0, E->s>>>(E->d_dom, E->d_state, E->n, 0, E->d_step + k, E->eps_arm,
                                        E->h_max);
   ECK(cudaGetLastError());
   return LBM_OK;
 }
 
-lbm_status ensure_graph(lbm_ensemble *E) {
-  if (E->exec) return LBM_OK;
+lbm_status ensure_graph(lbm_ensemble *E, int K) {
+  cudaGraph_t &graph = K == 1 ? E->graph : E->graph_b;
+  cudaGraphExec_t &exec = K == 1 ? E->exec : E->exec_b;
+  if (exec) return LBM_OK;
   ECK(cudaStreamBeginCapture(E->s, cudaStreamCaptureModeThreadLocal));
-  lbm_status st = enqueue_interval(E);
+  lbm_status st = LBM_OK;
+  for (int k = 0; k < K && st == LBM_OK; ++k) st = enqueue_interval(E, k);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(E->s, &g);
   if (st != LBM_OK) {
@@ -395,29 +413,36 @@ lbm_status ensure_graph(lbm_ensemble *E) {
     return st;
   }
   ECK(e);
-  E->graph = g;
-  ECK(cudaGraphInstantiate(&E->exec, g, 0));
+  graph = g;
+  ECK(cudaGraphInstantiate(&exec, g, 0));
   return LBM_OK;
 }
 
-lbm_status ens_interval(lbm_ensemble *E) {
-  double cells = 0;
-  for (int d = 0; d < E->n; ++d)
-    if (E->hstate[d].active) cells += (double)E->hdom[d].NX * E->hdom[d].NZ;
-  const int64_t now = E->steps + E->diag_every;
-  *E->h_step = now;
-  ECK(cudaMemcpyAsync(E->d_step, E->h_step, sizeof(now), cudaMemcpyHostToDevice, E->s));
-  ECKS(ensure_graph(E));
-  ECK(cudaGraphLaunch(E->exec, E->s));
+// K intervals in one launch (K = 1 or ENS_BATCH), then the domain states
+// on the host.  A domain that a probe of this launch settled was stepped up
+// to that probe's step counter, which its state records.
+lbm_status ens_interval(lbm_ensemble *E, int K) {
+  std::vector<char> was(E->n);
+  for (int d = 0; d < E->n; ++d) was[d] = E->hstate[d].active != 0;
+  for (int k = 0; k < K; ++k) E->h_step[k] = E->steps + (int64_t)(k + 1) * E->diag_every;
+  ECK(cudaMemcpyAsync(E->d_step, E->h_step, sizeof(int64_t) * K, cudaMemcpyHostToDevice, E->s));
+  ECKS(ensure_graph(E, K));
+  ECK(cudaGraphLaunch(K == 1 ? E->exec : E->exec_b, E->s));
   ECK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(EnsState) * E->n, cudaMemcpyDeviceToHost,
                       E->s));
   ECK(cudaStreamSynchronize(E->s));
   std::copy(E->h_state, E->h_state + E->n, E->hstate.begin());
-  E->steps = now;
-  E->updates += cells * E->diag_every;
+  const int64_t end = E->steps + (int64_t)K * E->diag_every;
+  for (int d = 0; d < E->n; ++d) {
+    if (!was[d]) continue;
+    const EnsState &st = E->hstate[d];
+    const int64_t ran = (st.active ? end : st.step) - E->steps;
+    E->updates += (double)E->hdom[d].NX * E->hdom[d].NZ * (double)ran;
+  }
+  E->steps = end;
   int ncls = 0;
   for (int c = 0; c < NCLASS; ++c) ncls += E->max_items[c] > 0;
-  E->launches += (int64_t)E->diag_every * ncls + 1;
+  E->launches += (int64_t)K * ((int64_t)E->diag_every * ncls + 1);
   return LBM_OK;
 }
 
@@ -467,7 +492,8 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
     lbm_ensemble_destroy(E);
     return efail(LBM_ECUDA, "ensemble: stream creation failed");
   }
-  if (cudaMallocHost(reinterpret_cast<void **>(&E->h_step), sizeof(int64_t)) != cudaSuccess ||
+  if (cudaMallocHost(reinterpret_cast<void **>(&E->h_step), sizeof(int64_t) * ENS_BATCH) !=
+          cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void **>(&E->h_state), sizeof(EnsState) * (size_t)n) !=
           cudaSuccess) {
     cudaGetLastError();
@@ -537,7 +563,7 @@ lbm_status lbm_ensemble_create(const lbm_domain *dom, int32_t n, double eps_arm,
   E->d_mapsB = static_cast<FusedMaps *>(p);
   if ((st = ealloc(E, sizeof(EnsState) * n, &p)) != LBM_OK) return bail(st);
   E->d_state = static_cast<EnsState *>(p);
-  if ((st = ealloc(E, sizeof(int64_t), &p)) != LBM_OK) return bail(st);
+  if ((st = ealloc(E, sizeof(int64_t) * ENS_BATCH, &p)) != LBM_OK) return bail(st);
   E->d_step = static_cast<int64_t *>(p);
   // work-list capacity per class: every domain could be moved to any class
   for (int c = 0; c < NCLASS; ++c) {
@@ -662,7 +688,10 @@ lbm_status lbm_ensemble_run(lbm_ensemble *E, int64_t max_steps, int64_t *steps_d
     if (!active) break;
     std::vector<int32_t> before(E->n);
     for (int d = 0; d < E->n; ++d) before[d] = E->hstate[d].active;
-    ECKS(ens_interval(E));
+    const int64_t left = max_steps - (E->steps - start);
+    const int K = active <= ENS_BATCH_ACTIVE && left >= (int64_t)ENS_BATCH * E->diag_every
+                      ? ENS_BATCH : 1;
+    ECKS(ens_interval(E, K));
     bool changed = false;
     for (int d = 0; d < E->n; ++d) changed |= before[d] != E->hstate[d].active;
     if (changed) ECKS(refresh_work(E));
