@@ -8,9 +8,11 @@
 // column march as the single-lattice fused kernel, with the domain's TMA
 // descriptors read from global memory.  After diag_every steps a probe
 // kernel measures each active domain's film (FP64) and advances its rupture
-// state machine.  The diag_every steps plus the probe are captured once into
-// a CUDA graph and replayed; domains whose criterion fired (or whose film is
-// gone) drop out of the work lists between replays.
+// state machine.  The diag_every steps plus the probe (ten such intervals
+// when few domains remain) are captured once into a CUDA graph and
+// replayed; domains whose criterion fired (or whose film is gone) drop out
+// of the work lists between replays, and within a replay their steps return
+// at once.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
