@@ -1,13 +1,17 @@
 #!/usr/bin/env python3
 """Benchmark of the Shan-Chen bubble-merging LBM hot path on GB300.
 
-One bench step = one diagnostic interval of the 128^3 D3Q19 FP32 foam
-workload (64 nucleation sites, r = 3, blowing agent 1e-4 per step, budget 50):
-100 fused collide-stream-force steps with injection, then the diagnostics of
-the interval: FP64 totals and gas labelling in one pass, the per-site merge
-bookkeeping, the FP64 EOS pressure and the film test at every lattice point,
-and the bubble census with its size histogram, all through the C ABI.
-Throughput is MLUPS = cells * 100 / seconds / 1e6 over the whole step.
+One bench step = one diagnostic interval of the 512^3 D3Q19 FP32 foam
+workload (1000 seeded gas bubbles, radii uniform 4..12, tau 0.8, G -5): 100
+fused collide-stream-force steps, then the diagnostics of the interval: FP64
+totals and gas labelling in one pass, the per-site merge bookkeeping, the
+FP64 EOS pressure and the film test at every lattice point, and the bubble
+census with its size histogram, all through the C ABI.  Throughput is
+MLUPS = cells * 100 / seconds / 1e6 over the whole step.  The default 20
+timed bench steps cover the workload's 2000 LBM steps.  --workload foam128
+(64 injecting nuclei on 128^3), foam768 (the FP16 full foam) and ensemble256
+(the batched two-bubble sweep) select the other workloads; --storage
+f16/bf16/f64 the storage form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,11 +37,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1708_01608_gb300.workloads import FOAM_128 as W  # noqa: E402
+from paper_1708_01608_gb300.workloads import FOAM_512 as W  # noqa: E402
 
-METRIC = "D3Q19 Shan-Chen MLUPS (FP32, 128^3 foam, 64 sites, injection + diagnostics every 100 steps)"
+METRIC = ("D3Q19 Shan-Chen MLUPS (512^3 foam, FP32 storage, 1000 bubbles, "
+          "diagnostics every 100 steps)")
 UNIT = "MLUPS"
-INNER = W["diag_every"]                       # LBM steps per bench step
+INNER = 100                                   # LBM steps per bench step
 CELLS = W["nx"] * W["ny"] * W["nz"]
 Q = 19
 B_ALG = 2 * Q * 4                             # bytes per lattice update, FP32 storage
@@ -58,10 +63,12 @@ NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.8e6,
                           ("d3q19_foam_768", "f16", 14): 27 * 1270.09e6}
 # FP64 storage: the step kernel is bound by the FP64 pipe, not by HBM.  FP64
 # operations per lattice update of its D3Q19 kernel, DADD + DMUL + 2 DFMA as
-# ncu counts them on the 128^3 case (146 + 71 + 2 x 332), and the FP64 peak
-# from the unit counts: 2 DFMA per SM and cycle x 152 SMs x 2 FLOP x 2.07 GHz.
+# ncu counts them on the 128^3 case (146 + 71 + 2 x 332).  The peak is
+# measured in the run by lbm_fp64_rate (a DFMA-chain kernel timed with CUDA
+# events); the unit counts give 2 DFMA per SM and cycle x 152 SMs x 2 FLOP x
+# 2.07 GHz = 1.26 TFLOP/s, used only if that measurement fails.
 FP64_FLOP_PER_UPDATE = 881
-FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+FP64_PEAK_DERIVED_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 STORAGE_NAME = {"f32": "FP32", "f64": "FP64", "f16": "FP16-offset", "bf16": "BF16-offset"}
 # D3Q19 tile ids of the x-pair kernel (fused_step_kernel_x2)
 X_PAIR_TILES = range(14, 26)
@@ -225,13 +232,13 @@ def site_budgets(n):
     return np.full(n, float(b))
 
 
-def make_lattice(lbm, kernel="auto"):
+def make_lattice(lbm, kernel="auto", tile=0):
     s = W["sites"]
     bub = lbm.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
                            s["min_spacing"], s["min_gap"], W["seed"])
     L = lbm.Lattice("D3Q19", W["nx"], W["ny"], W["nz"], tau=W["tau"], G=W["G"],
                     rho0=W["rho0"], storage=W["storage"], gas_threshold=W["threshold"],
-                    rho_ref=W["rho_ref"], kernel=kernel)
+                    rho_ref=W["rho_ref"], kernel="fused" if tile else kernel, tile=tile)
     L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
     rate = np.full(len(bub), W["rate"])
     budget = site_budgets(len(bub))
@@ -240,10 +247,11 @@ def make_lattice(lbm, kernel="auto"):
 
 
 def diagnostics(L):
-    """The diagnostic interval through the C ABI (labels computed once)."""
+    """The diagnostic interval through the C ABI (labels computed once);
+    returns the number of gas components."""
     # FP64 totals + gas labels in one pass, site labels and merge events, the
     # film test at every lattice point, the bubble census: one call, one sync
-    L.diagnostic_interval(FILM_H_MAX, FILM_EPS_ARM, FILM_CAP, CENSUS_BINS)
+    return L.diagnostic_interval(FILM_H_MAX, FILM_EPS_ARM, FILM_CAP, CENSUS_BINS)["ncomp"]
 
 
 # kernels of one diagnostic interval (FP32 storage): scan + final (totals and
@@ -252,28 +260,51 @@ def diagnostics(L):
 DIAG_LAUNCHES = 8
 
 
+# The oracle's FP64 populations of a 512^3 or 768^3 lattice (20 GB, 68 GB)
+# do not fit a bounded CPU sample, so the CPU legs step a 128^3 periodic
+# lattice seeded by the same recipe, its bubble count scaled to the volume.
+CPU_SAMPLE_SIDE = 128
+
+
+def cpu_sample():
+    """(side, bubbles, site cells, rates, budgets, description) of the
+    lattice the oracle steps for the CPU legs: the workload itself up to
+    128^3, else a 128^3 lattice with the same recipe (parameters, radius
+    law, spacing rule, seed) and the bubble count scaled by volume."""
+    import oracle as O
+    s = W["sites"]
+    side = min(W["nx"], CPU_SAMPLE_SIDE)
+    n = s["n"] if side == W["nx"] else max(1, round(s["n"] * (side / W["nx"]) ** 3))
+    got, bub = O.sample_sites(side, side, side, n, s["r_min"], s["r_max"], s["min_spacing"],
+                              s["min_gap"], W["seed"])
+    cells = (np.floor(bub[:, 0] + 0.5) + side * (np.floor(bub[:, 1] + 0.5)
+             + side * np.floor(bub[:, 2] + 0.5))).astype(np.int64)
+    rate = np.full(len(bub), W["rate"])
+    budget = site_budgets(len(bub))
+    what = ("the full %d^3 lattice" % side if side == W["nx"] else
+            "a %d^3 periodic lattice of the %d^3 recipe (%d bubbles, the %d scaled by volume)"
+            % (side, W["nx"], n, s["n"]))
+    if W["rate"] > 0:
+        what += " with injection"
+    return side, bub, cells, rate, budget, what
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle on the host cores, bounded sample of the workload."""
     import oracle as O
-    s = W["sites"]
-    got, bub = O.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
-                              s["min_spacing"], s["min_gap"], W["seed"])
-    f, _ = O.init(O.D3Q19, W["nx"], W["ny"], W["nz"], bub, W["rho_l"], W["rho_g"], W["width"],
+    side, bub, cells, rate, budget, what = cpu_sample()
+    f, _ = O.init(O.D3Q19, side, side, side, bub, W["rho_l"], W["rho_g"], W["width"],
                   W["noise"], W["seed"])
-    cells = (np.floor(bub[:, 0] + 0.5) + W["nx"] * (np.floor(bub[:, 1] + 0.5)
-             + W["ny"] * np.floor(bub[:, 2] + 0.5))).astype(np.int64)
-    rate = np.full(len(bub), W["rate"])
-    budget = site_budgets(len(bub))
     O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)  # warm
     n, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds_target:
         f = O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": CELLS * n / dt / 1e6, "unit": UNIT, "cores": os.cpu_count(),
+    return {"value": side ** 3 * n / dt / 1e6, "unit": UNIT, "cores": os.cpu_count(),
             "kind": "oracle",
-            "sample": f"{n} oracle time steps of the full 128^3 lattice with injection "
-                      f"({dt:.1f} s, OpenMP over all host cores)"}
+            "sample": f"{n} oracle time steps of {what} ({dt:.1f} s, OpenMP over all host "
+                      f"cores)"}
 
 
 def base_config():
@@ -292,32 +323,26 @@ def run_reference(args, world, rank):
         return
     steps, warm = args.steps, args.warmup
     import oracle as O
-    s = W["sites"]
-    got, bub = O.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
-                              s["min_spacing"], s["min_gap"], W["seed"])
-    f, _ = O.init(O.D3Q19, W["nx"], W["ny"], W["nz"], bub, W["rho_l"], W["rho_g"], W["width"],
+    side, bub, cells, rate, budget, what = cpu_sample()
+    f, _ = O.init(O.D3Q19, side, side, side, bub, W["rho_l"], W["rho_g"], W["width"],
                   W["noise"], W["seed"])
-    cells = (np.floor(bub[:, 0] + 0.5) + W["nx"] * (np.floor(bub[:, 1] + 0.5)
-             + W["ny"] * np.floor(bub[:, 2] + 0.5))).astype(np.int64)
-    rate = np.full(len(bub), W["rate"])
-    budget = site_budgets(len(bub))
     for _ in range(warm):
         f = O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)
     t0 = time.perf_counter()
     for _ in range(steps):
         f = O.run(O.D3Q19, f, 1, W["tau"], W["G"], sites=cells, rate=rate, budget=budget)
     dt = time.perf_counter() - t0
-    val = CELLS * steps / dt / 1e6
+    val = side ** 3 * steps / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": dict(base_config(),
-                           sample="the FP64 oracle, one LBM time step of the full lattice "
-                                  "with injection per bench step"),
+                           sample=f"the FP64 oracle, one LBM time step of {what} per bench "
+                                  f"step"),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": f"{steps} oracle time steps of the full 128^3 lattice"},
+                             "sample": f"{steps} oracle time steps of {what}"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -332,11 +357,13 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    L, rate, budget = make_lattice(lbm, args.kernel)
+    L, rate, budget = make_lattice(lbm, args.kernel, args.tile)
     tuned = None
-    if args.kernel != "two_pass":
+    if args.kernel != "two_pass" and not args.tile:
         tuned = L.autotune(10)  # set-up, outside the timed region; state is restored
     plan = L.plan()
+
+    gas = []  # gas components found by each timed interval
 
     def bench_step(e_begin=None, e_end=None):
         if e_begin is not None:
@@ -344,7 +371,7 @@ def run_ours(args, world, rank, local):
         L.step(INNER)
         if e_end is not None:
             e_end.record(stream)
-        diagnostics(L)
+        return diagnostics(L)
 
     for _ in range(args.warmup):
         bench_step()
@@ -360,7 +387,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     t_start.record(stream)
     for k in range(args.steps):
-        bench_step(*ev_step[k])
+        gas.append(bench_step(*ev_step[k]))
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -409,9 +436,16 @@ def run_ours(args, world, rank, local):
     kname = "fused_step_kernel_x2" if plan[1] in X_PAIR_TILES else "fused_step_kernel"
     if W["storage"] == "f64":
         tflops = FP64_FLOP_PER_UPDATE * CELLS / (step_kernel_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                    "peak_source": "derived from unit counts and the 2.07 GHz clock",
+        try:
+            fp64_peak = lbm.fp64_rate()
+            fp64_src = ("measured in this run: DFMA-chain kernel over every SM "
+                        "(lbm_fp64_rate, CUDA events, fastest of 3)")
+        except lbm.LBMError:
+            fp64_peak = FP64_PEAK_DERIVED_TFLOPS
+            fp64_src = "derived from unit counts and the 2.07 GHz clock"
+        roofline = {"bound": "alu", "achieved": tflops, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": tflops / fp64_peak,
+                    "peak_source": fp64_src,
                     "traffic": traffic, "kernel": kname, "flop_per_update": FP64_FLOP_PER_UPDATE,
                     "bytes_per_update": B_ALG, "kernel_ms": step_kernel_ms}
     else:
@@ -432,7 +466,11 @@ def run_ours(args, world, rank, local):
             "config": dict(base_config(), kernel=args.kernel,
                            plan={"kernel": plan[0], "tile": plan[1], "tile_xy": [plan[2], plan[3]],
                                  "z_chunks": plan[4], "ctas": plan[5]},
-                           parallelism=f"replicas x{world}"),
+                           parallelism=f"replicas x{world}",
+                           rho_l=W["rho_l"],
+                           gas_components={"per_timed_interval": gas,
+                                           "min": min(gas) if gas else None},
+                           lbm_steps_before_timing=INNER * args.warmup),
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
@@ -565,7 +603,7 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "two_pass"])
@@ -574,49 +612,52 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="no timing: build the workload lattice, run this many steps, exit "
                          "(a short fixed case for ncu captures)")
-    ap.add_argument("--tile", type=int, default=0, help="fused tile id for --profile-steps")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="fused tile id: for --profile-steps, or for a timed run without the "
+                         "autotuner (a launch-list capture under ncu, whose serialised "
+                         "launches would mislead the autotuner's timing)")
     ap.add_argument("--extent", type=int, default=0,
-                    help="--profile-steps: cubic lattice side (default: the foam's 128)")
+                    help="--profile-steps: cubic lattice side (default: the workload's)")
     ap.add_argument("--profile-diagnostics", action="store_true",
                     help="--profile-steps: then run one diagnostic interval")
-    ap.add_argument("--workload", default="foam128",
+    ap.add_argument("--workload", default=None,
                     choices=["foam128", "foam512", "foam768", "ensemble256"],
-                    help="foam128: the default benchmark line; foam512: the 512^3 foam "
-                         "(FP32 or --storage f16/bf16); foam768: the 768^3 FP16-offset full "
-                         "foam with 4096 injection sites; ensemble256: the batched two-bubble "
-                         "sweep run to completion")
+                    help="foam512: the default benchmark line, the 512^3 foam (FP32, or "
+                         "--storage f16/bf16/f64); foam128: 64 injecting nuclei on 128^3 (the "
+                         "default of --profile-steps, whose --extent keeps its 64 sites); "
+                         "foam768: the 768^3 FP16-offset full foam with 4096 injection sites; "
+                         "ensemble256: the batched two-bubble sweep run to completion")
     ap.add_argument("--storage", default=None, choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--single", action="store_true",
                     help="ensemble256: also run every domain alone, one after the other")
     args = ap.parse_args()
+    global W, METRIC, CELLS, B_ALG
+    from paper_1708_01608_gb300 import workloads as WL
+    if args.workload is None:
+        args.workload = "foam128" if args.profile_steps > 0 else "foam512"
+    if args.workload == "foam128":
+        W = dict(WL.FOAM_128)
+        METRIC = ("D3Q19 Shan-Chen MLUPS (128^3 foam, FP32 storage, 64 sites, injection + "
+                  "diagnostics every 100 steps)")
+    elif args.workload == "foam768":
+        W = dict(WL.FOAM_768)
+        METRIC = ("D3Q19 Shan-Chen MLUPS (768^3 full foam, FP16-offset storage, 4096 sites "
+                  "with injection, diagnostics every 100 steps)")
+    CELLS = W["nx"] * W["ny"] * W["nz"]
     if args.profile_steps > 0:
         run_profile_case(args)
         return
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup(args.gpus)
-    if args.workload != "foam128":
-        global W, METRIC, INNER, CELLS, B_ALG
-        from paper_1708_01608_gb300 import workloads as WL
-        if args.workload == "ensemble256":
-            try:
-                run_ensemble(args, world, rank, local)
-            finally:
-                if world > 1:
-                    import torch.distributed as dist
-                    dist.destroy_process_group()
-            return
-        if args.workload == "foam512":
-            W = dict(WL.FOAM_512)
-            METRIC = ("D3Q19 Shan-Chen MLUPS (512^3 foam, FP32 storage, 1000 bubbles, "
-                      "diagnostics every 100 steps)")
-        else:
-            W = dict(WL.FOAM_768)
-            METRIC = ("D3Q19 Shan-Chen MLUPS (768^3 full foam, FP16-offset storage, 4096 sites "
-                      "with injection, diagnostics every 100 steps)")
-        INNER = 100
-        CELLS = W["nx"] * W["ny"] * W["nz"]
-        args.no_cpu_baseline = True
+    if args.workload == "ensemble256":
+        try:
+            run_ensemble(args, world, rank, local)
+        finally:
+            if world > 1:
+                import torch.distributed as dist
+                dist.destroy_process_group()
+        return
     if args.storage:
         # the metric names the storage form measured
         METRIC = METRIC.replace(STORAGE_NAME[W["storage"]], STORAGE_NAME[args.storage])

@@ -109,6 +109,9 @@ typedef struct {
                            second staged plane, so that its bounded wait
                            (1 s) expires and lbm_sync reports LBM_ETIMEOUT;
                            exercises the timeout path without a fault */
+  double nucleus_radius; /* radius of the nuclei lbm_seed_bubbles samples
+                            when given no bubble list (Sec. 3: random
+                            nucleation sites); default 3 cells */
 } lbm_config;
 
 #define LBM_DEBUG_WITHHOLD_TMA 1
@@ -118,13 +121,21 @@ typedef struct {
 } lbm_bubble;
 
 /* Fill *cfg with defaults: D3Q19, F32, 64^3, tau 1, G -5, rho0 1,
- * rho_ref 1, threshold 1, automatic kernel, default stream, cudaMalloc. */
+ * rho_ref 1, threshold 1, automatic kernel, default stream, cudaMalloc,
+ * nucleus radius 3. */
 void lbm_config_default(lbm_config *cfg);
 
 /* Create a context on the current CUDA device and allocate its two
- * population lattices.  Errors: EINVAL (extents < 1, nz != 1 for D2Q9,
- * tau <= 0.5, rho0 <= 0, unknown enum), ENOMEM, ECUDA.  *out is NULL on
- * failure. */
+ * population lattices: the lattice on which the Shan-Chen model of Sec. 3.1
+ * runs its "streams and collisions" (the paper runs it in OpenLB; the
+ * lattice type, extents, tau, G and the psi scale rho0 of psi = rho0 (1 -
+ * exp(-rho/rho0)) are this call's configuration).  Populations are stored
+ * as f[i][z][y][x] with the x extent padded to a multiple of 8 elements;
+ * lbm_read and lbm_write_f convert to the unpadded layout above.  Errors:
+ * EINVAL (extents < 1, nz != 1 for D2Q9, an extent above 2^20 or more than
+ * 2^31 - 1 padded cells, tau not finite and > 0.5, rho0 <= 0, G not
+ * finite, unknown enum, alloc without free), ENOMEM, ECUDA.  *out is NULL
+ * on failure. */
 lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
 
 /* Release all device memory of the context (after synchronising its
@@ -145,18 +156,30 @@ lbm_status lbm_sample_sites(int64_t nx, int64_t ny, int64_t nz, int32_t n,
                             double min_gap, uint64_t seed, int64_t max_tries,
                             lbm_bubble *out, int32_t *got);
 
-/* Initial state (Sec. 3.1: nucleation sites in liquid): with s = min over
- * bubbles of (minimum-image distance - r),
+/* Initial state (Sec. 3.1: a time-random model places the nucleation
+ * sites; every other lattice point is filled with liquid).  b is a host
+ * array of n bubbles, or NULL: then n nuclei of radius cfg.nucleus_radius
+ * are drawn from `seed` exactly as lbm_sample_sites(nx, ny, nz, n, r, r,
+ * min_spacing, 0, seed) draws them (min_spacing is used only in that case;
+ * lbm_read_sites returns the drawn list).  With s = min over bubbles of
+ * (minimum-image distance - r),
  *   rho = rho_g + (rho_l - rho_g)/2 (1 + tanh(2 s / width))
  * (rho = rho_l when n = 0), plus noise_amp*(2u - 1) with u the SplitMix64
  * output at the cell's linear index keyed by seed ^ 0x6E6F697365000000, then
  * f_i = w_i rho (equilibrium at rest).  The bubble centres, rounded to the
  * nearest cell, become the injection sites (in order).  Resets the step
- * counter, disables injection and clears the label history.  b is a host
- * array of n bubbles (may be NULL when n = 0).  Errors: EINVAL. */
+ * counter, disables injection and clears the label history.  Errors:
+ * EINVAL (n < 0, non-finite values, width <= 0, min_spacing < 0 when
+ * sampling), ESTATE (fewer than n nuclei fit the spacing rule; nothing is
+ * seeded). */
 lbm_status lbm_seed_bubbles(lbm_ctx *ctx, const lbm_bubble *b, int32_t n,
                             double rho_l, double rho_g, double width,
-                            double noise_amp, uint64_t seed);
+                            double noise_amp, double min_spacing, uint64_t seed);
+
+/* The bubbles of the last lbm_seed_bubbles call (given or drawn), in site
+ * order; n must equal their number.  Host only.  Errors: EINVAL, ESTATE
+ * (not seeded). */
+lbm_status lbm_read_sites(const lbm_ctx *ctx, lbm_bubble *out, int32_t n);
 
 /* Virtual blowing agent (Sec. 3: gas added to each bubble every step until
  * the agent is finished).  rate[s] and budget[s] (host, n = number of seeded
@@ -266,11 +289,14 @@ lbm_status lbm_run_until_rupture(lbm_ctx *ctx, const int64_t *line, double rho_m
                                   double eps_arm, double h_max, int64_t diag_every,
                                   int64_t max_steps, lbm_rupture *out);
 
-/* Gas connected-component labelling: gas cells are rho < gas_threshold
- * (FP64 density), face-connected (4 in 2-D, 6 in 3-D) with periodic wrap;
- * each gas cell gets the smallest linear index of its component, liquid
- * cells -1.  labels: host array of N int32 or NULL; *ncomp receives the
- * number of components (may be NULL).  Synchronous. */
+/* Gas connected-component labelling, the bubble identification behind the
+ * paper's count of merging defects (Sec. 4) and the merge events of its
+ * foam runs (Sec. 3: bubbles merge by film rupture): gas cells are
+ * rho < gas_threshold (FP64 density), face-connected (4 in 2-D, 6 in 3-D)
+ * with periodic wrap; each gas cell gets the smallest linear index of its
+ * component, liquid cells -1.  labels: host array of N int32 or NULL;
+ * *ncomp receives the number of components (may be NULL).  Synchronous.
+ * Errors: EINVAL, ESTATE (not seeded), ENUMERIC, ECUDA. */
 lbm_status lbm_label_gas(lbm_ctx *ctx, int32_t *labels, int64_t *ncomp);
 
 /* The record of one diagnostic interval in a single pass over the
@@ -391,8 +417,12 @@ lbm_status lbm_diagnostic_interval(lbm_ctx *ctx, int32_t h_max, double eps_arm, 
  * Synchronous. */
 lbm_status lbm_totals(lbm_ctx *ctx, double out[4]);
 
-/* Copy a field (doubles, see lbm_field) to host; bytes must be exactly the
- * field's size.  Synchronous. */
+/* Copy a field (doubles, see lbm_field) to host: the density, pressure and
+ * velocity fields are the quantities whose profiles Fig. 2 plots across the
+ * film (Sec. 4), with p the EOS of Sec. 3.1 and psi its pseudopotential;
+ * LBM_F returns the populations themselves.  bytes must be exactly the
+ * field's size.  Synchronous.  Errors: EINVAL (NULL, unknown field, wrong
+ * size), ESTATE (not seeded), ENUMERIC (non-finite density), ECUDA. */
 lbm_status lbm_read(lbm_ctx *ctx, int32_t field, double *host_dst, size_t bytes);
 
 /* Overwrite the populations with host data f[i*N + cell] (doubles, rounded
@@ -446,25 +476,41 @@ lbm_status lbm_ensemble_stats(const lbm_ensemble *ens, double out[4]);
 lbm_status lbm_ensemble_read_f(lbm_ensemble *ens, int32_t domain, double *host, size_t bytes);
 
 /* Allocation-free time step.  The paper has no counterpart: this entry point
- * serves callers that cannot allocate device memory - code that runs while
- * a CUDA graph is being captured, hosts that forbid cudaMalloc inside their
- * time loop, programs with a fixed device-memory budget.  It advances FP32
- * populations f_in -> f_out by one step of the two-pass kernels (no
- * injection).  Layout: Q fields of nx*ny*nz floats, f[i*N + cell], cell =
- * x + nx*(y + ny*z), the post-streaming form lbm_read(LBM_F) returns, plain
- * values (no offset).  The psi field passed between the two kernels lives
- * in a file-scope device array of 2,097,152 floats (8 MB) that every GPU
- * loading the library holds until the process exits; larger lattices are
- * rejected with LBM_EINVAL.  The first call on a device looks up that
- * array's device address and caches it; make that first call before any
- * stream capture.  Every call uses the same array: calls that overlap on
- * the GPU (other streams or threads without ordering) race on it.  f_in and
- * f_out are distinct device buffers owned by the caller; stream may be
- * NULL.  Asynchronous; no memory is allocated or freed.  Errors: EINVAL,
- * ECUDA. */
+ * serves callers that cannot allocate device memory - a host framework that
+ * owns the whole device-memory pool and forbids allocations behind its
+ * back, a time loop that must not stall on the allocator (cudaMalloc and
+ * cudaFree can synchronise the device), a program held to a fixed
+ * device-memory budget.  It advances FP32 populations f_in -> f_out by one
+ * step of the two-pass kernels (no injection).  Layout: Q fields of
+ * nx*ny*nz floats, f[i*N + cell], cell = x + nx*(y + ny*z), the
+ * post-streaming form lbm_read(LBM_F) returns, plain values (no offset).
+ * The psi field passed between the two kernels lives in a file-scope device
+ * array of 2,097,152 floats (8 MB) that every GPU loading the library holds
+ * until the process exits; lattices of more cells are rejected with
+ * LBM_EINVAL (the product is bounded without overflow).  The first call in
+ * each CUDA context (the current one: the device's primary context, or a
+ * driver context the caller made current) looks up that array's device
+ * address and caches it under the context's process-unique id; make that
+ * first call before any stream capture.  Every call uses the same array,
+ * which keeps the last call's psi: calls that overlap on the GPU (other
+ * streams or threads without ordering) race on it.  f_in and f_out are
+ * distinct device buffers owned by the caller; stream may be NULL.
+ * Asynchronous; no memory is allocated or freed.  Errors: EINVAL (unknown
+ * lattice, extents < 1 or nz != 1 for D2Q9, more than 2,097,152 cells, tau
+ * not finite and > 0.5, rho0 not finite and > 0, G not finite, NULL or
+ * aliased buffers), ECUDA. */
 lbm_status lbm_step_static_f32(int32_t lattice, int64_t nx, int64_t ny, int64_t nz, double tau,
                                double G, double rho0, const float *f_in, float *f_out,
                                void *stream);
+
+/* FP64 fused multiply-add rate of the current device, measured: a kernel
+ * of independent chains of dependent FMAs (8 per thread, `iters` rounds)
+ * over every SM, the fastest of three timed launches (CUDA events, after one
+ * warm-up launch).  *tflops = 2 * FMAs / seconds / 1e12.  The paper has no
+ * counterpart: this is the denominator of the FP64 storage form's roofline,
+ * whose step kernel is bound by the FP64 pipe.  Synchronous (legacy default
+ * stream).  Errors: EINVAL, ECUDA. */
+lbm_status lbm_fp64_rate(int32_t iters, double *tflops);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *lbm_last_error(void);

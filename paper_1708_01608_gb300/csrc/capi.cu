@@ -275,6 +275,7 @@ void lbm_config_default(lbm_config *cfg) {
   cfg->gas_threshold = 1.0;
   cfg->kernel = LBM_KERNEL_AUTO;
   cfg->tile = 0;
+  cfg->nucleus_radius = 3.0;
 }
 
 lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
@@ -416,11 +417,24 @@ lbm_status lbm_sample_sites(int64_t nx, int64_t ny, int64_t nz, int32_t n, doubl
 }
 
 lbm_status lbm_seed_bubbles(lbm_ctx *c, const lbm_bubble *b, int32_t n, double rho_l,
-                            double rho_g, double width, double noise_amp, uint64_t seed) {
+                            double rho_g, double width, double noise_amp, double min_spacing,
+                            uint64_t seed) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
-  if (n < 0 || (n > 0 && !b)) return fail(LBM_EINVAL, "bad bubble list");
+  if (n < 0) return fail(LBM_EINVAL, "bad bubble list");
   if (!(width > 0) || !std::isfinite(rho_l) || !std::isfinite(rho_g) || !std::isfinite(noise_amp))
     return fail(LBM_EINVAL, "width must be > 0, densities finite");
+  std::vector<lbm_bubble> drawn;
+  if (!b && n > 0) {
+    // no list: draw n nuclei from the seed with the host sampler
+    const double r = c->cfg.nucleus_radius;
+    if (!(min_spacing >= 0) || !std::isfinite(min_spacing) || !(r >= 0) || !std::isfinite(r))
+      return fail(LBM_EINVAL, "min_spacing and the nucleus radius must be finite and >= 0");
+    drawn.resize(n);
+    int32_t got = 0;
+    CKS(lbm_sample_sites(c->cfg.nx, c->cfg.ny, c->cfg.nz, n, r, r, min_spacing, 0.0, seed,
+                         10000000, drawn.data(), &got));
+    b = drawn.data();
+  }
   for (int32_t k = 0; k < n; ++k)
     if (!std::isfinite(b[k].x) || !std::isfinite(b[k].y) || !std::isfinite(b[k].z) ||
         !std::isfinite(b[k].r))
@@ -470,6 +484,15 @@ lbm_status lbm_seed_bubbles(lbm_ctx *c, const lbm_bubble *b, int32_t n, double r
   c->site_pending = false;
   c->site_labels.assign(n, -1);
   CK(cudaStreamSynchronize(c->s));  // host staging buffers go out of scope
+  return LBM_OK;
+}
+
+lbm_status lbm_read_sites(const lbm_ctx *c, lbm_bubble *out, int32_t n) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
+  if (n != (int32_t)c->bubbles.size() || (n > 0 && !out))
+    return fail(LBM_EINVAL, "n must equal the number of seeded bubbles");
+  std::copy(c->bubbles.begin(), c->bubbles.end(), out);
   return LBM_OK;
 }
 

@@ -4,6 +4,7 @@
 // injection runs as a third, one-thread-per-site kernel.  This path moves
 // 3*Q*S + 2*sizeof(psi) bytes per update instead of the fused kernel's
 // 2*Q*S; it is kept as a simple, independently written comparison path.
+#include <cmath>
 #include <mutex>
 
 #include "internal.h"
@@ -193,38 +194,92 @@ cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi, cudaSt
 }  // namespace sclbm
 
 // ---- allocation-free time step ---------------------------------------------
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, hosts that forbid device allocation inside their time
-// loop, or programs that hand the library a fixed memory budget.  The
+// Some callers cannot call cudaMalloc: a host framework that owns the whole
+// device-memory pool and forbids allocations behind its back, a time loop
+// that must not stall on the allocator (cudaMalloc and cudaFree can
+// synchronise the device), or a program held to a fixed memory budget.  The
 // two-pass step needs a psi field between its two kernels; this entry point
 // keeps that field in a file-scope device array of fixed size, so it
-// allocates nothing.  Its device address is looked up once per device (the
-// array's name is only a host-side stand-in in host code).
+// allocates nothing.  In host code the array's name is only a host-side
+// stand-in: its device address is looked up with cudaGetSymbolAddress, once
+// per CUDA context (keyed by the context's process-unique id, so a second
+// context on the same device, or the new primary context after
+// cudaDeviceReset, gets its own look-up).
 namespace sclbm {
 namespace {
 
 constexpr int64_t kStaticPsiCells = 2097152;  // 8 MB of FP32: up to 128^3 cells
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 
 static __device__ __align__(256) float g_static_psi[kStaticPsiCells];
 
-std::mutex g_static_mu;
-float *g_static_psi_ptr[kMaxDevices] = {};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
-// device address of g_static_psi on the current device (looked up once)
-cudaError_t static_psi_address(float **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_psi_ptr[dev]) {
+std::mutex g_static_mu;
+struct StaticEntry {
+  unsigned long long ctx_id;
+  float *psi;
+};
+StaticEntry g_static_cache[kMaxContexts];
+int g_static_n = 0, g_static_next = 0;
+
+// driver functions used to identify the current context (fetched once)
+bool ctx_functions(CtxGetCurrentFn *cur, CtxGetIdFn *id) {
+  static CtxGetCurrentFn f_cur = nullptr;
+  static CtxGetIdFn f_id = nullptr;
+  if (!f_cur || !f_id) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_psi);
-    if (e != cudaSuccess) return e;
-    g_static_psi_ptr[dev] = static_cast<float *>(p);
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f_cur = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f_id = reinterpret_cast<CtxGetIdFn>(p);
   }
-  *out = g_static_psi_ptr[dev];
+  *cur = f_cur;
+  *id = f_id;
+  return f_cur && f_id;
+}
+
+// device address of g_static_psi in the current context (looked up on the
+// first call in each context, then cached)
+cudaError_t static_psi_address(float **out) {
+  CtxGetCurrentFn get_cur;
+  CtxGetIdFn get_id;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!ctx_functions(&get_cur, &get_id)) return cudaErrorNotSupported;
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (!ctx) {
+    // no context is current yet: cudaSetDevice makes the current device's
+    // primary context current (it allocates nothing)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return e;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  }
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  for (int k = 0; k < g_static_n; ++k)
+    if (g_static_cache[k].ctx_id == id) {
+      *out = g_static_cache[k].psi;
+      return cudaSuccess;
+    }
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_psi);
+  if (e != cudaSuccess) return e;
+  // a full table reuses its oldest entry: a context evicted that way is
+  // looked up again on its next call
+  const int slot = g_static_n < kMaxContexts ? g_static_n++ : g_static_next;
+  if (g_static_n == kMaxContexts) g_static_next = (slot + 1) % kMaxContexts;
+  g_static_cache[slot] = StaticEntry{id, static_cast<float *>(p)};
+  *out = static_cast<float *>(p);
   return cudaSuccess;
 }
 
@@ -239,13 +294,16 @@ extern "C" lbm_status lbm_step_static_f32(int32_t lattice, int64_t nx, int64_t n
     return set_error(LBM_EINVAL, "lbm_step_static_f32: unknown lattice");
   if (nx < 1 || ny < 1 || nz < 1 || (lattice == LBM_D2Q9 && nz != 1))
     return set_error(LBM_EINVAL, "lbm_step_static_f32: extents must be >= 1 (nz = 1 for D2Q9)");
-  if (nx > kStaticPsiCells || ny > kStaticPsiCells || nz > kStaticPsiCells ||
-      nx * ny * nz > kStaticPsiCells)
+  // nx * ny * nz <= cap, tested by division so that no product can overflow
+  if (nx > kStaticPsiCells || ny > kStaticPsiCells / nx || nz > kStaticPsiCells / (nx * ny))
     return set_error(LBM_EINVAL,
                      "lbm_step_static_f32: more than 2097152 cells, the size of the static "
                      "scratch array (use lbm_create/lbm_step for larger lattices)");
-  if (!(tau > 0.5) || !(rho0 > 0) || !(G == G))
-    return set_error(LBM_EINVAL, "lbm_step_static_f32: tau must be > 0.5, rho0 > 0");
+  if (!(tau > 0.5) || !std::isfinite(tau) || !(rho0 > 0) || !std::isfinite(rho0) ||
+      !std::isfinite(G))
+    return set_error(LBM_EINVAL,
+                     "lbm_step_static_f32: tau must be finite and > 0.5, rho0 finite and > 0, "
+                     "G finite");
   if (!f_in || !f_out || static_cast<const void *>(f_in) == static_cast<const void *>(f_out))
     return set_error(LBM_EINVAL, "lbm_step_static_f32: f_in and f_out must be distinct buffers");
   float *psi = nullptr;

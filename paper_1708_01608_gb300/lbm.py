@@ -48,7 +48,7 @@ class Config(C.Structure):
         ("kernel", C.c_int32), ("tile", C.c_int32),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-        ("debug_flags", C.c_int32),
+        ("debug_flags", C.c_int32), ("nucleus_radius", C.c_double),
     ]
 
 
@@ -113,7 +113,8 @@ def _load():
         "lbm_create": (i32, [C.POINTER(Config), C.POINTER(P_)]),
         "lbm_destroy": (None, [P_]),
         "lbm_sample_sites": (i32, [i64, i64, i64, i32, d, d, d, d, u64, i64, P_, C.POINTER(i32)]),
-        "lbm_seed_bubbles": (i32, [P_, P_, i32, d, d, d, d, u64]),
+        "lbm_seed_bubbles": (i32, [P_, P_, i32, d, d, d, d, d, u64]),
+        "lbm_read_sites": (i32, [P_, P_, i32]),
         "lbm_inject": (i32, [P_, P_, P_, i32]),
         "lbm_read_budgets": (i32, [P_, P_, i32]),
         "lbm_step": (i32, [P_, i64]),
@@ -143,6 +144,7 @@ def _load():
         "lbm_ensemble_results": (i32, [P_, P_, i32]),
         "lbm_ensemble_stats": (i32, [P_, P_]),
         "lbm_ensemble_read_f": (i32, [P_, i32, P_, sz]),
+        "lbm_fp64_rate": (i32, [i32, C.POINTER(d)]),
         "lbm_last_error": (C.c_char_p, []),
         "lbm_version": (C.c_char_p, []),
     }
@@ -157,14 +159,15 @@ _lib = _load()
 
 # every symbol the header declares (checked by the CPU tests)
 EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites",
-           "lbm_seed_bubbles", "lbm_inject", "lbm_set_injection_mode", "lbm_read_budgets",
+           "lbm_seed_bubbles", "lbm_read_sites", "lbm_inject", "lbm_set_injection_mode", "lbm_read_budgets",
            "lbm_step", "lbm_step_count",
            "lbm_autotune", "lbm_plan_info",
            "lbm_sync", "lbm_pressure_laplacian", "lbm_label_gas", "lbm_diagnose", "lbm_film_probe",
            "lbm_run_until_rupture",
            "lbm_site_labels", "lbm_bubble_sizes", "lbm_film_cells", "lbm_film_pairs",
            "lbm_diagnostic_interval",
-           "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_last_error",
+           "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_fp64_rate",
+           "lbm_last_error",
            "lbm_version", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_run",
            "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f")
 
@@ -225,7 +228,8 @@ class Lattice:
 
     def __init__(self, lattice="D3Q19", nx=64, ny=64, nz=1, tau=1.0, G=-5.0, rho0=1.0,
                  storage="f32", rho_ref=1.0, gas_threshold=1.0, kernel="auto", tile=0,
-                 stream: Optional[int] = None, torch_memory: bool = True, debug_flags: int = 0):
+                 stream: Optional[int] = None, torch_memory: bool = True, debug_flags: int = 0,
+                 nucleus_radius: float = 3.0):
         cfg = Config()
         _lib.lbm_config_default(C.byref(cfg))
         cfg.lattice = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
@@ -236,6 +240,7 @@ class Lattice:
         cfg.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         cfg.tile = int(tile)
         cfg.debug_flags = int(debug_flags)
+        cfg.nucleus_radius = float(nucleus_radius)
         self._mem = None
         if torch_memory:
             try:
@@ -283,12 +288,28 @@ class Lattice:
         return self._h
 
     # -- set-up
-    def seed_bubbles(self, bubbles, rho_l, rho_g, width=2.0, noise_amp=0.0, seed=0):
+    def seed_bubbles(self, bubbles, rho_l, rho_g, width=2.0, noise_amp=0.0, seed=0, n=0,
+                     min_spacing=0.0):
+        """Initial state (lbm_seed_bubbles).  bubbles: (n, 4) rows x, y, z, r;
+        None with n > 0 draws n nuclei of the configured nucleus radius from
+        the seed, at least min_spacing apart (read them with sites())."""
+        if bubbles is None and n > 0:
+            self.nsites = int(n)
+            _check(_lib.lbm_seed_bubbles(self._h, None, int(n), rho_l, rho_g, width, noise_amp,
+                                         float(min_spacing), seed & (2**64 - 1)))
+            return
         b = np.ascontiguousarray(np.zeros((0, 4)) if bubbles is None else bubbles,
                                  dtype=np.float64).reshape(-1, 4)
         self.nsites = len(b)
         _check(_lib.lbm_seed_bubbles(self._h, _ptr(b) if len(b) else None, len(b), rho_l, rho_g,
-                                     width, noise_amp, seed & (2**64 - 1)))
+                                     width, noise_amp, float(min_spacing), seed & (2**64 - 1)))
+
+    def sites(self):
+        """The seeded bubbles (given or drawn) as (n, 4) rows x, y, z, r."""
+        out = (Bubble * max(self.nsites, 1))()
+        _check(_lib.lbm_read_sites(self._h, C.cast(out, C.c_void_p), self.nsites))
+        return np.array([[b.x, b.y, b.z, b.r] for b in out[:self.nsites]],
+                        dtype=np.float64).reshape(-1, 4)
 
     def inject(self, rate, budget):
         r = np.ascontiguousarray(rate, dtype=np.float64).reshape(-1)
@@ -486,6 +507,13 @@ def step_static_f32(lattice, nx, ny, nz, tau, G, rho0, f_in_ptr, f_out_ptr, stre
     lat = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
     _check(_lib.lbm_step_static_f32(lat, nx, ny, nz, tau, G, rho0, C.c_void_p(f_in_ptr),
                                     C.c_void_p(f_out_ptr), C.c_void_p(stream) if stream else None))
+
+
+def fp64_rate(iters=20000):
+    """Measured FP64 FMA rate of the current device in TFLOP/s (lbm_fp64_rate)."""
+    out = C.c_double(0)
+    _check(_lib.lbm_fp64_rate(int(iters), C.byref(out)))
+    return float(out.value)
 
 
 class Ensemble:

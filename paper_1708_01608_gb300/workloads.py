@@ -25,12 +25,19 @@ FOAM_128 = dict(
     sites=dict(n=64, r_min=3.0, r_max=3.0, min_spacing=12.0, min_gap=0.0),
     rate=1e-4, budget=50.0, steps=20000, diag_every=100, threshold=1.0, rho_ref=2.0)
 
-# 1000 bubbles r ~ U(4, 12) on 512^3, tau 0.8 (precision study)
+# 1000 bubbles r ~ U(4, 12) on 512^3, tau 0.8.  The liquid starts at 1.80,
+# not at the nominal 2.0: in a closed periodic box a bubble of radius R holds
+# only while the liquid sits below the flat-interface coexistence density
+# (1.93 at G = -5) by about 2 sigma / R, since no reservoir absorbs what the
+# Laplace pressure pushes into the liquid.  With 1.9 % of the volume in gas,
+# the FP64 oracle dissolves these bubbles within 100 steps at 2.0 and at 1.93
+# and keeps them over 800 steps at 1.80 (64^3, the same recipe).  The offset
+# storage's reference density is that liquid density.
 FOAM_512 = dict(
     name="d3q19_foam_512", lattice="D3Q19", nx=512, ny=512, nz=512, tau=0.8, G=-5.0,
-    rho0=1.0, storage="f32", rho_l=2.0, rho_g=0.15, width=2.0, noise=1e-3, seed=2,
+    rho0=1.0, storage="f32", rho_l=1.8, rho_g=0.15, width=2.0, noise=1e-3, seed=2,
     sites=dict(n=1000, r_min=4.0, r_max=12.0, min_spacing=0.0, min_gap=4.0),
-    rate=0.0, budget=0.0, steps=2000, rho_ref=2.0, threshold=1.0)
+    rate=0.0, budget=0.0, steps=2000, rho_ref=1.8, threshold=1.0)
 
 # full foam, 4096 sites, FP16-offset storage (768^3)
 FOAM_768 = dict(

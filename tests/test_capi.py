@@ -110,3 +110,62 @@ def test_fig3_fit_recovers_exact_forms():
     assert f["corr_h_c_R_d"] > 0.99 and f["n"] == 7
     with pytest.raises(ValueError):
         fit_fig3(R_b[:2], R_d[:2], h_c[:2])
+
+
+def test_static_step_rejects_without_gpu(lbm):
+    """lbm_step_static_f32 bounds nx*ny*nz by its 2,097,152-cell scratch
+    array without forming an overflowing product (2^21 per axis passes
+    every per-axis bound, and (2^21)^3 = 2^63 overflows int64), rejects
+    non-finite parameters and aliased buffers, and launches nothing."""
+    L = lbm.lib()
+    p, q = C.c_void_p(1 << 20), C.c_void_p(1 << 21)
+    big = 2 ** 21
+    for ext in [(big, big, big), (big, big, 1), (256, 128, 128), (big + 1, 1, 1),
+                (2, big, 2), (1, 1, big + 1)]:
+        assert L.lbm_step_static_f32(1, *ext, 0.9, -5.0, 1.0, p, q, None) == lbm.EINVAL, ext
+        assert "2097152" in L.lbm_last_error().decode()
+    inf, nan = float("inf"), float("nan")
+    for tau, G, rho0 in [(inf, -5.0, 1.0), (0.9, inf, 1.0), (0.9, nan, 1.0), (0.9, -5.0, inf),
+                         (0.5, -5.0, 1.0), (0.9, -5.0, 0.0)]:
+        assert L.lbm_step_static_f32(1, 16, 16, 16, tau, G, rho0, p, q, None) == lbm.EINVAL
+    assert L.lbm_step_static_f32(1, 16, 16, 16, 0.9, -5.0, 1.0, p, p, None) == lbm.EINVAL
+    assert L.lbm_step_static_f32(0, 16, 16, 2, 0.9, -5.0, 1.0, p, q, None) == lbm.EINVAL
+    assert L.lbm_step_static_f32(2, 16, 16, 16, 0.9, -5.0, 1.0, p, q, None) == lbm.EINVAL
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("lat,ext,n,r,spacing,seed", [
+    ("D3Q19", (128, 128, 128), 64, 3.0, 12.0, 1),
+    ("D2Q9", (96, 64, 1), 5, 6.0, 20.0, 9)])
+def test_seed_bubbles_draws_sites_like_the_oracle(lbm, lat, ext, n, r, spacing, seed):
+    """lbm_seed_bubbles with no bubble list draws n nuclei from the seed:
+    the drawn sites equal the oracle's sampler bit for bit, and the seeded
+    state equals the one seeded from that explicit list."""
+    import torch
+    assert torch.cuda.is_available()
+    nx, ny, nz = ext
+    A = lbm.Lattice(lat, nx, ny, nz, storage="f64", nucleus_radius=r)
+    A.seed_bubbles(None, 2.0, 0.15, 2.0, 1e-3, seed, n=n, min_spacing=spacing)
+    got, want = O.sample_sites(nx, ny, nz, n, r, r, spacing, 0.0, seed)
+    assert got == n
+    assert (A.sites() == want).all()
+    B = lbm.Lattice(lat, nx, ny, nz, storage="f64")
+    B.seed_bubbles(want, 2.0, 0.15, 2.0, 1e-3, seed)
+    assert (A.read("rho") == B.read("rho")).all()
+    with pytest.raises(lbm.LBMError) as e:  # more nuclei than the spacing allows
+        A.seed_bubbles(None, 2.0, 0.15, 2.0, 0.0, seed, n=10 ** 4, min_spacing=40.0)
+    assert e.value.status == lbm.ESTATE
+    A.close()
+    B.close()
+
+
+@pytest.mark.gpu
+def test_fp64_rate_is_measured(lbm):
+    """The measured FP64 FMA rate is positive and within an order of
+    magnitude of what the unit counts give (2 DFMA per SM and cycle)."""
+    import torch
+    assert torch.cuda.is_available()
+    r = lbm.fp64_rate(2000)
+    props = torch.cuda.get_device_properties(0)
+    derived = 2 * props.multi_processor_count * 2 * 2.07e9 / 1e12
+    assert 0.1 * derived < r < 10 * derived, (r, derived)

@@ -839,3 +839,98 @@ def test_spread_injection_mass_ledger_with_relabelling():
     # FP64 totals of a mass ~3800 carry ~1e-11 of rounding; a lost or doubled
     # deposit would be off by >= 2e-4
     assert O.totals(O.D2Q9, g)[0] - m0 == pytest.approx(taken, abs=1e-9)
+
+
+# ------------------------------------------------- hand-expanded 4x4 D2Q9 step
+
+# D2Q9 as printed in the lattice Boltzmann textbooks (rest, E, N, W, S, NE,
+# NW, SW, SE), written out here rather than read from the oracle
+HAND_C = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+
+
+def _hand_step(f, tau, G, exp, one, sites=()):
+    """One Shan-Chen step on a 4x4 periodic grid, every operation written out
+    in the number type of ``one`` (Fraction: exact; Decimal: 50 digits).
+    f[i][y][x] are the populations that have arrived at (x, y); ``exp`` is
+    the exponential of that number type (unused when G = 0).  Order of
+    Sec. 3.1: moments, psi of every cell, the force from the neighbours'
+    psi, the velocity shift u = (j + tau F)/rho, the equilibrium, BGK, the
+    blowing-agent deposit w_i dm at a site cell, streaming to x + c_i."""
+    n = 4
+    w = [one * 4 / 9] + [one / 9] * 4 + [one / 36] * 4
+    rho = [[sum(f[i][y][x] for i in range(9)) for x in range(n)] for y in range(n)]
+    jx = [[sum(f[i][y][x] * HAND_C[i][0] for i in range(9)) for x in range(n)] for y in range(n)]
+    jy = [[sum(f[i][y][x] * HAND_C[i][1] for i in range(9)) for x in range(n)] for y in range(n)]
+    psi = [[(one - exp(-rho[y][x])) if G != 0 else one for x in range(n)] for y in range(n)]
+    fs = [[[None] * n for _ in range(n)] for _ in range(9)]
+    for y in range(n):
+        for x in range(n):
+            sx = sum(w[i] * psi[(y + HAND_C[i][1]) % n][(x + HAND_C[i][0]) % n] * HAND_C[i][0]
+                     for i in range(1, 9))
+            sy = sum(w[i] * psi[(y + HAND_C[i][1]) % n][(x + HAND_C[i][0]) % n] * HAND_C[i][1]
+                     for i in range(1, 9))
+            Fx, Fy = -G * psi[y][x] * sx, -G * psi[y][x] * sy
+            ux = (jx[y][x] + tau * Fx) / rho[y][x]
+            uy = (jy[y][x] + tau * Fy) / rho[y][x]
+            for i in range(9):
+                cu = HAND_C[i][0] * ux + HAND_C[i][1] * uy
+                feq = w[i] * rho[y][x] * (1 + 3 * cu + cu * cu * 9 / 2 - (ux * ux + uy * uy) * 3 / 2)
+                fs[i][y][x] = f[i][y][x] - (f[i][y][x] - feq) / tau
+    for (sxy, dm) in sites:
+        for i in range(9):
+            fs[i][sxy[1]][sxy[0]] += w[i] * dm
+    out = [[[None] * n for _ in range(n)] for _ in range(9)]
+    for i in range(9):
+        for y in range(n):
+            for x in range(n):
+                out[i][(y + HAND_C[i][1]) % n][(x + HAND_C[i][0]) % n] = fs[i][y][x]
+    return out
+
+
+def _hand_start():
+    """Seeded 4x4 start (float64), far from equilibrium: densities 0.2..2.2,
+    every population perturbed."""
+    rng = np.random.default_rng(44)
+    rho = rng.uniform(0.2, 2.2, (4, 4))
+    _, w = O.velocities(O.D2Q9)
+    f = w[:, None, None] * rho[None] * (1 + rng.uniform(-0.3, 0.3, (9, 4, 4)))
+    return f
+
+
+@pytest.mark.parametrize("G", [0.0, -5.0])
+def test_hand_expanded_single_step_4x4(G):
+    """One D2Q9 step on a 4x4 periodic grid written out by hand: G = 0 in
+    exact rational arithmetic (with one blowing-agent site), G = -5 with
+    psi = 1 - exp(-rho) and everything after it in 50-digit decimal
+    arithmetic.  The oracle's FP64 step matches to 1e-15 of the largest
+    population (a few ulp), which pins its velocity table and order,
+    streaming direction, force sign and neighbour, velocity shift,
+    equilibrium, relaxation and deposit placement at once."""
+    from decimal import Decimal, localcontext
+    from fractions import Fraction
+    c, _ = O.velocities(O.D2Q9)
+    assert [tuple(v[:2]) for v in c.tolist()] == HAND_C   # the convention both use
+    f0 = _hand_start()
+    tau = 0.8
+    if G == 0.0:
+        site, dm = (1, 2), 1.0 / 64
+        exact = _hand_step([[[Fraction(float(v)) for v in row] for row in f0[i]] for i in range(9)],
+                           Fraction(tau), Fraction(0), None, Fraction(1),
+                           sites=[(site, Fraction(dm))])
+        want = np.array([[[float(v) for v in row] for row in exact[i]] for i in range(9)])
+        budget = np.array([1.0])
+        got = O.run(O.D2Q9, f0[:, None], 1, tau, G, sites=np.array([site[0] + 4 * site[1]]),
+                    rate=np.array([dm]), budget=budget)[:, 0]
+        assert budget[0] == 1.0 - dm
+    else:
+        with localcontext() as ctx:
+            ctx.prec = 50
+            D = lambda v: Decimal(float(v))  # noqa: E731  exact binary value
+            exact = _hand_step([[[D(v) for v in row] for row in f0[i]] for i in range(9)],
+                               Decimal(tau), Decimal(G), lambda v: v.exp(), Decimal(1))
+            want = np.array([[[float(v) for v in row] for row in exact[i]] for i in range(9)])
+        got = O.run(O.D2Q9, f0[:, None], 1, tau, G)[:, 0]
+        # the force is not small here: the step differs from the G = 0 one
+        base = O.run(O.D2Q9, f0[:, None], 1, tau, 0.0)[:, 0]
+        assert np.abs(base - want).max() > 1e-3
+    assert np.abs(got - want).max() <= 1e-15 * np.abs(want).max()

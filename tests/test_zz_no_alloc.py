@@ -1,10 +1,12 @@
 """The allocation-free step entry point (lbm_step_static_f32).
 
-Callers that cannot allocate device memory (graph capture, allocation-free
-time loops, fixed memory budgets) advance caller-owned FP32 buffers with
-lbm_step_static_f32, whose scratch psi field is a static device array.  This
-file is collected last so that a run stopping at the first failure has run
-every other test; it passes alone in a fresh process and after the others.
+Some callers cannot allocate device memory: a host framework that owns the
+whole device-memory pool, a time loop that must not stall on the allocator,
+a program held to a fixed memory budget.  They advance caller-owned FP32
+buffers with lbm_step_static_f32, whose scratch psi field is a static device
+array.  This file is collected last so that a run stopping at the first
+failure has run every other test; it passes alone in a fresh process and
+after the others.
 """
 import ctypes as C
 
