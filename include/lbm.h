@@ -112,6 +112,18 @@ typedef struct {
   double nucleus_radius; /* radius of the nuclei lbm_seed_bubbles samples
                             when given no bubble list (Sec. 3: random
                             nucleation sites); default 3 cells */
+  int32_t mass_residual; /* 16-bit storages only; 0 (default) or 1.  With
+                            1 every cell keeps an FP32 rounding residual:
+                            what the rounding of its stored populations took
+                            off in the last step (the blowing agent's deposit
+                            included) joins the cell's mass in its next
+                            collision, so stored mass plus residuals is
+                            conserved to FP32 rounding, and a deposit far
+                            below a 16-bit quantum is kept (Sec. 3: gas is
+                            added every step until the agent is finished).
+                            The residual is part of population 0 in every
+                            read-back and diagnostic; it costs 8 bytes per
+                            lattice update on top of 2 Q x 2 */
 } lbm_config;
 
 #define LBM_DEBUG_WITHHOLD_TMA 1
@@ -474,6 +486,87 @@ lbm_status lbm_ensemble_stats(const lbm_ensemble *ens, double out[4]);
 
 /* Current populations of one domain as doubles f[i*N + x + nx*y]. */
 lbm_status lbm_ensemble_read_f(lbm_ensemble *ens, int32_t domain, double *host, size_t bytes);
+
+/* ---- multi-lattice Shan-Chen model (Sec. 3.1, Fig. 1) -------------------
+ * The paper's modified model puts each phase on its own lattice: every
+ * bubble on one, the fluid on another (Fig. 1 steps 3-5); the lattices are
+ * coupled and their interactions computed (step 6); eta_m switches the
+ * barrier algorithm off when d2p/dn2 = 0 across the film, and the bubbles
+ * merge (Sec. 3.1; lattices merged, steps 8-9).  The paper gives no
+ * equations for it; this library's reading: lattice 0 holds the fluid and
+ * lattice k = 1 .. nl-1 the gas of bubble k, coupled by the multicomponent
+ * Shan-Chen force
+ *   F_s(x) = -psi_s(x) sum_t Gm[s][t] sum_i w_i psi_t(x + c_i) c_i,
+ * psi_s = rho0 (1 - exp(-rho_s/rho0)), with Gm[0][0] = G (the fluid's own
+ * attraction: nl = 1 is the single-component model of lbm_step), Gm[0][k] =
+ * Gm[k][0] = G_x (fluid and gas), Gm[k][k] = 0 and, between two bubbles,
+ * Gm[k][l] = eta_m(k, l) G_b (the barrier; eta_m = 1 until the criterion
+ * fires).  Every lattice relaxes with tau towards f_eq(rho_s, u_s),
+ *   u' = sum_s j_s / sum_s rho_s,  u_s = u' + tau F_s / rho_s
+ * (u_s = u' where rho_s = 0: an empty lattice has f_eq = 0), then streams.  Populations are plain FP64 or FP32 values f[s][i][cell] (same
+ * cell order and velocity order as above).  The pressure of the coupled
+ * lattices is p = rho_total/3 + 1/6 sum_s sum_t Gm[s][t] psi_s psi_t (the
+ * EOS of Sec. 3.1 for nl = 1). */
+typedef struct lbm_ml_ctx lbm_ml_ctx; /* opaque */
+typedef struct {
+  int32_t lattice;       /* LBM_D2Q9 or LBM_D3Q19 */
+  int32_t storage;       /* LBM_F64 or LBM_F32 */
+  int64_t nx, ny, nz;    /* periodic extents; nz = 1 for D2Q9 */
+  int32_t nl;            /* lattices, 1..8: the fluid and nl - 1 bubbles */
+  double tau, rho0;
+  double G, G_x, G_b;    /* fluid self-coupling, fluid-gas, inter-bubble barrier */
+  void *stream;          /* cudaStream_t, may be NULL */
+  lbm_alloc_fn alloc;    /* NULL: cudaMalloc/cudaFree */
+  lbm_free_fn free;
+  void *alloc_user;
+} lbm_ml_config;
+
+/* Defaults: D2Q9, FP64, 128^2, nl 3, tau 1, rho0 1, G -5, G_x 1, G_b 0. */
+void lbm_ml_config_default(lbm_ml_config *cfg);
+/* Create on the current device.  Errors: EINVAL (as lbm_create; nl outside
+ * 1..8, storage not FP64/FP32, non-finite couplings), ENOMEM. */
+lbm_status lbm_ml_create(const lbm_ml_config *cfg, lbm_ml_ctx **out);
+void lbm_ml_destroy(lbm_ml_ctx *ctx);
+/* The coupling matrix in use (nl x nl, row-major): it changes only when a
+ * pair merges. */
+lbm_status lbm_ml_coupling(const lbm_ml_ctx *ctx, double *Gm);
+/* Initial state (Sec. 3.1: bubbles at the nucleation sites, the fluid
+ * elsewhere): b holds the nl - 1 bubbles (x, y, z, r).  The fluid lattice
+ * gets the profile of lbm_seed_bubbles over all bubbles (liquid rho_l, its
+ * vapour rho_v inside, noise from seed); bubble k's lattice gets rho_gas
+ * inside bubble k with the same tanh profile (zero far outside, no noise);
+ * f = w rho at rest.  The bubble centres, rounded, are the injection
+ * sites, site k depositing into lattice k.  Every barrier is switched on
+ * (eta_m = 1).  Synchronous.  Errors: EINVAL. */
+lbm_status lbm_ml_seed(lbm_ml_ctx *ctx, const lbm_bubble *b, double rho_l, double rho_v,
+                       double rho_gas, double width, double noise_amp, uint64_t seed);
+/* Populations as doubles f[(s*Q + i)*N + cell] (bytes = nl*Q*N*8), written
+ * (rounded to the storage) or read.  Synchronous. */
+lbm_status lbm_ml_write_f(lbm_ml_ctx *ctx, const double *f, size_t bytes);
+lbm_status lbm_ml_read_f(lbm_ml_ctx *ctx, double *f, size_t bytes);
+/* Virtual blowing agent (Sec. 3), one site per bubble: each step dm =
+ * min(rate[k], budget[k]) leaves the FP64 budget and w_i dm joins lattice
+ * k + 1's post-collision populations at the site.  n = nl - 1, or 0 to
+ * stop.  Errors: EINVAL, ESTATE. */
+lbm_status lbm_ml_inject(lbm_ml_ctx *ctx, const double *rate, const double *budget, int32_t n);
+lbm_status lbm_ml_read_budgets(lbm_ml_ctx *ctx, double *budget, int32_t n);
+/* Advance nsteps (asynchronous on the stream).  Errors: EINVAL, ESTATE, ECUDA. */
+lbm_status lbm_ml_step(lbm_ml_ctx *ctx, int64_t nsteps);
+int64_t lbm_ml_step_count(const lbm_ml_ctx *ctx);
+/* eta_m(k, l) = 0 (Sec. 3.1): bubble l's lattice is merged into bubble k's
+ * (f_k += f_l, f_l = 0) and their barrier coupling removed.  Synchronous. */
+lbm_status lbm_ml_merge(lbm_ml_ctx *ctx, int32_t k, int32_t l);
+/* FP64 fields to host: rho (nl*N: every lattice's density, may be NULL) and
+ * p (N: the pressure of the coupled lattices, may be NULL).  Synchronous. */
+lbm_status lbm_ml_fields(lbm_ml_ctx *ctx, double *rho, double *p);
+/* The rupture criterion of lbm_run_until_rupture (Sec. 3.1 / Sec. 4) on
+ * this model: the film is found on the fluid lattice's density, its
+ * d2p/dn2 on the coupled pressure.  When it fires, eta_m of the pair (k, l)
+ * becomes 0 and their lattices merge (lbm_ml_merge); a film that vanishes
+ * first is reported as merged.  Synchronous. */
+lbm_status lbm_ml_run_until_rupture(lbm_ml_ctx *ctx, const int64_t *line, double rho_mid,
+                                     double eps_arm, double h_max, int64_t diag_every,
+                                     int64_t max_steps, int32_t k, int32_t l, lbm_rupture *out);
 
 /* Allocation-free time step.  The paper has no counterpart: this entry point
  * serves callers that cannot allocate device memory - a host framework that

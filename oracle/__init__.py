@@ -82,6 +82,9 @@ def _L():
         _lib.orc_film_cells.argtypes = [C.c_int, i64, i64, i64, P, P, C.c_int, d, P, P, i64, P, P]
         _lib.orc_film_midpoints.argtypes = [C.c_int, i64, i64, i64, P, P, C.c_int, d, P, P, i64,
                                             P, P]
+        _lib.orc_ml_run.argtypes = [C.c_int, i64, i64, i64, i32, d, P, d, P, i64, i32, P, P, P, P]
+        _lib.orc_ml_force.argtypes = [C.c_int, i64, i64, i64, i32, P, P, P, P, P]
+        _lib.orc_ml_pressure.argtypes = [i64, i32, P, P, d, P]
     return _lib
 
 
@@ -428,3 +431,119 @@ def run_until_rupture(lat, f, tau, G, start, axis, length, rho_mid, eps_arm, max
         if out is not None:
             return dict(step=t, f=f, **out)
     return dict(fired=False, merged=False, step=t, h_c=0.0, h_probe=0.0, r_d=0.0, f=f)
+
+
+# ---- multi-lattice Shan-Chen (Sec. 3.1, Fig. 1) -----------------------------
+
+def ml_coupling(nl, G, G_x, G_b, eta=None):
+    """Coupling matrix of the multi-lattice model: lattice 0 = the fluid
+    (self-attraction G), lattices 1..nl-1 = one gas lattice per bubble
+    (fluid-gas coupling G_x, no self-coupling) and, between two different
+    bubbles k and l, the barrier eta_m(k, l) G_b (eta: nl x nl array of 0/1,
+    default all 1)."""
+    Gm = np.zeros((nl, nl))
+    Gm[0, 0] = G
+    Gm[0, 1:] = G_x
+    Gm[1:, 0] = G_x
+    for k in range(1, nl):
+        for l in range(1, nl):
+            if k != l:
+                Gm[k, l] = G_b * (1.0 if eta is None else float(eta[k][l]))
+    return Gm
+
+
+def ml_run(lat, f, nsteps, tau, Gm, rho0=1.0, sites=None, site_lattice=None, rate=None,
+           budget=None):
+    """Advance the lattices f (nl, Q, nz, ny, nx), copied, by nsteps of the
+    multi-lattice step (orc_ml_step).  sites: linear cells; site_lattice:
+    the lattice each site deposits into; budget is updated in place."""
+    f = _f64(f).copy()
+    nl, q, nz, ny, nx = f.shape
+    Gm = _f64(Gm)
+    assert Gm.shape == (nl, nl)
+    n = 0 if sites is None else len(sites)
+    sc = np.ascontiguousarray(sites, dtype=np.int64) if n else None
+    sl = np.ascontiguousarray(site_lattice, dtype=np.int32) if n else None
+    rt = _f64(rate) if n else None
+    if n:
+        assert budget is not None and budget.dtype == np.float64 and budget.flags.c_contiguous
+    _L().orc_ml_run(lat, nx, ny, nz, nl, tau, _p(Gm), rho0, _p(f), int(nsteps), n, _p(sc),
+                    _p(sl), _p(rt), _p(budget) if n else None)
+    return f
+
+
+def ml_force(lat, psi, Gm):
+    """Multicomponent Shan-Chen force (Fx, Fy, Fz), each (nl, nz, ny, nx),
+    from psi fields (nl, nz, ny, nx) and the coupling matrix."""
+    psi = _f64(psi)
+    nl, nz, ny, nx = psi.shape
+    out = [np.empty_like(psi) for _ in range(3)]
+    _L().orc_ml_force(lat, nx, ny, nz, nl, _p(psi), _p(_f64(Gm)), *[_p(o) for o in out])
+    return tuple(out)
+
+
+def ml_moments(lat, f):
+    """(rho, jx, jy, jz) of every lattice, each (nl, nz, ny, nx)."""
+    f = _f64(f)
+    out = [moments(lat, f[s]) for s in range(f.shape[0])]
+    return tuple(np.stack([o[m] for o in out]) for m in range(4))
+
+
+def ml_pressure(rho, Gm, rho0=1.0):
+    """Pressure of the coupled lattices, rho (nl, ...) -> p (...):
+    p = rho_total/3 + 1/6 sum_s sum_t Gm[s][t] psi_s psi_t."""
+    rho = _f64(rho)
+    nl = rho.shape[0]
+    p = np.empty(rho.shape[1:])
+    _L().orc_ml_pressure(p.size, nl, _p(rho), _p(_f64(Gm)), rho0, _p(p))
+    return p
+
+
+def ml_init(lat, nx, ny, nz, bubbles, rho_l, rho_v, rho_gas, width, noise_amp, seed):
+    """Initial lattices (nl = 1 + bubbles, Q, nz, ny, nx): the fluid as
+    init() (liquid rho_l, its vapour rho_v inside the bubbles, noise), and
+    bubble k's gas on lattice k: rho_gas inside bubble k with the same tanh
+    profile, zero far outside it; every lattice at rest, f = w rho."""
+    b = _f64(bubbles).reshape(-1, 4)
+    f0, _ = init(lat, nx, ny, nz, b, rho_l, rho_v, width, noise_amp, seed)
+    out = [f0]
+    for k in range(len(b)):
+        fk, _ = init(lat, nx, ny, nz, b[k:k + 1], 0.0, rho_gas, width, 0.0, seed)
+        out.append(fk)
+    return np.stack(out)
+
+
+def ml_merge(f, Gm, k, l):
+    """eta_m(k, l) = 0: bubble l's lattice is merged into bubble k's (Fig. 1
+    steps 8-9, merging lattices): f_k += f_l, f_l = 0, and the pair's
+    barrier coupling is removed.  Returns new (f, Gm)."""
+    f = _f64(f).copy()
+    Gm = _f64(Gm).copy()
+    f[k] = f[k] + f[l]
+    f[l] = 0.0
+    Gm[k, l] = Gm[l, k] = 0.0
+    return f, Gm
+
+
+def ml_run_until_rupture(lat, f, tau, Gm, start, axis, length, rho_mid, eps_arm, max_steps,
+                         diag_every, pair=(1, 2), rho0=1.0, h_max=8.0):
+    """The rupture criterion on the multi-lattice model, as a plain loop:
+    advance diag_every steps, probe the film on the fluid lattice's density
+    with the coupled pressure (ml_pressure), apply criterion_step; when it
+    fires, eta_m of the pair becomes 0 and the pair's lattices merge
+    (ml_merge), and the run stops.  Returns dict(fired, merged, step, h_c,
+    h_probe, r_d, f, Gm)."""
+    state = None
+    t = 0
+    while t < max_steps:
+        f = ml_run(lat, f, diag_every, tau, Gm, rho0)
+        t += diag_every
+        rho = ml_moments(lat, f)[0]
+        p = ml_pressure(rho, Gm, rho0)
+        pr = film_probe(lat, rho[0], p, start, axis, length, rho_mid)
+        state, out = criterion_step(state, pr, eps_arm, h_max)
+        if out is not None:
+            if out["fired"]:
+                f, Gm = ml_merge(f, Gm, pair[0], pair[1])
+            return dict(step=t, f=f, Gm=Gm, **out)
+    return dict(fired=False, merged=False, step=t, h_c=0.0, h_probe=0.0, r_d=0.0, f=f, Gm=Gm)

@@ -759,3 +759,144 @@ void orc_film_midpoints(int lat, int64_t nx, int64_t ny, int64_t nz, const int32
                         int64_t *counts, int64_t cap, int64_t *rec, double *d2out) {
   film_pass(lat, nx, ny, nz, label, p, h_max, eps_arm, state, counts, cap, rec, d2out, 1);
 }
+
+/* ==== multi-lattice Shan-Chen (Sec. 3.1, Fig. 1) ============================
+ * A reading of the paper's modified model: the fluid (liquid metal) on
+ * lattice 0 and the gas of bubble k on lattice k = 1 .. nl-1 ("each bubble
+ * in its own lattice and fluid in a separate lattice", Fig. 1 steps 3-5),
+ * coupled by interaction forces ("coupling the lattices and calculating the
+ * interactions", step 6) in the multicomponent Shan-Chen form
+ *   F_s(x) = -psi_s(x) sum_t Gm[s][t] sum_i w_i psi_t(x + c_i) c_i,
+ * psi_s = rho0 (1 - exp(-rho_s/rho0)) on every lattice; Gm is the caller's
+ * coupling matrix (fluid self-attraction G, fluid-gas coupling, and the
+ * eta_m-switched barrier between different bubbles).  All lattices relax
+ * with one tau towards f_eq(rho_s, u_s) with the common velocity
+ *   u' = sum_s j_s / sum_s rho_s,   u_s = u' + tau F_s / rho_s
+ * (u_s = u' where rho_s = 0: an empty lattice has f_eq = 0 whatever u_s).
+ * The blowing agent of a site deposits w_i dm into the post-collision
+ * populations of its own lattice at the site cell (Sec. 3: gas added to
+ * each bubble).  Streaming as in orc_step, lattice by lattice.  f holds nl
+ * lattices of Q*N values: f[(s*Q + i)*N + cell]. */
+
+/* Multicomponent Shan-Chen force of every lattice from given psi fields
+ * (nl x N): F_s = -psi_s sum_t Gm[s][t] sum_i w_i psi_t(x + c_i) c_i. */
+void orc_ml_force(int lat, int64_t nx, int64_t ny, int64_t nz, int32_t nl, const double *psi,
+                  const double *Gm, double *Fx, double *Fy, double *Fz) {
+  int q = lat_q(lat);
+  int64_t N = nx * ny * nz;
+  for (int32_t s = 0; s < nl; ++s)
+    for (int64_t z = 0; z < nz; ++z)
+      for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+          int64_t k = x + nx * (y + ny * z);
+          double ax = 0, ay = 0, az = 0;
+          for (int32_t t = 0; t < nl; ++t)
+            for (int i = 1; i < q; ++i) {
+              const int *ci = lat_c(lat, i);
+              double v = Gm[s * nl + t] * lat_w(lat, i) *
+                         psi[t * N + nb(x, y, z, ci[0], ci[1], ci[2], nx, ny, nz)];
+              ax += v * ci[0];
+              ay += v * ci[1];
+              az += v * ci[2];
+            }
+          Fx[s * N + k] = -psi[s * N + k] * ax;
+          Fy[s * N + k] = -psi[s * N + k] * ay;
+          Fz[s * N + k] = -psi[s * N + k] * az;
+        }
+}
+
+/* One step.  work must hold nl * (8 + Q) * N doubles. */
+void orc_ml_step(int lat, int64_t nx, int64_t ny, int64_t nz, int32_t nl, double tau,
+                 const double *Gm /* nl x nl */, double rho0, double *f, double *work,
+                 int32_t nsites, const int64_t *site_cell, const int32_t *site_lattice,
+                 const double *rate, double *budget) {
+  int q = lat_q(lat);
+  int64_t N = nx * ny * nz;
+  double *rho = work;                                              /* nl * N */
+  double *jx = rho + nl * N, *jy = jx + nl * N, *jz = jy + nl * N; /* nl * N each */
+  double *psi = jz + nl * N;                                       /* nl * N */
+  double *Fx = psi + nl * N, *Fy = Fx + nl * N, *Fz = Fy + nl * N; /* nl * N each */
+  double *fs = Fz + nl * N;                                        /* nl * Q * N */
+
+  /* 1 moments of every lattice */
+  for (int32_t s = 0; s < nl; ++s)
+    orc_moments(lat, nx, ny, nz, f + (int64_t)s * q * N, rho + s * N, jx + s * N, jy + s * N,
+                jz + s * N);
+  /* 2 psi of every lattice at every cell */
+  for (int32_t s = 0; s < nl; ++s)
+    for (int64_t k = 0; k < N; ++k) psi[s * N + k] = psi_of(rho[s * N + k], rho0);
+  /* 3 the coupled forces */
+  orc_ml_force(lat, nx, ny, nz, nl, psi, Gm, Fx, Fy, Fz);
+  /* 4-6 common velocity, shifted velocities, BGK for every lattice */
+  for (int64_t k = 0; k < N; ++k) {
+    double rt = 0, jtx = 0, jty = 0, jtz = 0;
+    for (int32_t s = 0; s < nl; ++s) {
+      rt += rho[s * N + k];
+      jtx += jx[s * N + k];
+      jty += jy[s * N + k];
+      jtz += jz[s * N + k];
+    }
+    double upx = jtx / rt, upy = jty / rt, upz = jtz / rt;
+    for (int32_t s = 0; s < nl; ++s) {
+      double r = rho[s * N + k];
+      double ux = upx, uy = upy, uz = upz;
+      if (r != 0.0) {
+        ux += tau * Fx[s * N + k] / r;
+        uy += tau * Fy[s * N + k] / r;
+        uz += tau * Fz[s * N + k] / r;
+      }
+      for (int i = 0; i < q; ++i) {
+        int64_t o = ((int64_t)s * q + i) * N + k;
+        fs[o] = f[o] - (f[o] - feq(lat, i, r, ux, uy, uz)) / tau;
+      }
+    }
+  }
+  /* 7 blowing agent into the site's own lattice */
+  for (int32_t m = 0; m < nsites; ++m) {
+    if (budget[m] <= 0) continue;
+    double dm = rate[m] < budget[m] ? rate[m] : budget[m];
+    budget[m] -= dm;
+    for (int i = 0; i < q; ++i)
+      fs[((int64_t)site_lattice[m] * q + i) * N + site_cell[m]] += lat_w(lat, i) * dm;
+  }
+  /* 8 streaming, lattice by lattice */
+  for (int32_t s = 0; s < nl; ++s)
+    for (int64_t z = 0; z < nz; ++z)
+      for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+          int64_t k = x + nx * (y + ny * z);
+          for (int i = 0; i < q; ++i) {
+            const int *c = lat_c(lat, i);
+            f[((int64_t)s * q + i) * N + nb(x, y, z, c[0], c[1], c[2], nx, ny, nz)] =
+                fs[((int64_t)s * q + i) * N + k];
+          }
+        }
+}
+
+void orc_ml_run(int lat, int64_t nx, int64_t ny, int64_t nz, int32_t nl, double tau,
+                const double *Gm, double rho0, double *f, int64_t nsteps, int32_t nsites,
+                const int64_t *site_cell, const int32_t *site_lattice, const double *rate,
+                double *budget) {
+  int q = lat_q(lat);
+  int64_t N = nx * ny * nz;
+  double *work = (double *)malloc(sizeof(double) * (size_t)((nl * 8 + nl * q) * N));
+  for (int64_t t = 0; t < nsteps; ++t)
+    orc_ml_step(lat, nx, ny, nz, nl, tau, Gm, rho0, f, work, nsites, site_cell, site_lattice,
+                rate, budget);
+  free(work);
+}
+
+/* Pressure of the coupled lattices (the multicomponent form of the EOS of
+ * Sec. 3.1): p = cs^2 sum_s rho_s + cs^2/2 sum_s sum_t Gm[s][t] psi_s psi_t,
+ * cs^2 = 1/3.  rho: nl x N densities; p: N. */
+void orc_ml_pressure(int64_t N, int32_t nl, const double *rho, const double *Gm, double rho0,
+                     double *p) {
+  for (int64_t k = 0; k < N; ++k) {
+    double r = 0, e = 0;
+    for (int32_t s = 0; s < nl; ++s) r += rho[s * N + k];
+    for (int32_t s = 0; s < nl; ++s)
+      for (int32_t t = 0; t < nl; ++t)
+        e += Gm[s * nl + t] * psi_of(rho[s * N + k], rho0) * psi_of(rho[t * N + k], rho0);
+    p[k] = r / 3.0 + e / 6.0;
+  }
+}

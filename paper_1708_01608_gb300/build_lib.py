@@ -20,9 +20,10 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsclbm.so")
 
 SOURCES = ["capi.cu", "step_plan.cu", "step_fused_f32.cu", "step_fused_f64.cu",
-           "step_fused_h16.cu", "step_fused_x2_f32.cu", "step_fused_x2_f16.cu",
-           "step_fused_x2_bf16.cu", "step_twopass.cu", "diag.cu", "census.cu", "inject.cu", "ensemble.cu",
-           "rates.cu"]
+           "step_fused_h16.cu", "step_fused_h16r.cu", "step_fused_x2_f32.cu",
+           "step_fused_x2_f16.cu", "step_fused_x2_bf16.cu", "step_fused_x2_h16r.cu",
+           "step_twopass.cu", "diag.cu", "census.cu", "inject.cu", "ensemble.cu", "rates.cu",
+           "multilattice.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -59,6 +59,11 @@ struct lbm_ctx {
   size_t lat_bytes = 0;
   DevBuf fA, fB;
   int cur = 0;  // 0: state in fA, 1: state in fB
+  // 16-bit storage with the per-cell FP32 rounding residual (mass_residual):
+  // the step kernels run in the residual forms ST_F16R / ST_BF16R
+  bool resid = false;
+  int st_step = 0;  // storage form of the step kernels
+  DevBuf d_resid;
   bool seeded = false;
   int64_t steps = 0;
   lbm_status sticky = LBM_OK;
@@ -295,6 +300,10 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     return fail(LBM_EINVAL, "unknown kernel");
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
     return fail(LBM_EINVAL, "alloc and free callbacks must be given together");
+  if (cfg->mass_residual != 0 && cfg->mass_residual != 1)
+    return fail(LBM_EINVAL, "mass_residual must be 0 or 1");
+  if (cfg->mass_residual && cfg->storage != LBM_F16_OFFSET && cfg->storage != LBM_BF16_OFFSET)
+    return fail(LBM_EINVAL, "mass_residual applies to the 16-bit offset storages");
 
   lbm_ctx *c = new lbm_ctx();
   c->cfg = *cfg;
@@ -319,6 +328,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
   c->N = c->v.NX * c->v.NY * c->v.NZ;
   c->kernel = cfg->kernel == LBM_KERNEL_TWO_PASS ? LBM_KERNEL_TWO_PASS : LBM_KERNEL_FUSED;
   c->lat_bytes = (size_t)c->Q * c->v.px * c->v.NY * c->v.NZ * storage_bytes(c->st);
+  c->resid = cfg->mass_residual == 1;
+  c->st_step = !c->resid ? c->st : (c->st == ST_F16 ? ST_F16R : ST_BF16R);
 
   auto bail = [&](lbm_status st) {
     lbm_destroy(c);
@@ -333,6 +344,15 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
   if ((st = dalloc(c, c->fA, c->lat_bytes)) != LBM_OK) return bail(st);
   if ((st = dalloc(c, c->fB, c->lat_bytes)) != LBM_OK) return bail(st);
   if ((st = dalloc(c, c->d_err, sizeof(int))) != LBM_OK) return bail(st);
+  if (c->resid) {
+    const size_t rb = sizeof(float) * (size_t)c->v.px * c->v.NY * c->v.NZ;
+    if ((st = dalloc(c, c->d_resid, rb)) != LBM_OK) return bail(st);
+    if (cudaMemsetAsync(c->d_resid.p, 0, rb, c->s) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(LBM_ECUDA, "memset failed"));
+    }
+    c->v.resid = static_cast<const float *>(c->d_resid.p);
+  }
   if (cudaMemsetAsync(c->d_err.p, 0, sizeof(int), c->s) != cudaSuccess ||
       cudaMemsetAsync(c->fA.p, 0, c->lat_bytes, c->s) != cudaSuccess ||
       cudaMemsetAsync(c->fB.p, 0, c->lat_bytes, c->s) != cudaSuccess) {
@@ -350,7 +370,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     }
   }
   if (c->kernel == LBM_KERNEL_FUSED) {
-    cudaError_t e = fused_prepare(c->lat, c->st, c->plan);
+    cudaError_t e = fused_prepare(c->lat, c->st_step, c->plan);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return bail(fail(LBM_ECUDA, std::string("fused kernel set-up: ") + cudaGetErrorString(e)));
@@ -372,7 +392,7 @@ void lbm_destroy(lbm_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->s);
   cudaGetLastError();
-  DevBuf *bufs[] = {&c->fA,     &c->fB,     &c->d_sx,    &c->d_sy,   &c->d_sz,     &c->d_rate,
+  DevBuf *bufs[] = {&c->fA,     &c->fB,     &c->d_resid, &c->d_sx,   &c->d_sy,   &c->d_sz,     &c->d_rate,
                     &c->d_budget, &c->d_goff, &c->d_gsite, &c->d_boff, &c->d_blist, &c->d_cells, &c->d_bub,
                     &c->psi_scratch, &c->d_err, &c->d_rho, &c->d_p, &c->d_tmp, &c->d_j, &c->d_u,
                     &c->d_labels, &c->d_ncomp, &c->d_part, &c->d_tot, &c->d_site_lab,
@@ -466,6 +486,8 @@ lbm_status lbm_seed_bubbles(lbm_ctx *c, const lbm_bubble *b, int32_t n, double r
                    seed, static_cast<double *>(c->d_rho.p), c->s));
   c->cur = 0;
   CK(diag_store_from_rho(c->v, static_cast<const double *>(c->d_rho.p), lattice_ptr(c, 0), c->s));
+  if (c->resid)  // a new state has no rounding residual yet
+    CK(cudaMemsetAsync(c->d_resid.p, 0, c->d_resid.bytes, c->s));
   // site cells (view linear index) for label look-ups
   std::vector<int32_t> cells(n);
   for (int32_t k = 0; k < n; ++k)
@@ -570,6 +592,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.bucket_site = static_cast<const int32_t *>(c->d_blist.p);
   a.err = static_cast<int *>(c->d_err.p);
   a.debug_flags = c->cfg.debug_flags;
+  a.resid = static_cast<float *>(c->d_resid.p);
   a.tau_f = (float)c->cfg.tau;
   a.omega_f = (float)(1.0 / c->cfg.tau);
   a.G_f = (float)c->cfg.G;
@@ -621,9 +644,9 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps) {
     for (int i = 0; i < c->Q; ++i) a.out_pop[i] = static_cast<char *>(a.fout) + i * pop_bytes;
     cudaError_t e;
     if (c->kernel == LBM_KERNEL_FUSED)
-      e = fused_launch(c->lat, c->st, c->plan, a, c->cur == 0 ? c->tmA : c->tmB, c->s);
+      e = fused_launch(c->lat, c->st_step, c->plan, a, c->cur == 0 ? c->tmA : c->tmB, c->s);
     else
-      e = twopass_launch(c->lat, c->st, a, c->psi_scratch.p, c->s);
+      e = twopass_launch(c->lat, c->st_step, a, c->psi_scratch.p, c->s);
     if (e == cudaSuccess && spread)
       e = inject_spread(c->v, ngroups, static_cast<const int4 *>(c->d_spread_groups.p),
                         static_cast<const int32_t *>(c->d_spread_sites.p),
@@ -670,7 +693,7 @@ lbm_status lbm_plan_info(const lbm_ctx *c, int32_t out[6]) {
 // switch the fused kernel to another plan: smem attribute, descriptors and
 // the per-CTA injection buckets
 static lbm_status use_plan(lbm_ctx *c, const FusedPlan &p) {
-  CK(fused_prepare(c->lat, c->st, p));
+  CK(fused_prepare(c->lat, c->st_step, p));
   FusedMaps ma, mb;
   if (fused_encode_maps(c->lat, c->st, p, c->fA.p, c->v.NX, c->v.NY, c->v.NZ, c->v.px, &ma) !=
           CUDA_SUCCESS ||
@@ -691,9 +714,10 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best_tile, double *b
   if (!c->seeded) return fail(LBM_ESTATE, "seed the lattice first");
   CKS(set_device(c));
   CKS(check_sticky(c));
-  // save the state: current lattice, budgets, step counter
+  // save the state: current lattice (and rounding residual), budgets, step
+  // counter
   DevBuf save_f, save_b;
-  lbm_status st = dalloc(c, save_f, c->lat_bytes);
+  lbm_status st = dalloc(c, save_f, c->lat_bytes + c->d_resid.bytes);
   if (st != LBM_OK) return st;
   const size_t bbytes = sizeof(double) * (size_t)std::max(c->ninj, 1);
   if ((st = dalloc(c, save_b, bbytes)) != LBM_OK) {
@@ -704,6 +728,9 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best_tile, double *b
   const int64_t steps0 = c->steps;
   auto restore = [&]() -> lbm_status {
     CK(cudaMemcpyAsync(lattice_ptr(c, cur0), save_f.p, c->lat_bytes, cudaMemcpyDeviceToDevice, c->s));
+    if (c->resid)
+      CK(cudaMemcpyAsync(c->d_resid.p, static_cast<char *>(save_f.p) + c->lat_bytes,
+                         c->d_resid.bytes, cudaMemcpyDeviceToDevice, c->s));
     if (c->ninj > 0)
       CK(cudaMemcpyAsync(c->d_budget.p, save_b.p, sizeof(double) * c->ninj,
                          cudaMemcpyDeviceToDevice, c->s));
@@ -714,6 +741,9 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best_tile, double *b
   };
   auto body = [&]() -> lbm_status {
     CK(cudaMemcpyAsync(save_f.p, lattice_ptr(c, cur0), c->lat_bytes, cudaMemcpyDeviceToDevice, c->s));
+    if (c->resid)
+      CK(cudaMemcpyAsync(static_cast<char *>(save_f.p) + c->lat_bytes, c->d_resid.p,
+                         c->d_resid.bytes, cudaMemcpyDeviceToDevice, c->s));
     if (c->ninj > 0)
       CK(cudaMemcpyAsync(save_b.p, c->d_budget.p, sizeof(double) * c->ninj,
                          cudaMemcpyDeviceToDevice, c->s));
@@ -1433,6 +1463,8 @@ lbm_status lbm_write_f(lbm_ctx *c, const double *src, size_t bytes) {
     CK(cudaMemcpyAsync(tmp, src + (size_t)i * c->N, nd, cudaMemcpyHostToDevice, c->s));
     CK(diag_store_pop(c->v, tmp, i, lattice_ptr(c, c->cur), c->s));
   }
+  if (c->resid)  // the written populations are the whole state
+    CK(cudaMemsetAsync(c->d_resid.p, 0, c->d_resid.bytes, c->s));
   CK(cudaStreamSynchronize(c->s));
   c->seeded = true;
   c->film_state_clear = false;

@@ -52,6 +52,17 @@ template <int ST>
 __device__ __forceinline__ double load_d(const void *p, int64_t k, double wref) {
   return decode_f<ST>(static_cast<const typename Storage<ST>::T *>(p)[k], wref);
 }
+// f_i at cell (x, y, z) in double: the stored value, and for population 0 of
+// a lattice that keeps a rounding residual, that residual too (added last,
+// so a view without one gets the same bits as load_d)
+template <int ST>
+__device__ __forceinline__ double pop_d(const View &v, const void *p, int i, int x, int y, int z,
+                                        double wref) {
+  const int64_t k = sidx(i, x, y, z, v);
+  double f = load_d<ST>(p, k, wref);
+  if (i == 0 && v.resid) f = __dadd_rn(f, (double)v.resid[k]);
+  return f;
+}
 template <int ST>
 __device__ __forceinline__ void store_d(void *p, int64_t k, double v, double wref) {
   static_cast<typename Storage<ST>::T *>(p)[k] = encode_f<ST>(v, wref);
@@ -210,7 +221,7 @@ __global__ void k_gather_f(const View v, const void *stored, double *f) {
     const Idx c = idx_of(k, v);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      f[(int64_t)i * N + k] = load_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), L::w(i) * v.rho_ref);
+      f[(int64_t)i * N + k] = pop_d<ST>(v, stored, i, c.x, c.y, c.z, L::w(i) * v.rho_ref);
   }
 }
 
@@ -231,7 +242,7 @@ __global__ void k_gather_pop(const View v, const void *stored, int i, double *ou
   const int64_t N = v.NX * v.NY * v.NZ;
   GRID_LOOP(k, N) {
     const Idx c = idx_of(k, v);
-    out[k] = load_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), w * v.rho_ref);
+    out[k] = pop_d<ST>(v, stored, i, c.x, c.y, c.z, w * v.rho_ref);
   }
 }
 
@@ -264,7 +275,7 @@ __device__ __forceinline__ void cell_moments(const View &v, const void *stored, 
   rho = jx = jy = jz = 0.0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const double f = load_d<ST>(stored, sidx(i, c.x, c.y, c.z, v), L::w(i) * v.rho_ref);
+    const double f = pop_d<ST>(v, stored, i, c.x, c.y, c.z, L::w(i) * v.rho_ref);
     rho += f;
     jx += L::cx(i) * f;
     jy += L::cy(i) * f;
@@ -278,7 +289,7 @@ __device__ __forceinline__ double cell_rho(const View &v, const void *stored, in
   using L = Lattice<LAT>;
   double rho = 0.0;
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) rho += load_d<ST>(stored, sidx(i, x, y, z, v), L::w(i) * v.rho_ref);
+  for (int i = 0; i < L::Q; ++i) rho += pop_d<ST>(v, stored, i, x, y, z, L::w(i) * v.rho_ref);
   return rho;
 }
 
@@ -480,6 +491,12 @@ __global__ void __launch_bounds__(TPB) k_scan(const View v, const void *stored, 
       if (L::cy(i) != 0) two_sum(hi[2], lo[2], L::cy(i) > 0 ? g[i] : -g[i]);
       if (L::cz(i) != 0) two_sum(hi[3], lo[3], L::cz(i) > 0 ? g[i] : -g[i]);
     }
+    // a lattice with a rounding residual: it is part of the rest population
+    const float res = v.resid ? v.resid[o] : 0.0f;
+    if (v.resid) {
+      cell += res;
+      two_sum(hi[0], lo[0], res);
+    }
     if (!isfinite(cell)) bad = true;
     if (labels) {
       const float r32 = rho_ref + cell;
@@ -490,6 +507,7 @@ __global__ void __launch_bounds__(TPB) k_scan(const View v, const void *stored, 
         double r64 = 0;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) r64 += __dadd_rn(__dmul_rn(L::w(i), v.rho_ref), (double)g[i]);
+        if (v.resid) r64 = __dadd_rn(r64, (double)res);
         gas = r64 < thr;
       }
       labels[k] = gas ? (int32_t)k : -1;

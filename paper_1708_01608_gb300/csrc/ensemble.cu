@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(BX)
   m.site_x = m.site_y = m.site_z = m.bucket_site = nullptr;
   m.rate = nullptr;
   m.budget = nullptr;
+  m.resid = nullptr;
   m.err = nullptr;
   m.debug_flags = 0;
   float *out = parity ? D.latA : D.latB;

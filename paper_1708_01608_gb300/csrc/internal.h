@@ -41,6 +41,10 @@ struct StepArgs {
   const int32_t *bucket_site;
   int *err;  // device status word (ERR_* bits)
   int debug_flags;  // LBM_DEBUG_* bits of the configuration
+  // 16-bit storage with the rounding residual (kernel forms ST_F16R /
+  // ST_BF16R): one FP32 per cell, indexed like population 0 (row pitch px);
+  // NULL otherwise
+  float *resid;
 };
 
 // TMA descriptors of one population lattice for the fused kernel: the
@@ -106,6 +110,13 @@ cudaError_t fused_x2_launch_f16(int lat, const FusedPlan &, const StepArgs &, co
 cudaError_t fused_x2_launch_bf16(int lat, const FusedPlan &, const StepArgs &,
                                  const FusedMaps &, cudaStream_t);
 cudaError_t fused_x2_prepare_f32(int lat, const FusedPlan &, int *blocks_per_sm);
+// the same kernels for the residual forms ST_F16R / ST_BF16R
+cudaError_t fused_launch_h16r(int lat, int st, const FusedPlan &, const StepArgs &,
+                              const FusedMaps &, cudaStream_t);
+cudaError_t fused_prepare_h16r(int lat, int st, const FusedPlan &, int *blocks_per_sm);
+cudaError_t fused_x2_launch_h16r(int lat, int st, const FusedPlan &, const StepArgs &,
+                                 const FusedMaps &, cudaStream_t);
+cudaError_t fused_x2_prepare_h16r(int lat, int st, const FusedPlan &, int *blocks_per_sm);
 cudaError_t fused_x2_prepare_f16(int lat, const FusedPlan &, int *blocks_per_sm);
 cudaError_t fused_x2_prepare_bf16(int lat, const FusedPlan &, int *blocks_per_sm);
 int fused_x2_smem_f32(int lat, int tile);
@@ -140,6 +151,9 @@ struct View {
   int64_t NX, NY, NZ, px;
   double rho_ref;
   FastDiv fx, fy;  // division by NX and by NY (view_prepare)
+  // per-cell FP32 rounding residual of the 16-bit storages (NULL: none):
+  // part of population 0's value, indexed like it
+  const float *resid = nullptr;
 };
 inline void view_prepare(View &v) {
   v.fx = make_fastdiv((uint32_t)v.NX);

@@ -22,6 +22,12 @@ namespace sclbm {
 
 enum { D2Q9 = 0, D3Q19 = 1 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+// Step-kernel forms of the 16-bit storages that also keep a per-cell FP32
+// rounding residual (the mass the stores' rounding took off the cell in the
+// last step, returned into its next collision): the same populations and
+// codec as ST_F16 / ST_BF16.  Diagnostics use the base form and read the
+// residual field through their View.
+enum { ST_F16R = 4, ST_BF16R = 5 };
 
 template <int LAT>
 struct Lattice;
@@ -92,7 +98,7 @@ template <>
 struct Storage<ST_F64> {
   using T = double;
   using C = double;
-  static constexpr bool OFFSET = false;
+  static constexpr bool OFFSET = false, RESID = false;
   __device__ static C load(T v) { return v; }
   __device__ static T store(C v) { return v; }
 };
@@ -100,7 +106,7 @@ template <>
 struct Storage<ST_F32> {
   using T = float;
   using C = float;
-  static constexpr bool OFFSET = true;
+  static constexpr bool OFFSET = true, RESID = false;
   __device__ static C load(T v) { return v; }
   __device__ static T store(C v) { return v; }
 };
@@ -108,7 +114,7 @@ template <>
 struct Storage<ST_F16> {
   using T = __half;
   using C = float;
-  static constexpr bool OFFSET = true;
+  static constexpr bool OFFSET = true, RESID = false;
   __device__ static C load(T v) { return __half2float(v); }
   __device__ static T store(C v) { return __float2half_rn(v); }
 };
@@ -116,9 +122,17 @@ template <>
 struct Storage<ST_BF16> {
   using T = __nv_bfloat16;
   using C = float;
-  static constexpr bool OFFSET = true;
+  static constexpr bool OFFSET = true, RESID = false;
   __device__ static C load(T v) { return __bfloat162float(v); }
   __device__ static T store(C v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct Storage<ST_F16R> : Storage<ST_F16> {
+  static constexpr bool RESID = true;
+};
+template <>
+struct Storage<ST_BF16R> : Storage<ST_BF16> {
+  static constexpr bool RESID = true;
 };
 
 // f_i from a stored value and back, in double (diagnostics, state I/O)

@@ -87,6 +87,7 @@ struct MarchArgs {
   double *budget;
   int *err;
   int debug_flags;
+  float *resid;  // rounding residual per cell (16-bit residual forms), else NULL
 };
 
 // Once per CTA, before its first march: the NS stage barriers and the
@@ -129,6 +130,9 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
   using C = typename K::C;
   constexpr int Q = K::Q, HY = K::HY, HX = K::HX, PW = K::PW, PH = K::PH, NT = K::NT;
   constexpr bool F64 = sizeof(C) == 8;
+  // 16-bit residual forms: the cell's rounding residual of the last step
+  // joins its mass R, and the new one is what this step's stores round off
+  constexpr bool RESID = S::RESID;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
@@ -424,8 +428,13 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
           // folded into the per-weight constants:
           //   g_i* = (1 - omega) g_i + omega w_i (K + 4.5 rho (c.u)^2) + omega 3 w_i rho c.u.
           // The rest population takes R minus the moving ones, so mass is
-          // conserved to rounding.
-          const C R = Rcur;
+          // conserved to rounding.  The residual forms add the cell's
+          // rounding residual of the last step to R and keep what this
+          // step's 16-bit stores round off (deposit included) as the next
+          // one, so stored mass plus residual is conserved to FP32 rounding.
+          const int32_t own = oz[1] + oy[1] + ox[1];
+          C R = Rcur;
+          if constexpr (RESID) R += m.resid[own];
           // -0 is the additive identity, so the first term is no addition
           C jx = -0.0f, jy = -0.0f, jz = -0.0f, sx = -0.0f, sy = -0.0f, sz = -0.0f;
           static_for<L::NP>([&](auto kc) {
@@ -451,6 +460,12 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
           // relax and push; SITE adds the blowing agent w_i dm to every
           // population of the cell (a separate copy of the loop, run only
           // by the site cell's warp)
+          C racc = 0;
+          auto put = [&](T *p, C v) {
+            const T q = S::store(v);
+            *p = q;
+            if constexpr (RESID) racc += v - S::load(q);
+          };
           auto relax_push = [&](auto with_site) {
             constexpr bool SITE = decltype(with_site)::value;
             float2 moved2;
@@ -466,20 +481,21 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
               moved2 = k2 == 0 ? g : __fadd2_rn(moved2, g);
               const C gi = g.x, go = g.y;
               if (SITE) {
-                *dst(i) = S::store(gi + (C)L::w(i) * dmc);
-                *dst(o) = S::store(go + (C)L::w(o) * dmc);
+                put(dst(i), gi + (C)L::w(i) * dmc);
+                put(dst(o), go + (C)L::w(o) * dmc);
               } else {
-                *dst(i) = S::store(gi);
-                *dst(o) = S::store(go);
+                put(dst(i), gi);
+                put(dst(o), go);
               }
             });
             const C g0 = R - (moved2.x + moved2.y);
-            *dst(0) = S::store(SITE ? g0 + (C)L::w(0) * dmc : g0);
+            put(dst(0), SITE ? g0 + (C)L::w(0) * dmc : g0);
           };
           if (site)
             relax_push(std::true_type{});
           else
             relax_push(std::false_type{});
+          if constexpr (RESID) m.resid[own] = racc;
         }
       }
     }
@@ -532,6 +548,7 @@ __device__ __forceinline__ MarchArgs march_args_of(const FusedMaps &tm, const St
   m.bucket_site = a.bucket_site;
   m.rate = a.rate;
   m.budget = a.budget;
+  m.resid = a.resid;
   m.err = a.err;
   m.debug_flags = a.debug_flags;
   return m;

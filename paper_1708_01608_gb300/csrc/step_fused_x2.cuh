@@ -87,6 +87,10 @@ struct Storage2<ST_BF16> {
   __device__ static float2 load(T2 v) { return __bfloat1622float2(v); }
   __device__ static T2 store(float2 v) { return __float22bfloat162_rn(v); }
 };
+template <>
+struct Storage2<ST_F16R> : Storage2<ST_F16> {};
+template <>
+struct Storage2<ST_BF16R> : Storage2<ST_BF16> {};
 
 // Sum of the Q staged values of one cell (or of a pair of cells), in one
 // fixed order for the scalar and the paired form: the same cell gets the
@@ -140,6 +144,9 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
   constexpr int Q = K::Q, HY = K::HY, HX = K::HX, PW = K::PW, PH = K::PH, RP = K::RP,
                 TPX = K::TPX;
   (void)PH;
+  // 16-bit residual forms: each cell's rounding residual of the last step
+  // joins its mass R, and the new one is what this step's stores round off
+  constexpr bool RESID = S1::RESID;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
@@ -361,24 +368,35 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
           const float *r = (cx == 0 ? ringN : ringS) + pl * RP;
           return *reinterpret_cast<const float2 *>(r + c0 + cy * PW + (cx < 0 ? -2 : 0));
         };
-        // push of velocity i for cells a and b
+        // push of velocity i for cells a and b; the residual forms sum what
+        // the 16-bit stores round off, per cell
+        float2 racc = f2(0.0f);
         auto put = [&](auto ic, float2 v) {
           constexpr int i = decltype(ic)::value;
           constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
           T *p = out_pop(i) + (oz[cz + 1] + oy[cy + 1] + x);
           if constexpr (cx == 0) {
-            *reinterpret_cast<T2 *>(p) = S2::store(v);
-          } else if constexpr (cx > 0) {
-            p[1] = S1::store(v.x);
-            p[dbp] = S1::store(v.y);
+            const T2 q = S2::store(v);
+            *reinterpret_cast<T2 *>(p) = q;
+            if constexpr (RESID) racc = add2(racc, sub2(v, S2::load(q)));
           } else {
-            p[dam] = S1::store(v.x);
-            p[0] = S1::store(v.y);
+            const T qa = S1::store(v.x), qb = S1::store(v.y);
+            if constexpr (cx > 0) {
+              p[1] = qa;
+              p[dbp] = qb;
+            } else {
+              p[dam] = qa;
+              p[0] = qb;
+            }
+            if constexpr (RESID)
+              racc = add2(racc, make_float2(v.x - S1::load(qa), v.y - S1::load(qb)));
           }
         };
 
         // moments and the Shan-Chen force sum, opposite velocities in pairs
-        const float2 R = Rcur;
+        const int32_t own = oz[1] + oy[1] + x;  // cell a; b is own + 1
+        float2 R = Rcur;
+        if constexpr (RESID) R = add2(R, *reinterpret_cast<const float2 *>(m.resid + own));
         float2 jx = f2(-0.0f), jy = f2(-0.0f), jz = f2(-0.0f);
         float2 sx = f2(-0.0f), sy = f2(-0.0f), sz = f2(-0.0f);
         static_for<L::NP>([&](auto kc) {
@@ -437,6 +455,7 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
           relax_push(std::true_type{});
         else
           relax_push(std::false_type{});
+        if constexpr (RESID) *reinterpret_cast<float2 *>(m.resid + own) = racc;
       }
     }
     // ---- populations of plane P into registers for the next collision

@@ -162,6 +162,8 @@ cudaError_t fused_launch(int lat, int st, const FusedPlan &p, const StepArgs &a,
       case ST_F32: return fused_x2_launch_f32(lat, p, a, tm, s);
       case ST_F16: return fused_x2_launch_f16(lat, p, a, tm, s);
       case ST_BF16: return fused_x2_launch_bf16(lat, p, a, tm, s);
+      case ST_F16R:
+      case ST_BF16R: return fused_x2_launch_h16r(lat, st, p, a, tm, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -170,6 +172,9 @@ cudaError_t fused_launch(int lat, int st, const FusedPlan &p, const StepArgs &a,
       return fused_launch_f64(lat, p, a, tm, s);
     case ST_F32:
       return fused_launch_f32(lat, p, a, tm, s);
+    case ST_F16R:
+    case ST_BF16R:
+      return fused_launch_h16r(lat, st, p, a, tm, s);
     default:
       return fused_launch_h16(lat, st, p, a, tm, s);
   }
@@ -181,6 +186,8 @@ cudaError_t fused_prepare(int lat, int st, const FusedPlan &p, int *blocks_per_s
       case ST_F32: return fused_x2_prepare_f32(lat, p, blocks_per_sm);
       case ST_F16: return fused_x2_prepare_f16(lat, p, blocks_per_sm);
       case ST_BF16: return fused_x2_prepare_bf16(lat, p, blocks_per_sm);
+      case ST_F16R:
+      case ST_BF16R: return fused_x2_prepare_h16r(lat, st, p, blocks_per_sm);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -189,6 +196,9 @@ cudaError_t fused_prepare(int lat, int st, const FusedPlan &p, int *blocks_per_s
       return fused_prepare_f64(lat, p, blocks_per_sm);
     case ST_F32:
       return fused_prepare_f32(lat, p, blocks_per_sm);
+    case ST_F16R:
+    case ST_BF16R:
+      return fused_prepare_h16r(lat, st, p, blocks_per_sm);
     default:
       return fused_prepare_h16(lat, st, p, blocks_per_sm);
   }

@@ -54,8 +54,15 @@ __global__ void tp_psi_kernel(const StepArgs a, typename Storage<ST>::C *psi) {
     const Cell c = cell_of(k, a.NX, a.NY);
     const int64_t o = (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
     C rho = 0;
+    if constexpr (S::OFFSET) {  // rho_ref + the sum of the offsets, as the collision has it
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) rho += dec<ST>(f[i * pop + o], (C)(L::w(i) * a.rho_ref));
+      for (int i = 0; i < L::Q; ++i) rho += S::load(f[i * pop + o]);
+      if constexpr (S::RESID) rho += a.resid[o];
+      rho += (C)a.rho_ref;
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) rho += dec<ST>(f[i * pop + o], (C)(L::w(i) * a.rho_ref));
+    }
     psi[k] = psi_of(rho, rho0, inv_rho0);
   }
 }
@@ -75,17 +82,7 @@ __global__ void tp_collide_kernel(const StepArgs a, const typename Storage<ST>::
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = cell_of(k, a.NX, a.NY);
-    C fi[L::Q];
-    C rho = 0, jx = 0, jy = 0, jz = 0;
     const int64_t own = (int64_t)c.z * plane + (int64_t)c.y * a.px + c.x;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      fi[i] = dec<ST>(f[i * pop + own], (C)(L::w(i) * a.rho_ref));
-      rho += fi[i];
-      jx += (C)L::cx(i) * fi[i];
-      jy += (C)L::cy(i) * fi[i];
-      jz += (C)L::cz(i) * fi[i];
-    }
     C sx = 0, sy = 0, sz = 0;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
@@ -97,32 +94,74 @@ __global__ void tp_collide_kernel(const StepArgs a, const typename Storage<ST>::
       sz += (C)L::cz(i) * wp;
     }
     const C gp = -G * psi[k];
-    C ux, uy, uz;
-    if (sizeof(C) == 8) {  // FP64 keeps the oracle's operation order
-      ux = (jx + tau * gp * sx) / rho;
-      uy = (jy + tau * gp * sy) / rho;
-      uz = (jz + tau * gp * sz) / rho;
-    } else {
-      const C ir = (C)1 / rho;
-      ux = (jx + tau * gp * sx) * ir;
-      uy = (jy + tau * gp * sy) * ir;
-      uz = (jz + tau * gp * sz) * ir;
-    }
-    const C uu = (C)1.5 * (ux * ux + uy * uy + uz * uz);
-    constexpr int i0 = sizeof(C) == 8 ? 0 : 1;
-    C moved = 0;  // FP32: rest population = rho - moving ones (mass to rounding)
+    if constexpr (sizeof(C) == 8) {
+      // FP64: the oracle's operation order on the populations themselves
+      C fi[L::Q];
+      C rho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-    for (int i = i0; i < L::Q; ++i) {
-      const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
-      const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
-      const C fs = sizeof(C) == 8 ? fi[i] - (fi[i] - feq) / tau : fi[i] - omega * (fi[i] - feq);
-      moved += fs;
-      const int X = wrapi(c.x + L::cx(i), NX), Y = wrapi(c.y + L::cy(i), NY),
-                Z = wrapi(c.z + L::cz(i), NZ);
-      g[i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X] =
-          enc<ST>(fs, (C)(L::w(i) * a.rho_ref));
+      for (int i = 0; i < L::Q; ++i) {
+        fi[i] = dec<ST>(f[i * pop + own], (C)(L::w(i) * a.rho_ref));
+        rho += fi[i];
+        jx += (C)L::cx(i) * fi[i];
+        jy += (C)L::cy(i) * fi[i];
+        jz += (C)L::cz(i) * fi[i];
+      }
+      const C ux = (jx + tau * gp * sx) / rho, uy = (jy + tau * gp * sy) / rho,
+              uz = (jz + tau * gp * sz) / rho;
+      const C uu = (C)1.5 * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
+        const C feq = (C)L::w(i) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - uu);
+        const int X = wrapi(c.x + L::cx(i), NX), Y = wrapi(c.y + L::cy(i), NY),
+                  Z = wrapi(c.z + L::cz(i), NZ);
+        g[i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X] =
+            enc<ST>(fi[i] - (fi[i] - feq) / tau, (C)(L::w(i) * a.rho_ref));
+      }
+    } else {
+      // FP32 on the offsets g_i = f_i - w_i rho_ref (rho = rho_ref + R with
+      // R = sum g_i; rho_ref = 0 gives the plain populations): the
+      // equilibrium offset is w_i (K + rho (3 c.u + 4.5 (c.u)^2)) with
+      // K = R - 1.5 rho u.u, and the rest population takes R minus the
+      // moving ones, so mass is conserved to FP32 rounding of the offsets
+      C gi[L::Q];
+      C R = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        gi[i] = S::load(f[i * pop + own]);
+        R += gi[i];
+        jx += (C)L::cx(i) * gi[i];
+        jy += (C)L::cy(i) * gi[i];
+        jz += (C)L::cz(i) * gi[i];
+      }
+      // residual forms: the cell's rounding residual of the last step is part
+      // of its mass (it enters the rest population below)
+      if constexpr (S::RESID) R += a.resid[own];
+      const C rho = (C)a.rho_ref + R;
+      const C ir = (C)1 / rho;
+      const C ux = (jx + tau * gp * sx) * ir, uy = (jy + tau * gp * sy) * ir,
+              uz = (jz + tau * gp * sz) * ir;
+      const C K = R - (C)1.5 * rho * (ux * ux + uy * uy + uz * uz);
+      C moved = 0;
+      C racc = 0;  // residual forms: what this cell's stores round off
+      auto put = [&](int64_t o, C off) {
+        const T q = S::store(off);
+        g[o] = q;
+        if constexpr (S::RESID) racc += off - S::load(q);
+      };
+#pragma unroll
+      for (int i = 1; i < L::Q; ++i) {
+        const C cu = (C)L::cx(i) * ux + (C)L::cy(i) * uy + (C)L::cz(i) * uz;
+        const C feq = (C)L::w(i) * (K + rho * ((C)3 * cu + (C)4.5 * cu * cu));
+        const C gs = gi[i] - omega * (gi[i] - feq);
+        moved += gs;
+        const int X = wrapi(c.x + L::cx(i), NX), Y = wrapi(c.y + L::cy(i), NY),
+                  Z = wrapi(c.z + L::cz(i), NZ);
+        put(i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X, gs);
+      }
+      put(own, R - moved);
+      if constexpr (S::RESID) a.resid[own] = racc;
     }
-    if (sizeof(C) == 4) g[own] = enc<ST>(rho - moved, (C)(L::w(0) * a.rho_ref));
   }
 }
 
@@ -155,9 +194,19 @@ __global__ void tp_inject_kernel(const StepArgs a) {
     const int X = wrapi(a.site_x[s0] + L::cx(i), (int)a.NX),
               Y = wrapi(a.site_y[s0] + L::cy(i), (int)a.NY),
               Z = wrapi(a.site_z[s0] + L::cz(i), (int)a.NZ);
-    T *o = g + i * pop + (int64_t)Z * plane + (int64_t)Y * a.px + X;
+    const int64_t cell = (int64_t)Z * plane + (int64_t)Y * a.px + X;
+    T *o = g + i * pop + cell;
     const C wref = (C)(L::w(i) * a.rho_ref);
-    *o = enc<ST>(dec<ST>(*o, wref) + (C)(L::w(i) * dm), wref);
+    if constexpr (S::RESID) {
+      // the deposit on the offset itself; its rounding goes to the receiving
+      // cell's residual (atomic: neighbouring sites can push into one cell)
+      const C off = S::load(*o) + (C)(L::w(i) * dm);
+      const T q = S::store(off);
+      *o = q;
+      atomicAdd(a.resid + cell, off - S::load(q));
+    } else {
+      *o = enc<ST>(dec<ST>(*o, wref) + (C)(L::w(i) * dm), wref);
+    }
   }
 }
 
@@ -180,6 +229,8 @@ cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi, cudaSt
       case ST_F64: return tp_launch_t<D3Q19, ST_F64>(a, psi, s);
       case ST_F32: return tp_launch_t<D3Q19, ST_F32>(a, psi, s);
       case ST_F16: return tp_launch_t<D3Q19, ST_F16>(a, psi, s);
+      case ST_F16R: return tp_launch_t<D3Q19, ST_F16R>(a, psi, s);
+      case ST_BF16R: return tp_launch_t<D3Q19, ST_BF16R>(a, psi, s);
       default: return tp_launch_t<D3Q19, ST_BF16>(a, psi, s);
     }
   }
@@ -187,6 +238,8 @@ cudaError_t twopass_launch(int lat, int st, const StepArgs &a, void *psi, cudaSt
     case ST_F64: return tp_launch_t<D2Q9, ST_F64>(a, psi, s);
     case ST_F32: return tp_launch_t<D2Q9, ST_F32>(a, psi, s);
     case ST_F16: return tp_launch_t<D2Q9, ST_F16>(a, psi, s);
+    case ST_F16R: return tp_launch_t<D2Q9, ST_F16R>(a, psi, s);
+    case ST_BF16R: return tp_launch_t<D2Q9, ST_BF16R>(a, psi, s);
     default: return tp_launch_t<D2Q9, ST_BF16>(a, psi, s);
   }
 }

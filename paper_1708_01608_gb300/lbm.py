@@ -49,6 +49,7 @@ class Config(C.Structure):
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
         ("debug_flags", C.c_int32), ("nucleus_radius", C.c_double),
+        ("mass_residual", C.c_int32),
     ]
 
 
@@ -92,6 +93,14 @@ class Domain(C.Structure):
                 ("rho_g", C.c_double), ("width", C.c_double), ("noise_amp", C.c_double),
                 ("seed", C.c_uint64), ("nbubbles", C.c_int32), ("bubbles", Bubble * 4),
                 ("line", C.c_int64 * 5), ("rho_mid", C.c_double)]
+
+
+class MLConfig(C.Structure):
+    _fields_ = [("lattice", C.c_int32), ("storage", C.c_int32), ("nx", C.c_int64),
+                ("ny", C.c_int64), ("nz", C.c_int64), ("nl", C.c_int32), ("tau", C.c_double),
+                ("rho0", C.c_double), ("G", C.c_double), ("G_x", C.c_double),
+                ("G_b", C.c_double), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
 class LBMError(RuntimeError):
@@ -145,6 +154,21 @@ def _load():
         "lbm_ensemble_stats": (i32, [P_, P_]),
         "lbm_ensemble_read_f": (i32, [P_, i32, P_, sz]),
         "lbm_fp64_rate": (i32, [i32, C.POINTER(d)]),
+        "lbm_ml_config_default": (None, [C.POINTER(MLConfig)]),
+        "lbm_ml_create": (i32, [C.POINTER(MLConfig), C.POINTER(P_)]),
+        "lbm_ml_destroy": (None, [P_]),
+        "lbm_ml_coupling": (i32, [P_, P_]),
+        "lbm_ml_seed": (i32, [P_, P_, d, d, d, d, d, u64]),
+        "lbm_ml_write_f": (i32, [P_, P_, sz]),
+        "lbm_ml_read_f": (i32, [P_, P_, sz]),
+        "lbm_ml_inject": (i32, [P_, P_, P_, i32]),
+        "lbm_ml_read_budgets": (i32, [P_, P_, i32]),
+        "lbm_ml_step": (i32, [P_, i64]),
+        "lbm_ml_step_count": (i64, [P_]),
+        "lbm_ml_merge": (i32, [P_, i32, i32]),
+        "lbm_ml_fields": (i32, [P_, P_, P_]),
+        "lbm_ml_run_until_rupture": (i32, [P_, P_, d, d, d, i64, i64, i32, i32,
+                                           C.POINTER(Rupture)]),
         "lbm_last_error": (C.c_char_p, []),
         "lbm_version": (C.c_char_p, []),
     }
@@ -167,7 +191,10 @@ EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites"
            "lbm_site_labels", "lbm_bubble_sizes", "lbm_film_cells", "lbm_film_pairs",
            "lbm_diagnostic_interval",
            "lbm_totals", "lbm_read", "lbm_write_f", "lbm_step_static_f32", "lbm_fp64_rate",
-           "lbm_last_error",
+           "lbm_last_error", "lbm_ml_config_default", "lbm_ml_create", "lbm_ml_destroy",
+           "lbm_ml_coupling", "lbm_ml_seed", "lbm_ml_write_f", "lbm_ml_read_f", "lbm_ml_inject",
+           "lbm_ml_read_budgets", "lbm_ml_step", "lbm_ml_step_count", "lbm_ml_merge",
+           "lbm_ml_fields", "lbm_ml_run_until_rupture",
            "lbm_version", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_run",
            "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f")
 
@@ -229,7 +256,7 @@ class Lattice:
     def __init__(self, lattice="D3Q19", nx=64, ny=64, nz=1, tau=1.0, G=-5.0, rho0=1.0,
                  storage="f32", rho_ref=1.0, gas_threshold=1.0, kernel="auto", tile=0,
                  stream: Optional[int] = None, torch_memory: bool = True, debug_flags: int = 0,
-                 nucleus_radius: float = 3.0):
+                 nucleus_radius: float = 3.0, mass_residual: bool = False):
         cfg = Config()
         _lib.lbm_config_default(C.byref(cfg))
         cfg.lattice = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
@@ -241,6 +268,7 @@ class Lattice:
         cfg.tile = int(tile)
         cfg.debug_flags = int(debug_flags)
         cfg.nucleus_radius = float(nucleus_radius)
+        cfg.mass_residual = 1 if mass_residual else 0
         self._mem = None
         if torch_memory:
             try:
@@ -514,6 +542,110 @@ def fp64_rate(iters=20000):
     out = C.c_double(0)
     _check(_lib.lbm_fp64_rate(int(iters), C.byref(out)))
     return float(out.value)
+
+
+class MultiLattice:
+    """The multi-lattice Shan-Chen model (lbm_ml_* in include/lbm.h): the
+    fluid on lattice 0 and the gas of bubble k on lattice k, coupled by the
+    multicomponent force with the eta_m-switched barrier between bubbles."""
+
+    def __init__(self, lattice="D2Q9", nx=128, ny=128, nz=1, nl=3, tau=1.0, rho0=1.0, G=-5.0,
+                 G_x=1.0, G_b=0.0, storage="f64", torch_memory=True):
+        cfg = MLConfig()
+        _lib.lbm_ml_config_default(C.byref(cfg))
+        cfg.lattice = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
+        cfg.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        cfg.nx, cfg.ny, cfg.nz, cfg.nl = int(nx), int(ny), int(nz), int(nl)
+        cfg.tau, cfg.rho0, cfg.G, cfg.G_x, cfg.G_b = (float(tau), float(rho0), float(G),
+                                                      float(G_x), float(G_b))
+        self._mem = None
+        if torch_memory:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    self._mem = _TorchMemory()
+                    cfg.alloc, cfg.free = self._mem.alloc, self._mem.free
+                    cfg.stream = torch.cuda.current_stream().cuda_stream or None
+            except ImportError:
+                pass
+        self.q = 9 if cfg.lattice == D2Q9 else 19
+        self.nl = cfg.nl
+        self.shape = (cfg.nz, cfg.ny, cfg.nx)
+        self.n = cfg.nx * cfg.ny * cfg.nz
+        h = C.c_void_p()
+        _check(_lib.lbm_ml_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lbm_ml_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coupling(self):
+        out = np.zeros((self.nl, self.nl))
+        _check(_lib.lbm_ml_coupling(self._h, _ptr(out)))
+        return out
+
+    def seed(self, bubbles, rho_l, rho_v, rho_gas, width=2.0, noise_amp=0.0, seed=0):
+        b = np.ascontiguousarray(bubbles, dtype=np.float64).reshape(-1, 4)
+        assert len(b) == self.nl - 1
+        _check(_lib.lbm_ml_seed(self._h, _ptr(b) if len(b) else None, rho_l, rho_v, rho_gas,
+                                width, noise_amp, seed & (2**64 - 1)))
+
+    def write_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.nl * self.q * self.n
+        _check(_lib.lbm_ml_write_f(self._h, _ptr(f), f.nbytes))
+
+    def read_f(self):
+        out = np.empty((self.nl, self.q) + self.shape)
+        _check(_lib.lbm_ml_read_f(self._h, _ptr(out), out.nbytes))
+        return out
+
+    def inject(self, rate, budget):
+        r = np.ascontiguousarray(rate, dtype=np.float64).reshape(-1)
+        b = np.ascontiguousarray(budget, dtype=np.float64).reshape(-1)
+        _check(_lib.lbm_ml_inject(self._h, _ptr(r) if len(r) else None,
+                                  _ptr(b) if len(b) else None, len(r)))
+        self._ninj = len(r)
+
+    def read_budgets(self):
+        out = np.empty(getattr(self, "_ninj", 0))
+        _check(_lib.lbm_ml_read_budgets(self._h, _ptr(out), len(out)))
+        return out
+
+    def step(self, n=1):
+        _check(_lib.lbm_ml_step(self._h, int(n)))
+
+    @property
+    def steps(self):
+        return int(_lib.lbm_ml_step_count(self._h))
+
+    def merge(self, k, l):
+        _check(_lib.lbm_ml_merge(self._h, int(k), int(l)))
+
+    def fields(self):
+        """(rho of every lattice (nl, nz, ny, nx), coupled pressure (nz, ny, nx))."""
+        rho = np.empty((self.nl,) + self.shape)
+        p = np.empty(self.shape)
+        _check(_lib.lbm_ml_fields(self._h, _ptr(rho), _ptr(p)))
+        return rho, p
+
+    def run_until_rupture(self, line, rho_mid, eps_arm, diag_every, max_steps, h_max=8.0,
+                          pair=(1, 2)):
+        ln = np.ascontiguousarray(line, dtype=np.int64)
+        out = Rupture()
+        _check(_lib.lbm_ml_run_until_rupture(self._h, _ptr(ln), float(rho_mid), float(eps_arm),
+                                             float(h_max), int(diag_every), int(max_steps),
+                                             int(pair[0]), int(pair[1]), C.byref(out)))
+        return dict(fired=bool(out.fired), merged=bool(out.merged), steps=int(out.steps),
+                    h_c=out.h_c, h_probe=out.h_probe, r_d=out.r_d)
 
 
 class Ensemble:

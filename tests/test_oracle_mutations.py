@@ -54,6 +54,19 @@ MUTATIONS = [
     ("s += p[nb(x, y, z, e[0], e[1], e[2], nx, ny, nz)] - 2.0 * p[k] +",
      "s += p[nb(x, y, z, e[0], e[0], e[2], nx, ny, nz)] - 2.0 * p[k] +"),
     ("for (int sg = -1; sg <= 1; sg += 2) {", "for (int sg = 1; sg <= 1; sg += 2) {"),
+    # multi-lattice model (Sec. 3.1, Fig. 1): the coupling matrix transposed,
+    # the common velocity of one lattice only, the shifted velocity without
+    # tau, the gas injected into the fluid, the coupled pressure's matrix
+    # entry, the streaming of the bubble lattices
+    ("double v = Gm[s * nl + t] * lat_w(lat, i) *", "double v = Gm[t * nl + s] * lat_w(lat, i) *"),
+    ("      rt += rho[s * N + k];\n", "      rt = rho[s * N + k];\n"),
+    ("        ux += tau * Fx[s * N + k] / r;", "        ux += Fx[s * N + k] / r;"),
+    ("      fs[((int64_t)site_lattice[m] * q + i) * N + site_cell[m]] += lat_w(lat, i) * dm;",
+     "      fs[((int64_t)i) * N + site_cell[m]] += lat_w(lat, i) * dm;"),
+    ("        e += Gm[s * nl + t] * psi_of(rho[s * N + k], rho0) * psi_of(rho[t * N + k], rho0);",
+     "        e += Gm[s * nl + s] * psi_of(rho[s * N + k], rho0) * psi_of(rho[t * N + k], rho0);"),
+    ("            f[((int64_t)s * q + i) * N + nb(x, y, z, c[0], c[1], c[2], nx, ny, nz)] =",
+     "            f[((int64_t)s * q + i) * N + nb(x, y, z, c[0], c[1], -c[2], nx, ny, nz)] ="),
     # film probe (crossings, midpoint tie, disc radius)
     ("x1 = (double)(m - 1) + lerp_cross(ra, rb, mid);", "x1 = (double)m + lerp_cross(ra, rb, mid);"),
     ("d2 = 0.5 * (dd[0] + dd[1]);", "d2 = dd[1];"),
@@ -89,6 +102,13 @@ PY_MUTATIONS = [
     ("h_c = h0 + (h - h0) * (-d0 / (d - d0))", "h_c = h"),
     ("    if h > h_max:\n        armed = False\n", "    if h > h_max:\n        pass\n"),
     ("    elif d < -eps_arm:\n", "    elif d < 0.0:\n"),
+    # multi-lattice model (Sec. 3.1, Fig. 1): the pair's lattices not summed
+    # on a merge, the fluid-gas coupling on one side only, a bubble's gas
+    # laid on the fluid's profile
+    ("    f[k] = f[k] + f[l]\n", "    f[k] = f[k]\n"),
+    ("    Gm[1:, 0] = G_x\n", "    Gm[1:, 0] = 0.0\n"),
+    ("        fk, _ = init(lat, nx, ny, nz, b[k:k + 1], 0.0, rho_gas, width, 0.0, seed)",
+     "        fk, _ = init(lat, nx, ny, nz, b, 0.0, rho_gas, width, 0.0, seed)"),
 ]
 
 

@@ -934,3 +934,142 @@ def test_hand_expanded_single_step_4x4(G):
         base = O.run(O.D2Q9, f0[:, None], 1, tau, 0.0)[:, 0]
         assert np.abs(base - want).max() > 1e-3
     assert np.abs(got - want).max() <= 1e-15 * np.abs(want).max()
+
+
+# ------------------------------------- multi-lattice Shan-Chen (Sec. 3.1, Fig. 1)
+
+def _ml_state(lat, nx, ny, nz, seed=5):
+    """Three lattices (fluid + two bubbles' gas), seeded, away from rest."""
+    rng = np.random.default_rng(seed)
+    b = np.array([[nx * 0.3, ny * 0.5, nz * 0.5 if nz > 1 else 0, 3.0],
+                  [nx * 0.7, ny * 0.45, nz * 0.5 if nz > 1 else 0, 3.5]])
+    f = O.ml_init(lat, nx, ny, nz, b, 2.0, 0.15, 0.3, 2.0, 1e-3, seed)
+    return f * (1 + 0.05 * rng.uniform(-1, 1, f.shape))
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_ml_single_lattice_is_the_single_component_step(lat):
+    """One lattice with coupling G is the single-component step of Sec. 3.1
+    (u = (j + tau F)/rho there, j/rho + tau (psi/rho)(-G S) here: equal up
+    to rounding)."""
+    nx, ny, nz = (16, 12, 1) if lat == O.D2Q9 else (10, 8, 6)
+    f = _ml_state(lat, nx, ny, nz)[0]
+    a = O.run(lat, f, 25, 0.85, -5.0)
+    b = O.ml_run(lat, f[None], 25, 0.85, np.array([[-5.0]]))[0]
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_ml_uncoupled_lattices_sum_to_one_ideal_fluid(lat):
+    """With every coupling zero the lattices share the common velocity
+    u' = sum j / sum rho, and f_eq is linear in rho at fixed u: the sum of
+    the lattices evolves exactly as one lattice (G = 0) started from the
+    summed populations.  A per-lattice velocity j_s / rho_s, or a mass-free
+    weighting, breaks this."""
+    nx, ny, nz = (16, 12, 1) if lat == O.D2Q9 else (10, 8, 6)
+    f = _ml_state(lat, nx, ny, nz)
+    nl = f.shape[0]
+    a = O.ml_run(lat, f, 30, 0.7, np.zeros((nl, nl))).sum(0)
+    b = O.run(lat, f.sum(0), 30, 0.7, 0.0)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+    # the lattices themselves differ from an even split (each keeps its mass)
+    rho = O.ml_moments(lat, O.ml_run(lat, f, 30, 0.7, np.zeros((nl, nl))))[0]
+    rho0 = O.ml_moments(lat, f)[0]
+    assert np.allclose(rho.sum(axis=(1, 2, 3)), rho0.sum(axis=(1, 2, 3)), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("lat,axis", [(O.D2Q9, 0), (O.D2Q9, 1), (O.D3Q19, 2)])
+def test_ml_force_on_cosines_with_an_asymmetric_coupling(lat, axis):
+    """psi_t = 1 + a_t cos(2 pi x/L) along one axis on each lattice: the
+    lattice sum sum_i w_i psi_t(x + c_i) c_i is -(1/3) a_t sin(2 pi x/L)
+    sin(2 pi/L) along the axis (the weights' second moment is 1/3 for every
+    shift pattern along one axis), so F_s = -psi_s sum_t Gm[s][t] (that),
+    closed form; an asymmetric Gm catches a transposed coupling."""
+    L = 12
+    shape = {0: (1, 1, L), 1: (1, L, 1), 2: (L, 1, 1)}[axis]
+    if lat == O.D2Q9:
+        shape = {0: (1, 1, L), 1: (1, L, 1)}[axis]
+    nz, ny, nx = shape
+    x = np.arange(L)
+    amp = np.array([0.3, 0.1, 0.2])
+    psi = np.stack([(1 + a * np.cos(2 * np.pi * x / L)).reshape(shape) for a in amp])
+    Gm = np.array([[-5.0, 0.7, 1.1], [0.4, 0.0, 2.0], [1.5, 3.0, 0.0]])
+    F = O.ml_force(lat, psi, Gm)
+    S = (-(1.0 / 3.0) * amp[:, None] * np.sin(2 * np.pi * x / L) * np.sin(2 * np.pi / L))
+    want = -psi.reshape(3, L) * (Gm @ S)
+    got = F[axis].reshape(3, L)
+    assert np.abs(got - want).max() < 1e-14
+    for a in range(3):
+        if a != axis and not (lat == O.D2Q9 and a == 2):
+            assert np.abs(F[a]).max() < 1e-15
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_ml_mass_per_lattice_momentum_and_ledger(lat):
+    """Without injection every lattice keeps its mass; with a symmetric
+    coupling matrix the pair forces cancel over the periodic lattice, so the
+    total momentum sum_s sum_x (j_s + F_s/2) stays at its start value; the
+    blowing agent adds its dm to its own lattice only (Sec. 3)."""
+    nx, ny, nz = (20, 16, 1) if lat == O.D2Q9 else (10, 8, 8)
+    f = _ml_state(lat, nx, ny, nz)
+    Gm = O.ml_coupling(3, -5.0, 0.9, 1.7)
+    assert np.array_equal(Gm, Gm.T)
+
+    def momentum(f):
+        rho, jx, jy, jz = O.ml_moments(lat, f)
+        psi, _ = O.eos(rho, 0.0)
+        F = O.ml_force(lat, psi, Gm)
+        return np.array([(j + F_ / 2).sum() for j, F_ in zip((jx, jy, jz), F)])
+
+    m0 = O.ml_moments(lat, f)[0].sum(axis=(1, 2, 3))
+    p0 = momentum(f)
+    g = O.ml_run(lat, f, 40, 0.9, Gm)
+    assert np.allclose(O.ml_moments(lat, g)[0].sum(axis=(1, 2, 3)), m0, rtol=1e-13, atol=0)
+    assert np.abs(momentum(g) - p0).max() < 1e-12
+    sites = np.array([3 + nx * 4, 7 + nx * 5])
+    budget = np.array([0.03, 0.01])
+    g = O.ml_run(lat, f, 40, 0.9, Gm, sites=sites, site_lattice=[1, 2],
+                 rate=np.array([1e-3, 4e-4]), budget=budget)
+    gain = O.ml_moments(lat, g)[0].sum(axis=(1, 2, 3)) - m0
+    assert budget[0] == 0.0 and budget[1] == 0.0           # 30 and 25 steps of the agent
+    assert np.allclose(gain, [0.0, 0.03, 0.01], rtol=0, atol=1e-14 * m0.max())
+
+
+def test_ml_uniform_rest_state_is_a_fixed_point_and_empty_lattices_stay_finite():
+    """Uniform lattices at rest: every force is zero and f_eq(rho, 0) = f,
+    so nothing changes beyond the rounding of the density sums; a lattice that is empty everywhere (a merged
+    bubble's) stays empty and finite (psi/rho is taken as its limit 1)."""
+    nx, ny = 8, 6
+    _, w = O.velocities(O.D2Q9)
+    f = np.stack([w[:, None, None, None] * r * np.ones((1, ny, nx)) for r in (1.9, 0.2, 0.0)])
+    g = O.ml_run(O.D2Q9, f, 10, 0.8, O.ml_coupling(3, -5.0, 1.0, 2.0))
+    assert np.abs(g - f).max() <= 4e-16     # the density sums round in the last bit
+    assert np.array_equal(g[2], f[2]) and np.isfinite(g).all()
+
+
+def test_ml_pressure_reduces_to_the_eos_and_expands_the_coupling():
+    """One lattice: p = rho/3 + G/6 psi^2 (Sec. 3.1).  Three lattices: the
+    double sum over the coupling matrix written out."""
+    rng = np.random.default_rng(2)
+    rho = rng.uniform(0.0, 2.0, (3, 5))
+    p1 = O.ml_pressure(rho[:1], np.array([[-5.0]]))
+    assert np.allclose(p1, O.eos(rho[0], -5.0)[1], rtol=1e-15, atol=1e-15)
+    Gm = np.array([[-5.0, 0.7, 0.7], [0.7, 0.0, 1.3], [0.7, 1.3, 0.0]])
+    psi = 1 - np.exp(-rho)
+    want = rho.sum(0) / 3 + (-5.0 * psi[0] ** 2 + 2 * 0.7 * psi[0] * (psi[1] + psi[2])
+                             + 2 * 1.3 * psi[1] * psi[2]) / 6
+    assert np.allclose(O.ml_pressure(rho, Gm), want, rtol=1e-14, atol=1e-15)
+
+
+def test_ml_merge_conserves_and_removes_the_barrier():
+    """eta_m = 0 merges lattice l into k: the pair's mass and momentum are
+    kept on lattice k, lattice l is empty, and their coupling is zero."""
+    f = _ml_state(O.D2Q9, 16, 12, 1)
+    Gm = O.ml_coupling(3, -5.0, 1.0, 2.0)
+    g, Gm2 = O.ml_merge(f, Gm, 1, 2)
+    rf, jxf, jyf, _ = O.ml_moments(O.D2Q9, f)
+    rg, jxg, jyg, _ = O.ml_moments(O.D2Q9, g)
+    assert np.array_equal(g[2], np.zeros_like(g[2]))
+    assert np.allclose(rg[1], rf[1] + rf[2], rtol=1e-15, atol=0)
+    assert np.allclose(jxg[1], jxf[1] + jxf[2], rtol=1e-15, atol=1e-17)
+    assert Gm2[1, 2] == Gm2[2, 1] == 0.0 and Gm2[0, 1] == Gm[0, 1]
