@@ -574,6 +574,72 @@ def run_ensemble(args, world=1, rank=0, local=0):
     print(json.dumps(line), flush=True)
 
 
+def run_ml_sweep(args, world=1, rank=0, local=0):
+    """Nine bubble sizes (Sec. 4, Fig. 3) in the multi-lattice model and in
+    the single-component model: per size, the two disks run until the
+    rupture criterion fires (eta_m = 0 merges the pair's lattices) or the
+    film is gone; h_c against R_d beside the paper's fitted forms.  Not a
+    throughput line: every domain runs once, and the rank-0 process alone
+    does the work."""
+    import torch
+    from paper_1708_01608_gb300 import build_lib
+    from paper_1708_01608_gb300 import workloads as WL
+    if rank != 0:
+        return
+    build_lib.build()
+    from paper_1708_01608_gb300 import lbm
+    torch.cuda.set_device(local)
+    R = WL.ML_SWEEP_9
+    rows = {"multi_lattice": [], "single_component": []}
+    t0 = time.perf_counter()
+    updates = 0.0
+    for dm in WL.ml_sweep_domains(R):
+        L = dm["L"]
+        b = np.array(dm["bubbles"])
+        mid = 0.5 * (R["rho_l"] + R["rho_v"])
+        M = lbm.MultiLattice("D2Q9", L, L, 1, nl=3, tau=R["tau"], rho0=R["rho0"], G=R["G"],
+                             G_x=R["G_x"], G_b=R["G_b"], storage="f64")
+        M.seed(b, R["rho_l"], R["rho_v"], R["rho_gas"], R["width"], R["noise"], R["seed"])
+        r = M.run_until_rupture(dm["line"], mid, R["eps_arm"], R["diag_every"], R["steps"],
+                                R["h_max"])
+        rows["multi_lattice"].append(dict(R_b=dm["R"], L=L, **r))
+        updates += 3.0 * L * L * r["steps"]
+        M.close()
+        S = lbm.Lattice("D2Q9", L, L, 1, tau=R["tau"], G=R["G"], rho0=R["rho0"], storage="f64",
+                        kernel="fused")
+        S.seed_bubbles(b, R["rho_l"], R["rho_v"], R["width"], R["noise"], R["seed"])
+        r = S.run_until_rupture(dm["line"], mid, R["eps_arm"], R["diag_every"], R["steps"],
+                                R["h_max"])
+        rows["single_component"].append(dict(R_b=dm["R"], L=L, **r))
+        updates += L * L * r["steps"]
+        S.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    from paper_1708_01608_gb300.sweep import fit_fig3
+    fits = {}
+    for k, rr in rows.items():
+        fired = [x for x in rr if x["fired"]]
+        if len(fired) >= 3:
+            fits[k] = fit_fig3([x["R_b"] for x in fired], [x["r_d"] for x in fired],
+                               [x["h_c"] for x in fired])
+    line = {"metric": "nine-size two-bubble sweep, multi-lattice vs single-component Shan-Chen "
+                      "(h_c vs R_d; not a throughput line)",
+            "value": updates / dt / 1e6, "unit": "MLUPS (lattice updates incl. every lattice)",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "seconds": dt,
+            "config": {"workload": R["name"], "radii": list(R["radii"]), "gap": R["gap"],
+                       "tau": R["tau"], "G": R["G"], "G_x": R["G_x"], "G_b": R["G_b"],
+                       "rho_gas": R["rho_gas"], "noise": R["noise"],
+                       "diag_every": R["diag_every"], "eps_arm": R["eps_arm"],
+                       "h_max": R["h_max"], "max_steps": R["steps"]},
+            "rows": {k: [{q: (round(v, 4) if isinstance(v, float) else v) for q, v in x.items()}
+                         for x in rr] for k, rr in rows.items()},
+            "fig3_fit": fits,
+            "paper_fit": {"h_c": "0.002 R_d^2 - 0.003 R_d + 0.035",
+                          "R_d": "2.088 ln(R_b) + 0.114", "units": "the paper's (unstated)"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(args):
     import torch
     from paper_1708_01608_gb300 import build_lib
@@ -621,12 +687,14 @@ def main():
     ap.add_argument("--profile-diagnostics", action="store_true",
                     help="--profile-steps: then run one diagnostic interval")
     ap.add_argument("--workload", default=None,
-                    choices=["foam128", "foam512", "foam768", "ensemble256"],
+                    choices=["foam128", "foam512", "foam768", "ensemble256", "ml9"],
                     help="foam512: the default benchmark line, the 512^3 foam (FP32, or "
                          "--storage f16/bf16/f64); foam128: 64 injecting nuclei on 128^3 (the "
                          "default of --profile-steps, whose --extent keeps its 64 sites); "
                          "foam768: the 768^3 FP16-offset full foam with 4096 injection sites; "
-                         "ensemble256: the batched two-bubble sweep run to completion")
+                         "ensemble256: the batched two-bubble sweep run to completion; ml9: "
+                         "nine bubble sizes in the multi-lattice and the single-component "
+                         "model (h_c vs R_d, not a throughput line)")
     ap.add_argument("--storage", default=None, choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--single", action="store_true",
                     help="ensemble256: also run every domain alone, one after the other")
@@ -650,6 +718,14 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup(args.gpus)
+    if args.workload == "ml9":
+        try:
+            run_ml_sweep(args, world, rank, local)
+        finally:
+            if world > 1:
+                import torch.distributed as dist
+                dist.destroy_process_group()
+        return
     if args.workload == "ensemble256":
         try:
             run_ensemble(args, world, rank, local)

@@ -55,7 +55,35 @@ ENSEMBLE_256 = dict(
     tau=(0.6, 1.0), G=-5.0, rho0=1.0, rho_ref=2.0, rho_l=2.0, rho_g=0.15, width=2.0,
     noise=1e-3, seed=3, steps=20000, diag_every=20, eps_arm=1e-3, h_max=8.0)
 
-WORKLOADS = {w["name"]: w for w in (TWO_DISKS_128, FOAM_128, FOAM_512, FOAM_768, ENSEMBLE_256)}
+# nine bubble sizes (Sec. 4, Fig. 3: simulations for 9 bubble sizes), two
+# D2Q9 disks of radius R_b at a 4-cell liquid gap on a periodic square of
+# side 4 R_b + 24 rounded up to a multiple of 8; run in the multi-lattice
+# model (fluid + one gas lattice per bubble, gas 0.05 inside each bubble,
+# fluid-gas coupling G_x, barrier G_b) and in the single-component model,
+# until the rupture criterion fires or the film is gone
+ML_SWEEP_9 = dict(
+    name="d2q9_ml_sweep_9", radii=(8.0, 11.0, 14.0, 17.0, 20.0, 24.0, 28.0, 33.0, 38.0),
+    gap=4.0, tau=1.0, G=-5.0, G_x=1.0, G_b=2.0, rho0=1.0, rho_l=2.0, rho_v=0.15, rho_gas=0.05,
+    width=2.0, noise=1e-4, seed=9, steps=20000, diag_every=20, eps_arm=1e-3, h_max=8.0)
+
+WORKLOADS = {w["name"]: w for w in (TWO_DISKS_128, FOAM_128, FOAM_512, FOAM_768, ENSEMBLE_256,
+                                    ML_SWEEP_9)}
+
+
+def ml_sweep_domains(recipe=ML_SWEEP_9):
+    """The domains of the nine-size sweep: dicts with side L, the two disks
+    (x, y, 0, R) on the middle row and the probe line from centre to
+    centre."""
+    import math
+    out = []
+    for R in recipe["radii"]:
+        L = int(math.ceil((4 * R + 24) / 8.0)) * 8
+        c1 = L / 2 - R - recipe["gap"] / 2
+        c2 = L / 2 + R + recipe["gap"] / 2
+        x0 = int(math.floor(c1))
+        out.append(dict(L=L, R=R, bubbles=[(c1, L / 2, 0.0, R), (c2, L / 2, 0.0, R)],
+                        line=(x0, L // 2, 0, 0, int(math.ceil(c2)) - x0 + 1)))
+    return out
 
 
 def ensemble_domains(recipe=ENSEMBLE_256, n=None, side=None):
