@@ -49,18 +49,16 @@ B_ALG = 2 * Q * 4                             # bytes per lattice update, FP32 s
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the fused kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the current kernel), keyed by
-# (workload, storage, tile id); workloads without a capture report null.
-# The 16-bit 512^3 and 768^3 entries are the 256^3 capture of the same tile
-# scaled by the cells per launch (x8, x27): at 256^3 the lattice is already
+# (workload, storage, tile id); workloads without a capture of the current
+# kernel report null.  The 512^3 entries are the 256^3 capture of the same
+# tile scaled by the cells per launch (x8): at 256^3 the lattice is already
 # five times the L2 and the capture's traffic equals the algorithmic bytes.
 NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.8e6,
                           ("d3q19_foam_128", "f32", 5): 277.5e6,
                           ("d3q19_foam_128", "f32", 16): 277.35e6,
                           ("d3q19_foam_128", "f32", 25): 277.57e6,
                           ("d3q19_foam_128", "f64", 6): 626.2e6,
-                          ("d3q19_foam_512", "f32", 16): 8 * 2534.04e6,
-                          ("d3q19_foam_512", "f16", 14): 8 * 1270.09e6,
-                          ("d3q19_foam_768", "f16", 14): 27 * 1270.09e6}
+                          ("d3q19_foam_512", "f32", 16): 8 * 2534.04e6}
 # FP64 storage: the step kernel is bound by the FP64 pipe, not by HBM.  FP64
 # operations per lattice update of its D3Q19 kernel, DADD + DMUL + 2 DFMA as
 # ncu counts them on the 128^3 case (146 + 71 + 2 x 332).  The peak is
@@ -232,13 +230,20 @@ def site_budgets(n):
     return np.full(n, float(b))
 
 
+def resid():
+    """The per-cell rounding residual of 16-bit storage, when the workload
+    asks for it (FP32 and FP64 storage have none)."""
+    return bool(W.get("mass_residual")) and W["storage"] in ("f16", "bf16")
+
+
 def make_lattice(lbm, kernel="auto", tile=0):
     s = W["sites"]
     bub = lbm.sample_sites(W["nx"], W["ny"], W["nz"], s["n"], s["r_min"], s["r_max"],
                            s["min_spacing"], s["min_gap"], W["seed"])
     L = lbm.Lattice("D3Q19", W["nx"], W["ny"], W["nz"], tau=W["tau"], G=W["G"],
                     rho0=W["rho0"], storage=W["storage"], gas_threshold=W["threshold"],
-                    rho_ref=W["rho_ref"], kernel="fused" if tile else kernel, tile=tile)
+                    rho_ref=W["rho_ref"], kernel="fused" if tile else kernel, tile=tile,
+                    mass_residual=resid())
     L.seed_bubbles(bub, W["rho_l"], W["rho_g"], W["width"], W["noise"], W["seed"])
     rate = np.full(len(bub), W["rate"])
     budget = site_budgets(len(bub))
@@ -310,7 +315,8 @@ def cpu_baseline(seconds_target=15.0):
 def base_config():
     """The workload's config, the same for both arms."""
     return {"workload": W["name"], "lattice": "D3Q19", "extent": [W["nx"], W["ny"], W["nz"]],
-            "storage": W["storage"], "tau": W["tau"], "G": W["G"], "sites": W["sites"]["n"],
+            "storage": W["storage"], "mass_residual": resid(), "tau": W["tau"], "G": W["G"],
+            "sites": W["sites"]["n"],
             "lbm_steps_per_bench_step": INNER, "rho_ref": W["rho_ref"],
             "l2": "inputs larger than L2: two %.0f MB population lattices"
                   % (CELLS * B_ALG / 2 / 1e6),
@@ -432,7 +438,8 @@ def run_ours(args, world, rank, local):
     e2e_val = job_value(units, world, e2e_s)
     peak, src = peak_hbm()
     achieved = B_ALG * CELLS / (step_kernel_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC_PER_LAUNCH.get((W["name"], W["storage"], plan[1]))
+    traffic = NCU_TRAFFIC_PER_LAUNCH.get((W["name"], W["storage"] + ("+resid" if resid() else ""),
+                                          plan[1]))
     kname = "fused_step_kernel_x2" if plan[1] in X_PAIR_TILES else "fused_step_kernel"
     if W["storage"] == "f64":
         tflops = FP64_FLOP_PER_UPDATE * CELLS / (step_kernel_ms / 1e3) / 1e12
@@ -738,7 +745,9 @@ def main():
         # the metric names the storage form measured
         METRIC = METRIC.replace(STORAGE_NAME[W["storage"]], STORAGE_NAME[args.storage])
         W = dict(W, storage=args.storage)
-    B_ALG = 2 * Q * {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[W["storage"]]
+    # bytes per lattice update: every population read and written once, plus
+    # the rounding residual's FP32 read and write when 16-bit storage keeps one
+    B_ALG = 2 * Q * {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[W["storage"]] + (8 if resid() else 0)
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)

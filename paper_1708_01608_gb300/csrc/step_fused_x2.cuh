@@ -14,11 +14,14 @@
 // loads: N at its own column for cx = 0, S at its own column for cx = +1 and
 // S two columns left for cx = -1.
 //
-// The staged populations of plane P are read twice: once for rho(P) (psi
-// of P must be complete before plane P - 1 can be collided) and once more,
-// into registers, after the collision of P - 1.  A stage is therefore free
-// one iteration after it was consumed, and NS - 1 planes are in flight
-// ahead of the plane being summed.
+// 16-bit storage reads the staged populations of plane P once, into
+// registers as packed pairs (psi of P must be complete before plane P - 1
+// can be collided, so P waits there one iteration); its stage is refilled
+// right after the psi phase and NS planes are in flight.  FP32 storage
+// reads plane P a second time, into registers, after the collision of
+// P - 1 (holding two planes of float pairs would cost 38 registers): its
+// stage is free one iteration after it was consumed, and NS - 1 planes are
+// in flight ahead of the plane being summed.
 #pragma once
 
 #include "step_fused.cuh"
@@ -147,6 +150,13 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
   // 16-bit residual forms: each cell's rounding residual of the last step
   // joins its mass R, and the new one is what this step's stores round off
   constexpr bool RESID = S1::RESID;
+  // 16-bit storage keeps a staged plane in registers as packed pairs (19
+  // registers): read from its stage once, for psi, it is collided one
+  // iteration later, and the stage is refilled right after the psi phase,
+  // so NS planes are in flight.  FP32 pairs would take 38 registers more;
+  // there the plane is read from its stage a second time after the
+  // collision, and NS - 1 planes are in flight.
+  constexpr bool KEEP = sizeof(T) == 2;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
@@ -270,9 +280,11 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
     h_j = (dy + HY) * PW + dx + 2;
   }
 
-  float2 cur[Q];  // populations of plane P - 1 (cells a, b) for the collision
+  // staged values (cells a, b) as stored: cur of plane P - 1 for the
+  // collision; with KEEP, nxt of plane P, read once from its stage for psi
+  T2 cur[Q], nxt[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) cur[i] = f2(0.0f);
+  for (int i = 0; i < Q; ++i) cur[i] = nxt[i] = S2::store(f2(0.0f));
   float2 Rcur = f2(0.0f), Rnxt = f2(0.0f);  // sums of the staged values
 
   const float om1 = 1.0f - omega;
@@ -297,8 +309,13 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
     float *rN = ringN + (k & 3) * RP;
     float *rS = ringS + (k & 3) * RP;
     if (active) {
-      const float2 r2 = sum_q<Q, float2>(
-          [&](int i) { return S2::load(main2[(i * BY + ty) * TPX + tp]); });
+      if constexpr (KEEP) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) nxt[i] = main2[(i * BY + ty) * TPX + tp];
+      }
+      const float2 r2 = sum_q<Q, float2>([&](int i) {
+        return S2::load(KEEP ? nxt[i] : main2[(i * BY + ty) * TPX + tp]);
+      });
       const float2 ps = psi_x2(add2(f2(rho_ref), r2), rho0, inv_rho0);
       *reinterpret_cast<float2 *>(rN + c0) = ps;
       rS[c0 - 1] = ps.x;
@@ -325,14 +342,20 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
       if (tid == 0) {
         if (m.err) atomicOr(m.err, ERR_TMA_TIMEOUT);
         // wait (bounded) for the copies still in flight into this CTA's stages
-        const int hi = min(NPL, max(NS, k + NS - 1));
+        const int hi = KEEP ? min(NPL, k + NS) : min(NPL, max(NS, k + NS - 1));
         for (int k2 = k + 1; k2 < hi; ++k2)
           mbar_wait_bounded(&bars[(k0 + k2) % NS], ((k0 + k2) / NS) & 1u, 100000000ull);
       }
       return false;
     }
-    // the stage of plane P - 1 was last read before this barrier
-    if (tid == 0 && k >= 1 && k - 1 + NS < NPL) issue(k - 1 + NS);
+    if constexpr (KEEP) {
+      // the stage of plane P was last read before this barrier (its values
+      // are in registers now): refill it with plane P + NS
+      if (tid == 0 && k + NS < NPL) issue(k + NS);
+    } else {
+      // the stage of plane P - 1 was last read before this barrier
+      if (tid == 0 && k >= 1 && k - 1 + NS < NPL) issue(k - 1 + NS);
+    }
 
     // ---- collide plane P - 1 (psi of P - 2, P - 1, P in the ring) and push
     if (k >= 2) {
@@ -402,7 +425,7 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
           constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-          const float2 d = sub2(cur[i], cur[o]);
+          const float2 d = sub2(S2::load(cur[i]), S2::load(cur[o]));
           jx = cacc2<cx>(jx, d);
           jy = cacc2<cy>(jy, d);
           jz = cacc2<cz>(jz, d);
@@ -436,8 +459,8 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
             const float2 a = mul2(rho, cu);
             const float2 A = fma2(a, mul2(f2(c45[wc]), cu), wK[wc]);
             const float2 Bv = mul2(f2(c3[wc]), a);
-            const float2 gi = fma2(om1_2, cur[i], add2(A, Bv));
-            const float2 go = fma2(om1_2, cur[o], sub2(A, Bv));
+            const float2 gi = fma2(om1_2, S2::load(cur[i]), add2(A, Bv));
+            const float2 go = fma2(om1_2, S2::load(cur[o]), sub2(A, Bv));
             moved = add2(moved, add2(gi, go));
             if (SITE) {
               put(std::integral_constant<int, i>{}, fma2(f2((float)L::w(i)), dmc, gi));
@@ -458,10 +481,13 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
         if constexpr (RESID) *reinterpret_cast<float2 *>(m.resid + own) = racc;
       }
     }
-    // ---- populations of plane P into registers for the next collision
-    if (active && k >= 1 && k + 1 < NPL) {
+    // ---- plane P is collided in the next iteration
+    if constexpr (KEEP) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) cur[i] = S2::load(main2[(i * BY + ty) * TPX + tp]);
+      for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
+    } else if (active && k >= 1 && k + 1 < NPL) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) cur[i] = main2[(i * BY + ty) * TPX + tp];
     }
     Rcur = Rnxt;
   }

@@ -39,12 +39,14 @@ FOAM_512 = dict(
     sites=dict(n=1000, r_min=4.0, r_max=12.0, min_spacing=0.0, min_gap=4.0),
     rate=0.0, budget=0.0, steps=2000, rho_ref=1.8, threshold=1.0)
 
-# full foam, 4096 sites, FP16-offset storage (768^3)
+# full foam, 4096 sites, FP16-offset storage (768^3); the per-cell rounding
+# residual keeps the blowing agent's sub-quantum deposits (mass_residual)
 FOAM_768 = dict(
     name="d3q19_foam_768", lattice="D3Q19", nx=768, ny=768, nz=768, tau=0.9, G=-5.0,
     rho0=1.0, storage="f16", rho_l=2.0, rho_g=0.15, width=2.0, noise=1e-3, seed=4,
     sites=dict(n=4096, r_min=3.0, r_max=3.0, min_spacing=12.0, min_gap=0.0),
-    rate=5e-5, budget=(20.0, 80.0), steps=50000, diag_every=100, rho_ref=2.0, threshold=1.0)
+    rate=5e-5, budget=(20.0, 80.0), steps=50000, diag_every=100, rho_ref=2.0, threshold=1.0,
+    mass_residual=True)
 
 # 256 independent two-bubble D2Q9 domains (FP32): side log-uniform 64..512
 # (rounded to multiples of 8), gap U(2, 10), radius U(8, min(60, (L - 2 gap)/4
