@@ -443,12 +443,15 @@ lbm_status lbm_write_f(lbm_ctx *ctx, const double *host_src, size_t bytes);
 
 /* ---- batched ensemble of independent two-bubble D2Q9 domains ------------
  * The bubble-size sweep of Sec. 4 (Fig. 3: critical film thickness h_c
- * against the film-disc radius R_d) runs many uneven lattices at once: one
- * launch per time step and tile class covers every active domain, and every
- * diag_every steps a probe measures each domain's film (lbm_film_probe) and
- * advances its rupture state machine (lbm_run_until_rupture) on the device.
- * Domains whose criterion fired, or whose film is gone, stop.  Storage is
- * FP32 offset form (f_i - w_i rho_ref), arithmetic FP32, probes FP64. */
+ * against the film-disc radius R_d) runs many uneven lattices at once, and
+ * every diag_every steps a probe measures each domain's film
+ * (lbm_film_probe) and advances its rupture state machine
+ * (lbm_run_until_rupture) on the device.  Domains whose criterion fired, or
+ * whose film is gone, stop.  Storage is FP32 offset form
+ * (f_i - w_i rho_ref), arithmetic FP32, probes FP64.  The steps run as one
+ * launch per time step and tile class over every active domain, or as
+ * persistent launches (lbm_ensemble_set_launch); the results do not depend
+ * on which. */
 typedef struct {
   int64_t nx, ny;          /* extents: 8..4096, nx a multiple of 4 */
   double tau, G, rho0, rho_ref;
@@ -486,6 +489,33 @@ lbm_status lbm_ensemble_stats(const lbm_ensemble *ens, double out[4]);
 
 /* Current populations of one domain as doubles f[i*N + x + nx*y]. */
 lbm_status lbm_ensemble_read_f(lbm_ensemble *ens, int32_t domain, double *host, size_t bytes);
+
+/* How lbm_ensemble_run launches the steps (not in the paper, which gives no
+ * implementation); the results do not depend on it.
+ * LBM_ENS_GRAPH: one launch per step and tile class over every active
+ *   domain, captured with the probe in a CUDA graph per interval.
+ * LBM_ENS_TEMPORAL: one launch per S steps (S = 2 or 5, diag_every a
+ *   multiple of 2 S): a CTA takes a tile of one domain with a halo of 2 S
+ *   cells through S steps in shared memory.
+ * LBM_ENS_PERSISTENT: per-step launches until the active domains' work
+ *   items (tiles of 128 columns x chunks of rows) fit in one wave of CTAs,
+ *   then one cooperative launch per ten intervals, in which every CTA keeps
+ *   its work item, waits between steps only for the items at most two
+ *   chunks and two tiles away, and the domain's first CTA runs the probe.
+ * LBM_ENS_AUTO (the default): the per-interval launches chosen by measured
+ *   time as the active set shrinks.
+ * LBM_ENS_DEBUG_WITHHOLD_FLAG (tests only): as PERSISTENT, but the first
+ *   CTA of every persistent launch never releases its step flag, so the
+ *   bounded waits (1 s) expire and lbm_ensemble_run returns LBM_ETIMEOUT;
+ *   exercises the timeout path without a fault.
+ * Errors: EINVAL (NULL, unknown mode), ETIMEOUT (after a timed-out launch),
+ * ECUDA. */
+#define LBM_ENS_AUTO 0
+#define LBM_ENS_GRAPH 1
+#define LBM_ENS_DEBUG_WITHHOLD_FLAG 2
+#define LBM_ENS_PERSISTENT 3
+#define LBM_ENS_TEMPORAL 4
+lbm_status lbm_ensemble_set_launch(lbm_ensemble *ens, int32_t mode);
 
 /* ---- multi-lattice Shan-Chen model (Sec. 3.1, Fig. 1) -------------------
  * The paper's modified model puts each phase on its own lattice: every

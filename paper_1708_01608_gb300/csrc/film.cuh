@@ -75,11 +75,13 @@ __device__ bool film_row_fails(const Acc &acc, int64_t x, int64_t y, int64_t z, 
 // out.  Crossings and disc rows are searched in parallel chunks: each
 // candidate is evaluated exactly as a sequential scan would evaluate it, and
 // the first hit is a block-wide minimum, so the result equals the
-// sequential scan's.
-template <class Acc>
+// sequential scan's.  need_disc(h, d2p), evaluated by every thread on the
+// same values, says whether R_d is wanted: when it is not, the disc rows are
+// not scanned and out[5] = -1 (the other outputs are unchanged).
+template <class Acc, class NeedDisc>
 __device__ void film_probe_block(const Acc &acc, int64_t x0, int64_t y0, int64_t z0,
                                  const int *e, const int *ep, int64_t len, double mid,
-                                 double *out) {
+                                 double *out, NeedDisc need_disc) {
   __shared__ unsigned long long s_first;
   const int tid = threadIdx.x, nt = blockDim.x;
   const unsigned long long NONE = ~0ull;
@@ -129,6 +131,18 @@ __device__ void film_probe_block(const Acc &acc, int64_t x0, int64_t y0, int64_t
     const double *q = s_v + 4 + (cc - c);
     return q[2] - 2.0 * q[1] + q[0];
   };
+  const double d2p = xm - fl == 0.5 ? 0.5 * (d2(c) + d2(c + 1)) : d2(xm - fl < 0.5 ? c : c + 1);
+  if (!need_disc(h, d2p)) {
+    if (tid == 0) {
+      out[0] = 1.0;
+      out[1] = x1;
+      out[2] = x2;
+      out[3] = h;
+      out[4] = d2p;
+      out[5] = -1.0;
+    }
+    return;
+  }
   const int64_t cm = (int64_t)floor(xm + 0.5);
   const int64_t xc = x0 + cm * e[0], yc = y0 + cm * e[1], zc = z0 + cm * e[2];
   // rows of the disc: the first row (outward from the midpoint row) whose
@@ -175,9 +189,16 @@ __device__ void film_probe_block(const Acc &acc, int64_t x0, int64_t y0, int64_t
     out[1] = x1;
     out[2] = x2;
     out[3] = h;
-    out[4] = xm - fl == 0.5 ? 0.5 * (d2(c) + d2(c + 1)) : d2(xm - fl < 0.5 ? c : c + 1);
+    out[4] = d2p;
     out[5] = 0.5 * (double)extent;
   }
+}
+
+template <class Acc>
+__device__ void film_probe_block(const Acc &acc, int64_t x0, int64_t y0, int64_t z0,
+                                 const int *e, const int *ep, int64_t len, double mid,
+                                 double *out) {
+  film_probe_block(acc, x0, y0, z0, e, ep, len, mid, out, [](double, double) { return true; });
 }
 
 }  // namespace sclbm

@@ -28,6 +28,8 @@ F64, F32, F16_OFFSET, BF16_OFFSET = 0, 1, 2, 3
 RHO, PSI, P, U, F, LAPP = range(6)
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_TWO_PASS = 0, 1, 2
 DEBUG_WITHHOLD_TMA = 1
+# lbm_ensemble_set_launch modes
+ENS_AUTO, ENS_GRAPH, ENS_DEBUG_WITHHOLD_FLAG, ENS_PERSISTENT, ENS_TEMPORAL = 0, 1, 2, 3, 4
 
 STORAGE = {"f64": F64, "f32": F32, "f16": F16_OFFSET, "bf16": BF16_OFFSET}
 LATTICE = {"D2Q9": D2Q9, "D3Q19": D3Q19}
@@ -153,6 +155,7 @@ def _load():
         "lbm_ensemble_results": (i32, [P_, P_, i32]),
         "lbm_ensemble_stats": (i32, [P_, P_]),
         "lbm_ensemble_read_f": (i32, [P_, i32, P_, sz]),
+        "lbm_ensemble_set_launch": (i32, [P_, i32]),
         "lbm_fp64_rate": (i32, [i32, C.POINTER(d)]),
         "lbm_ml_config_default": (None, [C.POINTER(MLConfig)]),
         "lbm_ml_create": (i32, [C.POINTER(MLConfig), C.POINTER(P_)]),
@@ -196,7 +199,8 @@ EXPORTS = ("lbm_config_default", "lbm_create", "lbm_destroy", "lbm_sample_sites"
            "lbm_ml_read_budgets", "lbm_ml_step", "lbm_ml_step_count", "lbm_ml_merge",
            "lbm_ml_fields", "lbm_ml_run_until_rupture",
            "lbm_version", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_run",
-           "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f")
+           "lbm_ensemble_results", "lbm_ensemble_stats", "lbm_ensemble_read_f",
+           "lbm_ensemble_set_launch")
 
 
 def lib():
@@ -711,6 +715,11 @@ class Ensemble:
         out = np.zeros(4)
         _check(_lib.lbm_ensemble_stats(self._h, _ptr(out)))
         return dict(steps=int(out[0]), updates=out[1], active=int(out[2]), launches=int(out[3]))
+
+    def set_launch(self, mode):
+        """ENS_AUTO, ENS_GRAPH, ENS_TEMPORAL, ENS_PERSISTENT or the test
+        hook ENS_DEBUG_WITHHOLD_FLAG (lbm_ensemble_set_launch)."""
+        _check(_lib.lbm_ensemble_set_launch(self._h, int(mode)))
 
     def read_f(self, d):
         ny, nx = self.shapes[d]

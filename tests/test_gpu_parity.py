@@ -628,12 +628,24 @@ def _small_domains(noise=None):
     return ensemble_domains(rec, n=6, side=(64, 136))
 
 
-def test_ensemble_matches_single_lattice_bitwise(lbm):
+@pytest.mark.parametrize("mode", ["auto", "graph", "persistent", "temporal"])
+def test_ensemble_matches_single_lattice_bitwise(lbm, mode):
     """Each domain of the batched launch evolves exactly as the same domain
-    run alone through the fused single-lattice path (same FP32 arithmetic)."""
+    run alone through the fused single-lattice path (same FP32 arithmetic),
+    under every launch mode: per-step launches, persistent ones (these six
+    domains fit in one wave at once), temporally blocked ones (5 steps per
+    launch) and the measured choice."""
     doms = _small_domains()
     E = lbm.Ensemble(doms, eps_arm=1e-3, diag_every=20)
+    E.set_launch(dict(auto=lbm.ENS_AUTO, graph=lbm.ENS_GRAPH, persistent=lbm.ENS_PERSISTENT,
+                      temporal=lbm.ENS_TEMPORAL)[mode])
     E.run(200)
+    launches = E.stats()["launches"]
+    # per-step launches: 200 steps of one or two tile classes plus 10 probes;
+    # temporally blocked: 4 launches of 5 steps plus the probe per interval
+    want = dict(graph=lambda n: n >= 210, persistent=lambda n: n == 1,
+                temporal=lambda n: n == 50, auto=lambda n: n >= 1)[mode]
+    assert want(launches), launches
     for d, dm in enumerate(doms):
         L = lbm.Lattice("D2Q9", dm["nx"], dm["ny"], 1, tau=dm["tau"], G=dm["G"], storage="f32",
                         rho_ref=dm["rho_ref"], kernel="fused")
@@ -643,6 +655,55 @@ def test_ensemble_matches_single_lattice_bitwise(lbm):
         L.step(r["steps"])
         assert (E.read_f(d) == L.read("f")).all(), d
         L.close()
+    E.close()
+
+
+@pytest.mark.parametrize("mode", ["persistent", "temporal", "auto"])
+def test_ensemble_launch_modes_match_per_step_launches(lbm, mode):
+    """200 domains of 64..200 cells (3.0M cells, 2231 work items of 16-row
+    chunks: more than one wave of persistent CTAs holds) run 3000 steps:
+    under PERSISTENT per-step launches at first, then persistent ones once
+    enough domains stopped; under TEMPORAL 5 steps per launch throughout;
+    under AUTO the measured choice.  Outcomes, stop steps, h_c, h_probe, R_d
+    and every domain's final populations are bit-identical to per-step
+    launches throughout."""
+    from paper_1708_01608_gb300.workloads import ENSEMBLE_256, ensemble_domains
+    doms = ensemble_domains(dict(ENSEMBLE_256, seed=5), n=200, side=(64, 200))
+    assert sum(d["nx"] * d["ny"] for d in doms) > 2.9e6
+    runs = []
+    m = dict(persistent=lbm.ENS_PERSISTENT, temporal=lbm.ENS_TEMPORAL, auto=lbm.ENS_AUTO)[mode]
+    for mode_k in (m, lbm.ENS_GRAPH):
+        E = lbm.Ensemble(doms, eps_arm=1e-3, diag_every=20)
+        E.set_launch(mode_k)
+        E.run(3000)
+        runs.append((E.results(), [E.read_f(d) for d in range(len(doms))], E.stats()))
+        E.close()
+    (ra, fa, sa), (rg, fg, sg) = runs
+    assert ra == rg
+    assert sum(r["fired"] or r["merged"] for r in ra) >= 100
+    for d in range(len(doms)):
+        assert (fa[d] == fg[d]).all(), d
+    assert sa["updates"] == sg["updates"]
+    if mode != "auto":
+        assert sa["launches"] < sg["launches"] / 3, (sa, sg)
+
+
+def test_ensemble_wait_timeout_is_reported(lbm):
+    """The withheld step flag of the test hook: the persistent launch's
+    bounded waits (1 s) expire, lbm_ensemble_run reports ETIMEOUT and
+    refuses to go on, and a new ensemble on the same device runs."""
+    doms = _small_domains()
+    E = lbm.Ensemble(doms, eps_arm=1e-3, diag_every=20)
+    E.set_launch(lbm.ENS_DEBUG_WITHHOLD_FLAG)  # persistent launches with the hook
+    with pytest.raises(lbm.LBMError) as e:
+        E.run(40)
+    assert e.value.status == lbm.ETIMEOUT
+    with pytest.raises(lbm.LBMError) as e:
+        E.run(40)
+    assert e.value.status == lbm.ETIMEOUT
+    E.close()
+    E = lbm.Ensemble(doms, eps_arm=1e-3, diag_every=20)
+    assert E.run(40) == 40
     E.close()
 
 
