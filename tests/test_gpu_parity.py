@@ -747,20 +747,45 @@ def test_ensemble_criterion_matches_oracle(lbm):
 
 
 def test_ensemble_noisy_domains_follow_oracle(lbm):
-    """Domains with the recipe's 1e-3 initial noise.  There h_c is
+    """Domains with the recipe's 1e-3 initial noise.  There h_c can be
     ill-conditioned: a 1e-6 relative perturbation of the initial state moves
     the oracle's own h_c by 0.9 % on the 104^2 domain of this set (and fires
     one probe later), and FP32 rounding over thousands of steps is a
-    perturbation of that order.  Checked: the same outcome, the firing probe
-    within one interval, h_c within 3 %."""
-    nfired = 0
-    for d, (g, ref) in enumerate(_ensemble_vs_oracle(lbm, _small_domains())):
+    perturbation of that order.  So each domain's oracle is also run from
+    two starts perturbed at FP32 rounding level (relative +-2^-24 per
+    population, seeded), and its own spread of h_c sets the bar: the
+    ensemble's h_c within 1 % of the oracle's where that spread is below
+    0.5 %, else within twice the spread.  Also: the same outcome and the
+    firing probe within one interval; at least one fired domain is held to
+    the 1 % bar."""
+    doms = _small_domains()
+    nfired = nstrict = 0
+    for d, (g, ref) in enumerate(_ensemble_vs_oracle(lbm, doms)):
         assert g["fired"] == ref["fired"] and g["merged"] == ref["merged"], (d, g, ref)
         assert abs(g["steps"] - ref["step"]) <= 20, (d, g, ref)
-        if ref["fired"]:
-            nfired += 1
-            assert abs(g["h_c"] / ref["h_c"] - 1) < 0.03, (d, g, ref)
-    assert nfired >= 1
+        if not ref["fired"]:
+            continue
+        nfired += 1
+        dm, ln = doms[d], doms[d]["line"]
+        f0 = as_stored("D2Q9", oracle_init("D2Q9", dm["nx"], dm["ny"], 1, dm["bubbles"],
+                                           dm["rho_l"], dm["rho_g"], dm["width"],
+                                           dm["noise_amp"], dm["seed"]), "f32", dm["rho_ref"])
+        rng = np.random.default_rng(100 + d)
+        spread = 0.0
+        for _ in range(2):
+            fp = f0 * (1 + 2.0 ** -24 * rng.choice([-1.0, 1.0], size=f0.shape))
+            rp = O.run_until_rupture(O.D2Q9, fp, dm["tau"], dm["G"], (ln[0], ln[1], 0), 0,
+                                     ln[4], dm["rho_mid"], 1e-3, 6000, 20)
+            if rp["fired"]:
+                spread = max(spread, abs(rp["h_c"] / ref["h_c"] - 1))
+            else:
+                spread = max(spread, 1.0)
+        bar = 0.01 if spread < 0.005 else 2 * spread
+        nstrict += bar == 0.01
+        err = abs(g["h_c"] / ref["h_c"] - 1)
+        print("domain", d, "h_c rel err", err, "oracle spread", spread)
+        assert err < bar, (d, g, ref, spread)
+    assert nfired >= 1 and nstrict >= 1, (nfired, nstrict)
 
 
 # ---------------------------------------------------------------- bubble census
