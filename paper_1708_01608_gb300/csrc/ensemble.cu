@@ -756,6 +756,7 @@ lbm_status ensure_graph(lbm_ensemble *E, cudaGraphExec_t *exec) {
     ECK(e);
     c.g = g;
     ECK(cudaGraphInstantiate(&c.x, g, 0));
+    ECK(cudaGraphUpload(c.x, E->s));  // not on the first launch's (timed) path
   }
   *exec = c.x;
   return LBM_OK;
@@ -1222,7 +1223,7 @@ static lbm_status set_tb(lbm_ensemble *E, int cfg) {
 // interval each, whenever the active cells fell below ENS_RETUNE of those
 // of the last measurement; the fastest per lattice update is kept.  Every
 // form gives the same populations, so a trial is ordinary work.
-constexpr double ENS_TUNE_CELLS = 3.0e6, ENS_RETUNE = 0.6, ENS_TB_CELLS = 1.0e6;
+constexpr double ENS_TUNE_CELLS = 3.0e6, ENS_RETUNE = 0.75, ENS_TB_CELLS = 4.0e5;
 
 static double active_cells(const lbm_ensemble *E) {
   double c = 0;
