@@ -688,6 +688,46 @@ def test_ensemble_launch_modes_match_per_step_launches(lbm, mode):
         assert sa["launches"] < sg["launches"] / 3, (sa, sg)
 
 
+def _tiny_domains():
+    """Domains far smaller than a temporally blocked tile's loaded region
+    (52 x 52 for 32 x 32 tiles, S = 5) and lopsided ones; two of them carry
+    a two-bubble film, the others have no film and stop at the first probe."""
+    base = dict(tau=0.9, G=-5.0, rho0=1.0, rho_ref=2.0, rho_l=2.0, rho_g=0.15, width=2.0,
+                noise_amp=1e-3, rho_mid=1.075)
+    out = []
+    for k, (nx, ny) in enumerate([(8, 8), (16, 8), (8, 24), (12, 136), (136, 12)]):
+        out.append(dict(base, nx=nx, ny=ny, seed=50 + k, bubbles=[], line=(0, ny // 2, 0, 0, 4)))
+    out.append(dict(base, nx=40, ny=24, seed=60, line=(12, 12, 0, 0, 17),
+                    bubbles=[(12.0, 12.0, 0.0, 6.0), (28.0, 12.0, 0.0, 6.0)]))
+    out.append(dict(base, nx=24, ny=40, seed=61, line=(12, 12, 0, 1, 17),
+                    bubbles=[(12.0, 12.0, 0.0, 6.0), (12.0, 28.0, 0.0, 6.0)]))
+    return out
+
+
+def test_ensemble_tiny_domains_every_launch_mode(lbm):
+    """Tiny and lopsided domains (the loaded region wraps the domain several
+    times) under every launch form, bit-identical to per-step launches over
+    200 steps.  Under AUTO these few cells make every candidate run one
+    interval, the three temporally blocked tiles included."""
+    doms = _tiny_domains()
+    runs = {}
+    for name, mode in (("graph", lbm.ENS_GRAPH), ("temporal", lbm.ENS_TEMPORAL),
+                       ("persistent", lbm.ENS_PERSISTENT), ("auto", lbm.ENS_AUTO)):
+        E = lbm.Ensemble(doms, eps_arm=1e-3, diag_every=20)
+        E.set_launch(mode)
+        E.run(200)
+        runs[name] = (E.results(), [E.read_f(d) for d in range(len(doms))], E.stats()["updates"])
+        E.close()
+    rg, fg, ug = runs["graph"]
+    assert sum(r["merged"] for r in rg[:5]) == 5  # no film: stopped at the first probe
+    for name in ("temporal", "persistent", "auto"):
+        r, f, u = runs[name]
+        assert r == rg, name
+        assert u == ug, name
+        for d in range(len(doms)):
+            assert (f[d] == fg[d]).all(), (name, d)
+
+
 def test_ensemble_wait_timeout_is_reported(lbm):
     """The withheld step flag of the test hook: the persistent launch's
     bounded waits (1 s) expire, lbm_ensemble_run reports ETIMEOUT and
