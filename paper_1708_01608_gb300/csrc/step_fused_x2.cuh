@@ -95,6 +95,24 @@ struct Storage2<ST_F16R> : Storage2<ST_F16> {};
 template <>
 struct Storage2<ST_BF16R> : Storage2<ST_BF16> {};
 
+// a + v for a 16-bit v, widened inside the add: the widening is exact, so
+// the result has the bits of converting v first and adding in FP32, with
+// one instruction instead of two
+__device__ __forceinline__ float add_w(float a, __half v) {
+  float d;
+  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(v)), "f"(a));
+  return d;
+}
+__device__ __forceinline__ float add_w(float a, __nv_bfloat16 v) {
+  float d;
+  asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(v)), "f"(a));
+  return d;
+}
+__device__ __forceinline__ __half lo16(__half2 v) { return __low2half(v); }
+__device__ __forceinline__ __half hi16(__half2 v) { return __high2half(v); }
+__device__ __forceinline__ __nv_bfloat16 lo16(__nv_bfloat162 v) { return __low2bfloat16(v); }
+__device__ __forceinline__ __nv_bfloat16 hi16(__nv_bfloat162 v) { return __high2bfloat16(v); }
+
 // Sum of the Q staged values of one cell (or of a pair of cells), in one
 // fixed order for the scalar and the paired form: the same cell gets the
 // same rho whether its own CTA or a neighbour's halo computes it.
@@ -110,6 +128,37 @@ __device__ __forceinline__ V sum_q(Ld ld) {
   }
   if constexpr (Q % 2 == 1) a = addv(a, ld(Q - 1));
   return addv(a, b);
+}
+// The same sums from 16-bit stored values, each widened inside its add
+// (0 + v is v exactly, so the bits are those of sum_q on converted values):
+// one cell, and a pair of cells from packed pairs.
+template <int Q, class Ld>
+__device__ __forceinline__ float sum_q_w1(Ld ld) {
+  float a = 0.0f, b = 0.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (i % 2 == 0)
+      a = add_w(a, ld(i));
+    else
+      b = add_w(b, ld(i));
+  }
+  return a + b;
+}
+template <int Q, class Ld>
+__device__ __forceinline__ float2 sum_q_w2(Ld ld) {
+  float ax = 0.0f, ay = 0.0f, bx = 0.0f, by = 0.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const auto v = ld(i);
+    if (i % 2 == 0) {
+      ax = add_w(ax, lo16(v));
+      ay = add_w(ay, hi16(v));
+    } else {
+      bx = add_w(bx, lo16(v));
+      by = add_w(by, hi16(v));
+    }
+  }
+  return __fadd2_rn(make_float2(ax, ay), make_float2(bx, by));
 }
 
 template <int LAT, int ST, int BX_, int BY_, int NS_>
@@ -313,9 +362,11 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
 #pragma unroll
         for (int i = 0; i < Q; ++i) nxt[i] = main2[(i * BY + ty) * TPX + tp];
       }
-      const float2 r2 = sum_q<Q, float2>([&](int i) {
-        return S2::load(KEEP ? nxt[i] : main2[(i * BY + ty) * TPX + tp]);
-      });
+      float2 r2;
+      if constexpr (sizeof(T) == 2)
+        r2 = sum_q_w2<Q>([&](int i) { return KEEP ? nxt[i] : main2[(i * BY + ty) * TPX + tp]; });
+      else
+        r2 = sum_q<Q, float2>([&](int i) { return S2::load(main2[(i * BY + ty) * TPX + tp]); });
       const float2 ps = psi_x2(add2(f2(rho_ref), r2), rho0, inv_rho0);
       *reinterpret_cast<float2 *>(rN + c0) = ps;
       rS[c0 - 1] = ps.x;
@@ -326,14 +377,22 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
       if (h_pair) {
         const T2 *b2 = reinterpret_cast<const T2 *>(st + h_off);
         const int ps2 = h_pstride / 2;
-        const float2 r2 = sum_q<Q, float2>([&](int i) { return S2::load(b2[i * ps2]); });
+        float2 r2;
+        if constexpr (sizeof(T) == 2)
+          r2 = sum_q_w2<Q>([&](int i) { return b2[i * ps2]; });
+        else
+          r2 = sum_q<Q, float2>([&](int i) { return S2::load(b2[i * ps2]); });
         const float2 ps = psi_x2(add2(f2(rho_ref), r2), rho0, inv_rho0);
         *reinterpret_cast<float2 *>(rN + h_j) = ps;
         rS[h_j - 1] = ps.x;
         rS[h_j] = ps.y;
       } else {
         const T *b1 = reinterpret_cast<const T *>(st + h_off);
-        const float r = sum_q<Q, float>([&](int i) { return S1::load(b1[i * h_pstride]); });
+        float r;
+        if constexpr (sizeof(T) == 2)
+          r = sum_q_w1<Q>([&](int i) { return b1[i * h_pstride]; });
+        else
+          r = sum_q<Q, float>([&](int i) { return S1::load(b1[i * h_pstride]); });
         rS[h_j - 1] = psi_x2(rho_ref + r, rho0, inv_rho0);  // N of side cells is never read
       }
     }
