@@ -108,6 +108,17 @@ __device__ __forceinline__ float add_w(float a, __nv_bfloat16 v) {
   asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(v)), "f"(a));
   return d;
 }
+// v - c for a 16-bit v, widened inside the subtraction (exact widening)
+__device__ __forceinline__ float sub_w(__half v, float c) {
+  float d;
+  asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(v)), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float sub_w(__nv_bfloat16 v, float c) {
+  float d;
+  asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(v)), "f"(c));
+  return d;
+}
 __device__ __forceinline__ __half lo16(__half2 v) { return __low2half(v); }
 __device__ __forceinline__ __half hi16(__half2 v) { return __high2half(v); }
 __device__ __forceinline__ __nv_bfloat16 lo16(__nv_bfloat162 v) { return __low2bfloat16(v); }
@@ -484,7 +495,13 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
           constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-          const float2 d = sub2(S2::load(cur[i]), S2::load(cur[o]));
+          float2 d;
+          if constexpr (sizeof(T) == 2) {
+            const float2 vo = S2::load(cur[o]);
+            d = make_float2(sub_w(lo16(cur[i]), vo.x), sub_w(hi16(cur[i]), vo.y));
+          } else {
+            d = sub2(S2::load(cur[i]), S2::load(cur[o]));
+          }
           jx = cacc2<cx>(jx, d);
           jy = cacc2<cy>(jy, d);
           jz = cacc2<cz>(jz, d);
