@@ -59,7 +59,7 @@ NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 4): 277.8e6,
                           ("d3q19_foam_128", "f32", 25): 277.57e6,
                           ("d3q19_foam_128", "f64", 6): 626.2e6,
                           ("d3q19_foam_512", "f32", 16): 8 * 2534.04e6,
-                          ("d3q19_foam_512", "f16", 24): 8 * 1272.32e6}
+                          ("d3q19_foam_512", "f16", 24): 8 * 1269.58e6}
 # FP64 storage: the step kernel is bound by the FP64 pipe, not by HBM.  FP64
 # operations per lattice update of its D3Q19 kernel, DADD + DMUL + 2 DFMA as
 # ncu counts them on the 128^3 case (146 + 71 + 2 x 332).  The peak is
