@@ -87,14 +87,16 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
   }
   __syncthreads();
 
-#pragma unroll 1
-  for (int s = 0; s < S; ++s) {
+  // steps unrolled, so that each phase runs over exactly its window with
+  // compile-time extents
+  static_for<S>([&](auto sc) {
+    constexpr int s = decltype(sc)::value;
     // ---- psi on the valid cells [2s, R - 2s)
     {
-      const int lo = 2 * s, hx = RX - 2 * s, hz = RZ - 2 * s;
-      for (int r = tid; r < RC; r += NT) {
-        const int rz = r / RX, rx = r - rz * RX;
-        if (rx < lo || rx >= hx || rz < lo || rz >= hz) continue;
+      constexpr int lo = 2 * s, wx = RX - 4 * s, wz = RZ - 4 * s;
+      for (int c = tid; c < wx * wz; c += NT) {
+        const int cz = c / wx;
+        const int r = (lo + cz) * RX + lo + (c - cz * wx);
         float2 s2;
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
@@ -108,10 +110,10 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
     __syncthreads();
     // ---- collide the cells [2s + 1, R - 2s - 1) and push into nxt
     {
-      const int lo = 2 * s + 1, hx = RX - 2 * s - 1, hz = RZ - 2 * s - 1;
-      for (int r = tid; r < RC; r += NT) {
-        const int rz = r / RX, rx = r - rz * RX;
-        if (rx < lo || rx >= hx || rz < lo || rz >= hz) continue;
+      constexpr int lo = 2 * s + 1, wx = RX - 4 * s - 2, wz = RZ - 4 * s - 2;
+      for (int c = tid; c < wx * wz; c += NT) {
+        const int cz = c / wx;
+        const int r = (lo + cz) * RX + lo + (c - cz * wx);
         float2 cur2[L::NP];
         float2 s2;
         static_for<L::NP>([&](auto kc) {
@@ -162,7 +164,7 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
     float *t = cur;
     cur = nxt;
     nxt = t;
-  }
+  });
 
   // ---- store the tile (valid after S steps), clipped to the domain
   for (int c = tid; c < 9 * K::TZ * K::TX; c += NT) {
