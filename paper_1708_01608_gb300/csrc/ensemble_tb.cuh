@@ -49,6 +49,44 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Paired FP32 operations over two cells (vertical neighbours), each lane the
+// scalar operation of the one-cell march
+__device__ __forceinline__ float2 tb_f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 tb_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as a + (-b): negation is exact, so the lanes are the scalar a - b
+__device__ __forceinline__ float2 tb_sub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 tb_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 tb_fma(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
+}
+// acc + c v for a velocity component c in {-1, 0, 1} (cacc per lane)
+template <int CC>
+__device__ __forceinline__ float2 tb_acc(float2 acc, float2 v) {
+  if constexpr (CC > 0) return tb_add(acc, v);
+  else if constexpr (CC < 0) return tb_sub(acc, v);
+  else return acc;
+}
+// acc + c w v (cfma per lane)
+template <int CC>
+__device__ __forceinline__ float2 tb_cfma(float2 acc, float w, float2 v) {
+  if constexpr (CC > 0) return tb_fma(tb_f2(w), v, acc);
+  else if constexpr (CC < 0) return tb_fma(tb_f2(-w), v, acc);
+  else return acc;
+}
+// c.u (cdot per lane)
+template <int A, int B, int Z>
+__device__ __forceinline__ float2 tb_dot(float2 x, float2 y, float2 z) {
+  float2 r;
+  if constexpr (A != 0) r = A > 0 ? x : make_float2(-x.x, -x.y);
+  else if constexpr (B != 0) r = B > 0 ? y : make_float2(-y.x, -y.y);
+  else r = Z > 0 ? z : make_float2(-z.x, -z.y);
+  if constexpr (A != 0 && B != 0) r = B > 0 ? tb_add(r, y) : tb_sub(r, y);
+  if constexpr ((A != 0 || B != 0) && Z != 0) r = Z > 0 ? tb_add(r, z) : tb_sub(r, z);
+  return r;
+}
+
 template <class K, int NT>
 __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
   using L = Lattice<D2Q9>;
@@ -91,73 +129,96 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
   // compile-time extents
   static_for<S>([&](auto sc) {
     constexpr int s = decltype(sc)::value;
-    // ---- psi on the valid cells [2s, R - 2s)
+    // ---- psi on the valid cells [2s, R - 2s), two cells (rows r, r + RX)
+    // per thread; wz is even
     {
       constexpr int lo = 2 * s, wx = RX - 4 * s, wz = RZ - 4 * s;
-      for (int c = tid; c < wx * wz; c += NT) {
-        const int cz = c / wx;
-        const int r = (lo + cz) * RX + lo + (c - cz * wx);
-        float2 s2;
+      static_assert(wz % 2 == 0, "windows hold whole pairs of rows");
+      for (int c = tid; c < wx * (wz / 2); c += NT) {
+        const int pz = c / wx;
+        const int r = (lo + 2 * pz) * RX + lo + (c - pz * wx);
+        auto g = [&](int i) { return make_float2(cur[i * RC + r], cur[i * RC + r + RX]); };
+        // the one-cell march's pair sums: i-directions and o-directions apart
+        float2 sI, sO;
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
-          const float2 v = make_float2(cur[i * RC + r], cur[o * RC + r]);
-          s2 = k2 == 0 ? v : __fadd2_rn(s2, v);
+          sI = k2 == 0 ? g(i) : tb_add(sI, g(i));
+          sO = k2 == 0 ? g(o) : tb_add(sO, g(o));
         });
-        const float rho = (s2.x + s2.y) + cur[r];
-        psi[r] = psi_of(rho_ref + rho, rho0, inv_rho0);
+        const float2 rho = tb_add(tb_add(sI, sO), g(0));
+        psi[r] = psi_of(rho_ref + rho.x, rho0, inv_rho0);
+        psi[r + RX] = psi_of(rho_ref + rho.y, rho0, inv_rho0);
       }
     }
     __syncthreads();
-    // ---- collide the cells [2s + 1, R - 2s - 1) and push into nxt
+    // ---- collide the cells [2s + 1, R - 2s - 1) and push into nxt, two
+    // cells per thread
     {
       constexpr int lo = 2 * s + 1, wx = RX - 4 * s - 2, wz = RZ - 4 * s - 2;
-      for (int c = tid; c < wx * wz; c += NT) {
-        const int cz = c / wx;
-        const int r = (lo + cz) * RX + lo + (c - cz * wx);
-        float2 cur2[L::NP];
-        float2 s2;
+      static_assert(wz % 2 == 0, "windows hold whole pairs of rows");
+      for (int c = tid; c < wx * (wz / 2); c += NT) {
+        const int pz = c / wx;
+        const int r = (lo + 2 * pz) * RX + lo + (c - pz * wx);
+        auto g = [&](int i) { return make_float2(cur[i * RC + r], cur[i * RC + r + RX]); };
+        auto psi2 = [&](int i) {
+          const int q = r + L::cz(i) * RX + L::cx(i);
+          return make_float2(psi[q], psi[q + RX]);
+        };
+        float2 gI[L::NP], gO[L::NP];
+        float2 sI, sO;
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
-          cur2[k2] = make_float2(cur[i * RC + r], cur[o * RC + r]);
-          s2 = k2 == 0 ? cur2[k2] : __fadd2_rn(s2, cur2[k2]);
+          gI[k2] = g(i);
+          gO[k2] = g(o);
+          sI = k2 == 0 ? gI[k2] : tb_add(sI, gI[k2]);
+          sO = k2 == 0 ? gO[k2] : tb_add(sO, gO[k2]);
         });
-        const float R = (s2.x + s2.y) + cur[r];
-        auto psi_at = [&](int i) -> float { return psi[r + L::cz(i) * RX + L::cx(i)]; };
-        float jx = -0.0f, jy = -0.0f, jz = -0.0f, sx = -0.0f, sy = -0.0f, sz = -0.0f;
+        const float2 R = tb_add(tb_add(sI, sO), g(0));
+        float2 jx = tb_f2(-0.0f), jy = tb_f2(-0.0f), jz = tb_f2(-0.0f);
+        float2 sx = tb_f2(-0.0f), sy = tb_f2(-0.0f), sz = tb_f2(-0.0f);
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
           constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-          const float d = cur2[k2].x - cur2[k2].y;
-          jx = cacc<cx>(jx, d);
-          jy = cacc<cy>(jy, d);
-          jz = cacc<cz>(jz, d);
-          const float dps = psi_at(i) - psi_at(o), w = (float)L::w(i);
-          sx = cfma<cx>(sx, w, dps);
-          sy = cfma<cy>(sy, w, dps);
-          sz = cfma<cz>(sz, w, dps);
+          const float2 d = tb_sub(gI[k2], gO[k2]);
+          jx = tb_acc<cx>(jx, d);
+          jy = tb_acc<cy>(jy, d);
+          jz = tb_acc<cz>(jz, d);
+          const float2 dps = tb_sub(psi2(i), psi2(o));
+          const float w = (float)L::w(i);
+          sx = tb_cfma<cx>(sx, w, dps);
+          sy = tb_cfma<cy>(sy, w, dps);
+          sz = tb_cfma<cz>(sz, w, dps);
         });
-        const float rho = rho_ref + R;
-        const float gp = -G * psi[r];
-        const float ir = __fdividef(1.0f, rho);
-        const float ux = (jx + tau * (gp * sx)) * ir, uy = (jy + tau * (gp * sy)) * ir,
-                    uz = (jz + tau * (gp * sz)) * ir;
-        const float Kc = fmaf(rho * -1.5f, ux * ux + uy * uy + uz * uz, R);
-        const float wK[2] = {cW[0] * Kc, cW[1] * Kc};
-        const float2 om1_2 = make_float2(om1, om1);
-        float2 moved2;
+        const float2 rho = tb_add(tb_f2(rho_ref), R);
+        const float2 gp = tb_mul(tb_f2(-G), make_float2(psi[r], psi[r + RX]));
+        const float2 ir = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
+        const float2 ux = tb_mul(tb_fma(tb_f2(tau), tb_mul(gp, sx), jx), ir);
+        const float2 uy = tb_mul(tb_fma(tb_f2(tau), tb_mul(gp, sy), jy), ir);
+        const float2 uz = tb_mul(tb_fma(tb_f2(tau), tb_mul(gp, sz), jz), ir);
+        const float2 Kc =
+            tb_fma(tb_mul(rho, tb_f2(-1.5f)), tb_fma(uz, uz, tb_fma(uy, uy, tb_mul(ux, ux))), R);
+        const float2 wK[2] = {tb_mul(tb_f2(cW[0]), Kc), tb_mul(tb_f2(cW[1]), Kc)};
+        float2 mI, mO;
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
           constexpr int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
-          const float cu = cdot<L::cx(i), L::cy(i), L::cz(i)>(ux, uy, uz);
-          const float a = rho * cu;
-          const float A = fmaf(a, c45[wc] * cu, wK[wc]);
-          const float B = c3[wc] * a;
-          const float2 g = __ffma2_rn(om1_2, cur2[k2], make_float2(A + B, A - B));
-          moved2 = k2 == 0 ? g : __fadd2_rn(moved2, g);
-          nxt[i * RC + r + L::cz(i) * RX + L::cx(i)] = g.x;
-          nxt[o * RC + r + L::cz(o) * RX + L::cx(o)] = g.y;
+          const float2 cu = tb_dot<L::cx(i), L::cy(i), L::cz(i)>(ux, uy, uz);
+          const float2 a = tb_mul(rho, cu);
+          const float2 A = tb_fma(a, tb_mul(tb_f2(c45[wc]), cu), wK[wc]);
+          const float2 gi = tb_fma(tb_f2(om1), gI[k2], tb_fma(tb_f2(c3[wc]), a, A));
+          const float2 go = tb_fma(tb_f2(om1), gO[k2], tb_fma(tb_f2(-c3[wc]), a, A));
+          mI = k2 == 0 ? gi : tb_add(mI, gi);
+          mO = k2 == 0 ? go : tb_add(mO, go);
+          const int di = i * RC + r + L::cz(i) * RX + L::cx(i);
+          const int dq = o * RC + r + L::cz(o) * RX + L::cx(o);
+          nxt[di] = gi.x;
+          nxt[di + RX] = gi.y;
+          nxt[dq] = go.x;
+          nxt[dq + RX] = go.y;
         });
-        nxt[r] = R - (moved2.x + moved2.y);
+        const float2 g0 = tb_sub(R, tb_add(mI, mO));
+        nxt[r] = g0.x;
+        nxt[r + RX] = g0.y;
       }
     }
     __syncthreads();

@@ -452,9 +452,11 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
           const C rho = rho_ref + R;
           const C gp = -G * p0[c0];
           const C ir = __fdividef((C)1, rho);
-          const C ux = (jx + tau * (gp * sx)) * ir, uy = (jy + tau * (gp * sy)) * ir,
-                  uz = (jz + tau * (gp * sz)) * ir;
-          const C K = fmaf(rho * (C)-1.5, ux * ux + uy * uy + uz * uz, R);
+          // every FMA written out, so that the temporally blocked ensemble
+          // kernel can repeat this arithmetic bit for bit
+          const C ux = fmaf(tau, gp * sx, jx) * ir, uy = fmaf(tau, gp * sy, jy) * ir,
+                  uz = fmaf(tau, gp * sz, jz) * ir;
+          const C K = fmaf(rho * (C)-1.5, fmaf(uz, uz, fmaf(uy, uy, ux * ux)), R);
           const C wK[2] = {cW[0] * K, cW[1] * K};
           const float2 om1_2 = make_float2(om1, om1);
           // relax and push; SITE adds the blowing agent w_i dm to every
@@ -475,9 +477,10 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
               const C cu = cdot<L::cx(i), L::cy(i), L::cz(i)>(ux, uy, uz);
               const C a = rho * cu;
               const C A = fmaf(a, c45[wc] * cu, wK[wc]);
-              const C B = c3[wc] * a;
-              // (g_i, g_o) = (1 - omega) (g_i, g_o) + (A + B, A - B): one paired FMA
-              const float2 g = __ffma2_rn(om1_2, cur2[k2], make_float2(A + B, A - B));
+              // (g_i, g_o) = (1 - omega) (g_i, g_o) + (A + B, A - B), B = c3 a,
+              // with A +- B as FMAs: one paired FMA
+              const float2 g = __ffma2_rn(
+                  om1_2, cur2[k2], make_float2(fmaf(c3[wc], a, A), fmaf(-c3[wc], a, A)));
               moved2 = k2 == 0 ? g : __fadd2_rn(moved2, g);
               const C gi = g.x, go = g.y;
               if (SITE) {
