@@ -534,9 +534,9 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
             const float2 cu = cdot2<L::cx(i), L::cy(i), L::cz(i)>(ux, uy, uz);
             const float2 a = mul2(rho, cu);
             const float2 A = fma2(a, mul2(f2(c45[wc]), cu), wK[wc]);
-            const float2 Bv = mul2(f2(c3[wc]), a);
-            const float2 gi = fma2(om1_2, S2::load(cur[i]), add2(A, Bv));
-            const float2 go = fma2(om1_2, S2::load(cur[o]), sub2(A, Bv));
+            // A +- B with B = 3 omega w_i a, as FMAs (the one-cell march's form)
+            const float2 gi = fma2(om1_2, S2::load(cur[i]), fma2(f2(c3[wc]), a, A));
+            const float2 go = fma2(om1_2, S2::load(cur[o]), fma2(f2(-c3[wc]), a, A));
             moved = add2(moved, add2(gi, go));
             if (SITE) {
               put(std::integral_constant<int, i>{}, fma2(f2((float)L::w(i)), dmc, gi));
