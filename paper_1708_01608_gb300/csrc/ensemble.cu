@@ -12,8 +12,8 @@
 // replays, and within a replay their launches return at once.  Launch
 // forms:
 //   - per-step launches, one per tile class: each CTA reads a work item
-//     (domain, x tile, chunk of rows) and runs the single-lattice fused
-//     kernel's column march with the domain's TMA descriptors;
+//     (domain, x tile, chunk of rows) and runs the single-lattice x-pair
+//     column march (two cells per thread) with the domain's TMA descriptors;
 //   - temporally blocked launches (ensemble_tb.cuh): a CTA advances a tile
 //     with a 2 S-cell halo S steps in shared memory;
 //   - persistent cooperative launches, in which each CTA keeps its work item
@@ -32,6 +32,7 @@
 #include "internal.h"
 #include "lattice.cuh"
 #include "step_fused.cuh"
+#include "step_fused_x2.cuh"
 
 namespace sclbm {
 namespace {
@@ -92,7 +93,7 @@ __device__ __forceinline__ MarchArgs ens_march_args(const EnsDomain &D, const in
 }
 
 template <int BX, int NS>
-__global__ void __launch_bounds__(BX)
+__global__ void __launch_bounds__(BX / 2)
     ens_step_kernel(const EnsDomain *doms, const FusedMaps *mapsA, const FusedMaps *mapsB,
                     const int4 *items, const int *count, const EnsState *st, int parity) {
   if ((int)blockIdx.x >= *count) return;
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(BX)
   MarchArgs m = ens_march_args(D, it, parity ? &mapsB[it.x] : &mapsA[it.x]);
   float *out = parity ? D.latA : D.latB;
   const int64_t ps = D.popstride;
-  fused_barriers_init<D2Q9, ST_F32, BX, 1, NS>(m);
+  fused_barriers_init_k<FusedK2<D2Q9, ST_F32, BX, 1, NS>>(m);
   // programmatic dependent launch within a class chain: the work item and
   // the domain record are never written by a step, the lattices are read
   // and written only after the previous step has completed
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(BX)
   if (!st[it.x].active) return;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   uint32_t kb = 0;
-  fused_march<D2Q9, ST_F32, BX, 1, NS>(m, [&](int i) { return out + i * ps; }, kb);
+  fused_march_x2<D2Q9, ST_F32, BX, 1, NS>(m, [&](int i) { return out + i * ps; }, kb);
 }
 
 // ---- temporally blocked steps (S steps per launch) ---------------------------
@@ -426,7 +427,7 @@ using EnsRunK = FusedK<D2Q9, ST_F32, ENS_RUN_BX, 1, ENS_RUN_NS>;
 template <int BX, int NS>
 cudaError_t ens_prepare_t() {
   return cudaFuncSetAttribute(ens_step_kernel<BX, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              FusedK<D2Q9, ST_F32, BX, 1, NS>::SMEM);
+                              FusedK2<D2Q9, ST_F32, BX, 1, NS>::SMEM);
 }
 template <int BX, int NS>
 cudaError_t ens_launch_t(int grid, const EnsDomain *doms, const FusedMaps *a, const FusedMaps *b,
@@ -434,8 +435,8 @@ cudaError_t ens_launch_t(int grid, const EnsDomain *doms, const FusedMaps *a, co
                   cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)BX);
-  cfg.dynamicSmemBytes = (size_t)FusedK<D2Q9, ST_F32, BX, 1, NS>::SMEM;
+  cfg.blockDim = dim3((unsigned)(BX / 2));
+  cfg.dynamicSmemBytes = (size_t)FusedK2<D2Q9, ST_F32, BX, 1, NS>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -12,10 +12,9 @@
 // tile itself is valid and is stored.  A launch reads one lattice and
 // writes the other, as a single step does.
 //
-// The per-cell arithmetic is the fused march's FP32 offset path, operation
-// for operation (pair sums of opposite populations, the same FMA and
-// fast-division forms), so the populations are bit-identical to those of S
-// single-step launches.  Shared memory: two population buffers and a psi
+// The per-cell arithmetic is the fused marches' FP32 offset path, operation
+// for operation (the same density order, FMA and fast-division forms), so the
+// populations are bit-identical to those of S single-step launches.  Shared memory: two population buffers and a psi
 // plane of the loaded region, 19 floats per cell.
 #pragma once
 
@@ -74,6 +73,18 @@ __device__ __forceinline__ float2 tb_cfma(float2 acc, float w, float2 v) {
   if constexpr (CC > 0) return tb_fma(tb_f2(w), v, acc);
   else if constexpr (CC < 0) return tb_fma(tb_f2(-w), v, acc);
   else return acc;
+}
+// density of two cells in the x-pair kernel's order (rho_chain per lane)
+template <class Ld>
+__device__ __forceinline__ float2 tb_rho(Ld g) {
+  float2 a = g(0), b = g(1);
+#pragma unroll
+  for (int i = 2; i + 1 < 9; i += 2) {
+    a = tb_add(a, g(i));
+    b = tb_add(b, g(i + 1));
+  }
+  a = tb_add(a, g(8));
+  return tb_add(a, b);
 }
 // c.u (cdot per lane)
 template <int A, int B, int Z>
@@ -138,14 +149,7 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
         const int pz = c / wx;
         const int r = (lo + 2 * pz) * RX + lo + (c - pz * wx);
         auto g = [&](int i) { return make_float2(cur[i * RC + r], cur[i * RC + r + RX]); };
-        // the one-cell march's pair sums: i-directions and o-directions apart
-        float2 sI, sO;
-        static_for<L::NP>([&](auto kc) {
-          constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
-          sI = k2 == 0 ? g(i) : tb_add(sI, g(i));
-          sO = k2 == 0 ? g(o) : tb_add(sO, g(o));
-        });
-        const float2 rho = tb_add(tb_add(sI, sO), g(0));
+        const float2 rho = tb_rho(g);
         psi[r] = psi_of(rho_ref + rho.x, rho0, inv_rho0);
         psi[r + RX] = psi_of(rho_ref + rho.y, rho0, inv_rho0);
       }
@@ -165,15 +169,12 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
           return make_float2(psi[q], psi[q + RX]);
         };
         float2 gI[L::NP], gO[L::NP];
-        float2 sI, sO;
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
           gI[k2] = g(i);
           gO[k2] = g(o);
-          sI = k2 == 0 ? gI[k2] : tb_add(sI, gI[k2]);
-          sO = k2 == 0 ? gO[k2] : tb_add(sO, gO[k2]);
         });
-        const float2 R = tb_add(tb_add(sI, sO), g(0));
+        const float2 R = tb_rho(g);
         float2 jx = tb_f2(-0.0f), jy = tb_f2(-0.0f), jz = tb_f2(-0.0f);
         float2 sx = tb_f2(-0.0f), sy = tb_f2(-0.0f), sz = tb_f2(-0.0f);
         static_for<L::NP>([&](auto kc) {
@@ -198,7 +199,7 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
         const float2 Kc =
             tb_fma(tb_mul(rho, tb_f2(-1.5f)), tb_fma(uz, uz, tb_fma(uy, uy, tb_mul(ux, ux))), R);
         const float2 wK[2] = {tb_mul(tb_f2(cW[0]), Kc), tb_mul(tb_f2(cW[1]), Kc)};
-        float2 mI, mO;
+        float2 m = tb_f2(-0.0f);  // sum over the pairs of (g_i + g_o)
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
           constexpr int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
@@ -207,8 +208,7 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
           const float2 A = tb_fma(a, tb_mul(tb_f2(c45[wc]), cu), wK[wc]);
           const float2 gi = tb_fma(tb_f2(om1), gI[k2], tb_fma(tb_f2(c3[wc]), a, A));
           const float2 go = tb_fma(tb_f2(om1), gO[k2], tb_fma(tb_f2(-c3[wc]), a, A));
-          mI = k2 == 0 ? gi : tb_add(mI, gi);
-          mO = k2 == 0 ? go : tb_add(mO, go);
+          m = tb_add(m, tb_add(gi, go));
           const int di = i * RC + r + L::cz(i) * RX + L::cx(i);
           const int dq = o * RC + r + L::cz(o) * RX + L::cx(o);
           nxt[di] = gi.x;
@@ -216,7 +216,7 @@ __device__ __forceinline__ void ens_tb_tile(const TbDomain &D, int x0, int z0) {
           nxt[dq] = go.x;
           nxt[dq + RX] = go.y;
         });
-        const float2 g0 = tb_sub(R, tb_add(mI, mO));
+        const float2 g0 = tb_sub(R, m);
         nxt[r] = g0.x;
         nxt[r + RX] = g0.y;
       }

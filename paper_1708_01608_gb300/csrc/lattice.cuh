@@ -155,9 +155,10 @@ inline size_t storage_bytes(int st) { return st == ST_F64 ? 8 : (st == ST_F32 ? 
 __device__ __forceinline__ double psi_of(double rho, double rho0, double inv_rho0) {
   return rho0 * (1.0 - exp(-rho * inv_rho0));
 }
-// (FP32: the hardware exponential, a few ulp, far below FP32 storage noise)
+// (FP32: the hardware exponential, a few ulp, far below FP32 storage noise;
+// evaluated as rho0 - rho0 e in one FMA, the form every FP32 kernel uses)
 __device__ __forceinline__ float psi_of(float rho, float rho0, float inv_rho0) {
-  return rho0 * (1.0f - __expf(-rho * inv_rho0));
+  return fmaf(-rho0, __expf(rho * -inv_rho0), rho0);
 }
 
 // ---- compile-time helpers of the FP32 collision ----------------------------

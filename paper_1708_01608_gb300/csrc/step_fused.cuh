@@ -116,6 +116,21 @@ __device__ __forceinline__ void fused_barriers_init(const MarchArgs &m) {
   fused_barriers_init_k<FusedK<LAT, ST, BX, BY, NS>>(m);
 }
 
+// Sum of the Q staged values of one cell in the order of the x-pair kernel's
+// sum_q (even indices and odd indices in two chains, then their sum), so that
+// the one-cell and the x-pair kernels give a cell the same density bits.
+template <int Q, class Ld>
+__device__ __forceinline__ float rho_chain(Ld ld) {
+  float a = ld(0), b = ld(1);
+#pragma unroll
+  for (int i = 2; i + 1 < Q; i += 2) {
+    a = a + ld(i);
+    b = b + ld(i + 1);
+  }
+  if constexpr (Q % 2 == 1) a = a + ld(Q - 1);
+  return a + b;
+}
+
 // The march of one CTA over planes zs..ze-1 of one column: TMA staging, psi
 // ring, collision, push.  out_pop(i) returns the base of population i of the
 // output lattice.  kb counts the planes this CTA staged before (stage slot
@@ -315,15 +330,13 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
           rho += v;
         }
       } else {
-        float2 s2;
         static_for<L::NP>([&](auto kc) {
           constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
           nxt2[k2] = make_float2(S::load(mainb[(i * BY + ty) * BX + tx]),
                                  S::load(mainb[(o * BY + ty) * BX + tx]));
-          s2 = k2 == 0 ? nxt2[k2] : __fadd2_rn(s2, nxt2[k2]);
         });
         nxt0 = S::load(mainb[ty * BX + tx]);
-        rho = (s2.x + s2.y) + nxt0;
+        rho = rho_chain<Q>([&](int i) { return S::load(mainb[(i * BY + ty) * BX + tx]); });
       }
       rk[(ty + HY) * PW + tx + 1] = psi_of(rho_ref + rho, rho0, inv_rho0);
       Rnxt = rho;
@@ -335,13 +348,7 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
 #pragma unroll
         for (int i = 0; i < Q; ++i) rho += S::load(b[i * h_pstride]);
       } else {
-        float2 s2;
-        static_for<L::NP>([&](auto kc) {
-          constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
-          const float2 v = make_float2(S::load(b[i * h_pstride]), S::load(b[o * h_pstride]));
-          s2 = k2 == 0 ? v : __fadd2_rn(s2, v);
-        });
-        rho = (s2.x + s2.y) + S::load(b[0]);
+        rho = rho_chain<Q>([&](int i) { return S::load(b[i * h_pstride]); });
       }
       rk[h_slot] = psi_of(rho_ref + rho, rho0, inv_rho0);
     }
@@ -470,7 +477,7 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
           };
           auto relax_push = [&](auto with_site) {
             constexpr bool SITE = decltype(with_site)::value;
-            float2 moved2;
+            C moved = -0.0f;  // sum over the pairs of (g_i + g_o), as the x-pair kernel
             static_for<L::NP>([&](auto kc) {
               constexpr int k2 = decltype(kc)::value, i = L::rep(k2), o = L::opp(i);
               constexpr int wc = L::w(i) == L::w(L::rep(0)) ? 0 : 1;
@@ -481,7 +488,7 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
               // with A +- B as FMAs: one paired FMA
               const float2 g = __ffma2_rn(
                   om1_2, cur2[k2], make_float2(fmaf(c3[wc], a, A), fmaf(-c3[wc], a, A)));
-              moved2 = k2 == 0 ? g : __fadd2_rn(moved2, g);
+              moved = moved + (g.x + g.y);
               const C gi = g.x, go = g.y;
               if (SITE) {
                 put(dst(i), gi + (C)L::w(i) * dmc);
@@ -491,7 +498,7 @@ __device__ __forceinline__ bool fused_march(const MarchArgs &m, OutPop out_pop, 
                 put(dst(o), go);
               }
             });
-            const C g0 = R - (moved2.x + moved2.y);
+            const C g0 = R - moved;
             put(dst(0), SITE ? g0 + (C)L::w(0) * dmc : g0);
           };
           if (site)
