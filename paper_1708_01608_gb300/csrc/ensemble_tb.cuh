@@ -14,8 +14,9 @@
 //
 // The per-cell arithmetic is the fused marches' FP32 offset path, operation
 // for operation (the same density order, FMA and fast-division forms), so the
-// populations are bit-identical to those of S single-step launches.  Shared memory: two population buffers and a psi
-// plane of the loaded region, 19 floats per cell.
+// populations are bit-identical to those of S single-step launches.  Shared
+// memory: two population buffers and a psi plane of the loaded region, 19
+// floats per cell.
 #pragma once
 
 #include "lattice.cuh"
