@@ -108,7 +108,8 @@ typedef struct {
                            fused-kernel CTA skips the TMA copies of its
                            second staged plane, so that its bounded wait
                            (1 s) expires and lbm_sync reports LBM_ETIMEOUT;
-                           exercises the timeout path without a fault */
+                           exercises the timeout path without a fault.
+                           LBM_DEBUG_CONVERT_BEFORE_FMA: see below */
   double nucleus_radius; /* radius of the nuclei lbm_seed_bubbles samples
                             when given no bubble list (Sec. 3: random
                             nucleation sites); default 3 cells */
@@ -127,6 +128,11 @@ typedef struct {
 } lbm_config;
 
 #define LBM_DEBUG_WITHHOLD_TMA 1
+/* 16-bit storages: the x-pair kernels convert each stored value to FP32
+   before the relaxation's FMA even where 1 - omega is itself a 16-bit value
+   (they otherwise widen it inside the FMA); the results are the same bits,
+   which a test checks by comparing the two forms */
+#define LBM_DEBUG_CONVERT_BEFORE_FMA 2
 
 typedef struct {
   double x, y, z, r; /* centre (cell coordinates; z = 0 in 2-D) and radius */

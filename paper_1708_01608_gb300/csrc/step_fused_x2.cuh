@@ -119,6 +119,22 @@ __device__ __forceinline__ float sub_w(__nv_bfloat16 v, float c) {
   asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(v)), "f"(c));
   return d;
 }
+// a * v + c for 16-bit a and v, both widened inside the FMA: when a holds a
+// float exactly, the result has the bits of fmaf((float)a, (float)v, c)
+__device__ __forceinline__ float fma_w(__half a, __half v, float c) {
+  float d;
+  asm("fma.rn.f32.f16 %0, %1, %2, %3;"
+      : "=f"(d)
+      : "h"(__half_as_ushort(a)), "h"(__half_as_ushort(v)), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float fma_w(__nv_bfloat16 a, __nv_bfloat16 v, float c) {
+  float d;
+  asm("fma.rn.f32.bf16 %0, %1, %2, %3;"
+      : "=f"(d)
+      : "h"(__bfloat16_as_ushort(a)), "h"(__bfloat16_as_ushort(v)), "f"(c));
+  return d;
+}
 __device__ __forceinline__ __half lo16(__half2 v) { return __low2half(v); }
 __device__ __forceinline__ __half hi16(__half2 v) { return __high2half(v); }
 __device__ __forceinline__ __nv_bfloat16 lo16(__nv_bfloat162 v) { return __low2bfloat16(v); }
@@ -195,7 +211,9 @@ struct FusedK2 {
   static_assert(NS >= 2, "one stage is consumed while the next is summed");
 };
 
-template <int LAT, int ST, int BX, int BY, int NS, class OutPop>
+// OM16: 1 - omega is exactly a value of the 16-bit storage type, so the
+// relaxation's (1 - omega) g_i takes the stored g_i unconverted (fma_w)
+template <int LAT, int ST, int BX, int BY, int NS, bool OM16 = false, class OutPop>
 __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_pop, uint32_t &kb) {
   using K = FusedK2<LAT, ST, BX, BY, NS>;
   using B = typename K::B;
@@ -522,6 +540,8 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
         const float2 Kc = fma2(mul2(rho, f2(-1.5f)), uu, R);
         const float2 wK[2] = {mul2(f2(cW[0]), Kc), mul2(f2(cW[1]), Kc)};
         const float2 om1_2 = f2(om1);
+        [[maybe_unused]] T om1h;
+        if constexpr (OM16) om1h = S1::store(om1);
         // relax and push (offset form, as in the one-cell march):
         //   g_i* = (1 - omega) g_i + omega w_i (K + 4.5 rho (c.u)^2) + 3 omega w_i rho c.u
         // SITE adds w_i dm to every population of the site cell
@@ -535,8 +555,15 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
             const float2 a = mul2(rho, cu);
             const float2 A = fma2(a, mul2(f2(c45[wc]), cu), wK[wc]);
             // A +- B with B = 3 omega w_i a, as FMAs (the one-cell march's form)
-            const float2 gi = fma2(om1_2, S2::load(cur[i]), fma2(f2(c3[wc]), a, A));
-            const float2 go = fma2(om1_2, S2::load(cur[o]), fma2(f2(-c3[wc]), a, A));
+            const float2 Ai = fma2(f2(c3[wc]), a, A), Ao = fma2(f2(-c3[wc]), a, A);
+            float2 gi, go;
+            if constexpr (OM16) {
+              gi = make_float2(fma_w(om1h, lo16(cur[i]), Ai.x), fma_w(om1h, hi16(cur[i]), Ai.y));
+              go = make_float2(fma_w(om1h, lo16(cur[o]), Ao.x), fma_w(om1h, hi16(cur[o]), Ao.y));
+            } else {
+              gi = fma2(om1_2, S2::load(cur[i]), Ai);
+              go = fma2(om1_2, S2::load(cur[o]), Ao);
+            }
             moved = add2(moved, add2(gi, go));
             if (SITE) {
               put(std::integral_constant<int, i>{}, fma2(f2((float)L::w(i)), dmc, gi));
@@ -571,7 +598,7 @@ __device__ __forceinline__ bool fused_march_x2(const MarchArgs &m, OutPop out_po
   return true;
 }
 
-template <int LAT, int ST, int BX, int BY, int NS>
+template <int LAT, int ST, int BX, int BY, int NS, bool OM16 = false>
 __global__ void __launch_bounds__(BX / 2 * BY, BX / 2 * BY <= 256 ? 512 / (BX / 2 * BY) : 1)
     fused_step_kernel_x2(const __grid_constant__ FusedMaps tm, const StepArgs a, const int tiles_x,
                          const int tiles_y, const int zlen) {
@@ -582,8 +609,24 @@ __global__ void __launch_bounds__(BX / 2 * BY, BX / 2 * BY <= 256 ? 512 / (BX / 
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   uint32_t kb = 0;
-  fused_march_x2<LAT, ST, BX, BY, NS>(m, [&](int i) { return static_cast<T *>(a.out_pop[i]); },
-                                      kb);
+  fused_march_x2<LAT, ST, BX, BY, NS, OM16>(
+      m, [&](int i) { return static_cast<T *>(a.out_pop[i]); }, kb);
+}
+
+// 16-bit storage: does 1 - omega convert to the storage type exactly?
+template <int ST>
+bool om1_is_16bit(float omega) {
+  using T = typename Storage<ST>::T;
+  if constexpr (sizeof(T) != 2) {
+    (void)omega;
+    return false;
+  } else {
+    const float om1 = 1.0f - omega;
+    if constexpr (std::is_same_v<T, __half>)
+      return __half2float(__float2half_rn(om1)) == om1;
+    else
+      return __bfloat162float(__float2bfloat16_rn(om1)) == om1;
+  }
 }
 
 template <int LAT, int ST, int BX, int BY, int NS>
@@ -591,6 +634,11 @@ cudaError_t fused_x2_prepare_t(int *blocks_per_sm) {
   using K = FusedK2<LAT, ST, BX, BY, NS>;
   cudaError_t e = cudaFuncSetAttribute(fused_step_kernel_x2<LAT, ST, BX, BY, NS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  if constexpr (sizeof(typename Storage<ST>::T) == 2) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_step_kernel_x2<LAT, ST, BX, BY, NS, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  }
   if (e == cudaSuccess && blocks_per_sm)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         blocks_per_sm, fused_step_kernel_x2<LAT, ST, BX, BY, NS>, K::NT, K::SMEM);
@@ -611,6 +659,11 @@ cudaError_t fused_x2_launch_t(const FusedPlan &p, const StepArgs &a, const Fused
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if constexpr (sizeof(typename Storage<ST>::T) == 2) {
+    if (!(a.debug_flags & 2) && om1_is_16bit<ST>(a.omega_f))  // 2: LBM_DEBUG_CONVERT_BEFORE_FMA
+      return cudaLaunchKernelEx(&cfg, fused_step_kernel_x2<LAT, ST, BX, BY, NS, true>, tm, a,
+                                p.tiles_x, p.tiles_y, p.zlen);
+  }
   return cudaLaunchKernelEx(&cfg, fused_step_kernel_x2<LAT, ST, BX, BY, NS>, tm, a, p.tiles_x,
                             p.tiles_y, p.zlen);
 }

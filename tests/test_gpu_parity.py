@@ -643,6 +643,34 @@ def test_one_cell_and_pair_kernels_bit_identical(lbm, lat, ext, one, pair):
     assert (out[0] == out[1]).all()
 
 
+@pytest.mark.parametrize("storage,tile,tau", [("f16", 24, 0.8), ("bf16", 16, 1.0),
+                                              ("f16", 14, 0.8), ("f16r", 25, 0.8)])
+def test_pair_kernel_fma_forms_bit_identical(lbm, storage, tile, tau):
+    """16-bit storage, 1 - omega a 16-bit value (tau 0.8: -0.25; tau 1: 0):
+    the x-pair relaxation widens the stored g inside its FMA.  The form that
+    converts g to FP32 first (LBM_DEBUG_CONVERT_BEFORE_FMA) gives the same
+    bits after 200 steps with injection; and the widened form follows the
+    oracle within the storage's bound."""
+    nx, ny, nz = 136, 23, 9
+    bub = [[6, 5, 4, 3.0], [nx - 3, ny - 2, nz - 1, 2.5], [20, 14, 10, 3.5]]
+    out = []
+    for flags in (0, lbm.DEBUG_CONVERT_BEFORE_FMA):
+        L = lbm.Lattice("D3Q19", nx, ny, nz, tau=tau, G=-5.0, storage=RESID.get(storage, storage),
+                        kernel="fused", tile=tile, rho_ref=1.0, debug_flags=flags,
+                        mass_residual=storage in RESID)
+        L.seed_bubbles(np.array(bub, float), 2.0, 0.15, 2.0, 1e-3, 5)
+        L.inject([2e-3, 1e-3, 5e-4], [0.05, 0.2, 0.01])
+        L.step(200)
+        out.append(L.read("f"))
+        L.close()
+    assert (out[0] == out[1]).all()
+    fg, fo, bg, bo, L = run_pair(lbm, "D3Q19", nx, ny, nz, storage, "fused", tile, bub, 60,
+                                 tau=tau, rate=[2e-3, 1e-3, 5e-4], budget=[0.05, 0.2, 0.01])
+    assert rel_err(fg, fo) < TOL[storage], rel_err(fg, fo)
+    assert np.abs(bg - bo).max() < 1e-15
+    L.close()
+
+
 def _small_domains(noise=None):
     from paper_1708_01608_gb300.workloads import ENSEMBLE_256, ensemble_domains
     rec = dict(ENSEMBLE_256, gap=(4.0, 6.0), seed=11)
