@@ -258,9 +258,10 @@ def diagnostics(L):
 
 
 # kernels of one diagnostic interval (FP32 storage): scan + final (totals and
-# gas flags), union + compress (labels), site gather, film test (pressure of
-# its midpoints computed in place), census count + list
-DIAG_LAUNCHES = 8
+# gas flags), union + compress (labels), site gather, film test (one walk per
+# lattice line and axis, pressure of its midpoints computed in place), census
+# count + list
+DIAG_LAUNCHES = 10
 
 
 # The oracle's FP64 populations of a 512^3 or 768^3 lattice (20 GB, 68 GB)

@@ -81,7 +81,8 @@ struct lbm_ctx {
   // diagnostics
   DevBuf d_err, d_rho, d_p, d_tmp, d_j, d_u, d_labels, d_ncomp, d_part, d_tot, d_site_lab;
   // bubble census and per-point film test
-  DevBuf d_count, d_census, d_film_state, d_film_counts, d_film_rec, d_film_save;
+  DevBuf d_count, d_census, d_film_state, d_film_counts, d_film_rec, d_film_save, d_film_mids;
+  int64_t film_mid_queue = 0;  // capacity of d_film_mids (queued film midpoints)
   bool film_state_clear = false;  // d_film_state must be zeroed before use
   int64_t census_cap = 4096;       // device capacity of the census list (grows)
   int64_t film_mid_cap = 1 << 16;  // device capacity of the midpoint records (grows)
@@ -397,7 +398,7 @@ void lbm_destroy(lbm_ctx *c) {
                     &c->psi_scratch, &c->d_err, &c->d_rho, &c->d_p, &c->d_tmp, &c->d_j, &c->d_u,
                     &c->d_labels, &c->d_ncomp, &c->d_part, &c->d_tot, &c->d_site_lab,
                     &c->d_count, &c->d_census, &c->d_film_state, &c->d_film_counts,
-                    &c->d_film_rec, &c->d_film_save, &c->d_spread_groups,
+                    &c->d_film_rec, &c->d_film_save, &c->d_film_mids, &c->d_spread_groups,
                     &c->d_spread_sites, &c->d_spread_count, &c->d_dep};
   for (DevBuf *b : bufs) dfree(c, *b);
   hfree(c->h_err);
@@ -1106,12 +1107,18 @@ static lbm_status film_prepare(lbm_ctx *c, int32_t h_max, double eps_arm) {
   CKS(check_sticky(c));
   CKS(ensure_labels(c));
   CKS(ensure_diag(c));
-  CKS(dalloc(c, c->d_film_state, (size_t)c->N));
+  // whole 32-bit words: the midpoint pass sets bits with word atomics
+  const size_t state_bytes = ((size_t)c->N + 3) & ~(size_t)3;
+  CKS(dalloc(c, c->d_film_state, state_bytes));
   if (!c->film_state_clear) {
-    CK(cudaMemsetAsync(c->d_film_state.p, 0, (size_t)c->N, c->s));
+    CK(cudaMemsetAsync(c->d_film_state.p, 0, state_bytes, c->s));
     c->film_state_clear = true;
   }
-  CKS(dalloc(c, c->d_film_counts, 5 * sizeof(unsigned long long)));
+  CKS(dalloc(c, c->d_film_counts, FILM_COUNT_SLOTS * sizeof(unsigned long long)));
+  // queue of the line walks' midpoints: up to 2^20 (one per cell and axis at
+  // most); midpoints beyond it are taken inside the walks
+  c->film_mid_queue = std::min<int64_t>(int64_t(1) << 20, c->N * (c->lat == D2Q9 ? 2 : 3));
+  CKS(dalloc(c, c->d_film_mids, sizeof(FilmMid) * (size_t)c->film_mid_queue));
   return LBM_OK;
 }
 
@@ -1125,7 +1132,7 @@ lbm_status lbm_film_cells(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
                      c->cfg.G, c->cfg.rho0, h_max, eps_arm,
                      static_cast<uint8_t *>(c->d_film_state.p),
                      static_cast<unsigned long long *>(c->d_film_counts.p), cap, c->d_film_rec.p,
-                     false, c->s));
+                     false, static_cast<FilmMid *>(c->d_film_mids.p), c->film_mid_queue, c->s));
   // mailbox: [counts: 4][up to cap records], one synchronisation
   const size_t rec_bytes = fired ? sizeof(lbm_film_cell) * (size_t)cap : 0;
   CKS(halloc(c, c->h_mail, 4 * sizeof(unsigned long long) + rec_bytes));
@@ -1172,7 +1179,8 @@ lbm_status lbm_film_pairs(lbm_ctx *c, int32_t h_max, double eps_arm, lbm_film_ce
                        c->cfg.G, c->cfg.rho0, h_max, eps_arm,
                        static_cast<uint8_t *>(c->d_film_state.p),
                        static_cast<unsigned long long *>(c->d_film_counts.p), capdev,
-                       c->d_film_rec.p, true, c->s));
+                       c->d_film_rec.p, true,
+                       static_cast<FilmMid *>(c->d_film_mids.p), c->film_mid_queue, c->s));
     // mailbox: [counts: 5, one padding word][records]
     CKS(halloc(c, c->h_mail, 6 * sizeof(unsigned long long) + rec_bytes));
     auto *m = static_cast<unsigned char *>(c->h_mail.p);
@@ -1276,7 +1284,8 @@ lbm_status lbm_diagnostic_interval(lbm_ctx *c, int32_t h_max, double eps_arm, in
                      c->cfg.G, c->cfg.rho0, h_max, eps_arm,
                      static_cast<uint8_t *>(c->d_film_state.p),
                      static_cast<unsigned long long *>(c->d_film_counts.p), fired_cap,
-                     c->d_film_rec.p, false, c->s));
+                     c->d_film_rec.p, false,
+                     static_cast<FilmMid *>(c->d_film_mids.p), c->film_mid_queue, c->s));
   CKS(dalloc(c, c->d_count, sizeof(int32_t) * c->N));
   // mailbox: [ncomp][totals 4][film counts 5][census block][fired records]
   const size_t rec_bytes = fired ? sizeof(lbm_film_cell) * (size_t)fired_cap : 0;

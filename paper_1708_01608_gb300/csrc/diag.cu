@@ -771,6 +771,309 @@ __global__ void __launch_bounds__(TPB)
   if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
 }
 
+// ---- the film test along lattice lines (h_max <= 63) --------------------------
+// The classification of k_film_cells, taken one lattice line at a time: the
+// first gas cells on either side of a liquid cell are the two gas cells that
+// close the liquid run holding it (periodically: the run through the line's
+// end closes at its first gas cell).  A run is a film when its two gas cells
+// carry different labels and it holds at most h_max cells; its midpoints are
+// the cell at equal distance from both ends, or the two cells one apart.  The
+// walk clears the axis bit of every cell it passes and queues each midpoint
+// with its old bit, kept in a window of the walk's last 64 cells (for the
+// run through the end: also of its first 64).  A second kernel takes the
+// queued midpoints one per thread: the FP64 pressure, the criterion, the new
+// bit and the record.  Midpoints beyond the queue's capacity are taken in
+// the walk itself.  The counts, states and records equal k_film_cells'; the
+// records come in another order (the callers sort them, or their order does
+// not matter).
+constexpr int FILM_LINE_HMAX = 63;
+
+struct FilmArgs {
+  View v;
+  const int32_t *labels;
+  const void *stored;
+  double G, rho0, eps_arm;
+  int h_max, all_mid;
+  uint8_t *state;
+  unsigned long long *counts;  // film, midpoints, armed, fired, midpoint slots, queued
+  int64_t cap;
+  FilmRec *rec;
+  FilmMid *mids;  // the midpoint queue
+  int64_t mid_cap;
+};
+
+// The criterion at the midpoint (cell k, user axis ua, old bit ob): the new
+// bit, set in the state (atomically: the queue holds midpoints of every axis,
+// and a cell's axes share its state byte), and the record.  Returns the new bit.
+template <int LAT, int ST>
+__device__ __noinline__ unsigned film_midpoint(const FilmArgs &A, int64_t k, int ua, int ob,
+                                               int32_t lm, int32_t lp, int len) {
+  const View &v = A.v;
+  const Idx c = idx_of(k, v);
+  const int va = LAT == D2Q9 && ua == 1 ? 2 : ua;
+  const int n = (int)(va == 0 ? v.NX : (va == 1 ? v.NY : v.NZ));
+  const int ca = va == 0 ? c.x : (va == 1 ? c.y : c.z);
+  auto p_at = [&](int s) -> double {
+    const int q = wr(ca + s, n);
+    const int xx = va == 0 ? q : c.x, yy = va == 1 ? q : c.y, zz = va == 2 ? q : c.z;
+    return eos_p(cell_rho<LAT, ST>(v, A.stored, xx, yy, zz), A.G, A.rho0);
+  };
+  const double d2 = p_at(1) - 2.0 * p_at(0) + p_at(-1);
+  bool fired = false;
+  int nb = ob;
+  if (d2 < -A.eps_arm) {
+    nb = 1;
+  } else if (ob && d2 >= 0.0) {
+    nb = 0;
+    fired = true;
+  }
+  if (nb) {
+    const uint64_t a = reinterpret_cast<uint64_t>(A.state + k);
+    atomicOr(reinterpret_cast<unsigned *>(a & ~3ull), (1u << ua) << (8 * (unsigned)(a & 3)));
+  }
+  unsigned long long q = ~0ull;
+  if (A.all_mid) {
+    q = atomicAdd(&A.counts[4], 1ull);
+    if (fired) atomicAdd(&A.counts[3], 1ull);
+  } else if (fired) {
+    q = atomicAdd(&A.counts[3], 1ull);
+  }
+  if ((int64_t)q < A.cap && q != ~0ull) {
+    FilmRec r;
+    r.cell = k;
+    r.axis = A.all_mid ? (ua | (fired ? 0x100 : 0)) : ua;
+    r.label_minus = lm;
+    r.label_plus = lp;
+    r.thickness = len;
+    r.d2p = d2;
+    A.rec[q] = r;
+  }
+  return (unsigned)nb;
+}
+
+// block sums of the film, midpoint and armed counts into counts[0..2]
+__device__ __forceinline__ void film_counts_add(unsigned nfilm, unsigned nmid, unsigned narmed,
+                                                unsigned long long *counts,
+                                                unsigned long long *sh) {
+  const unsigned wf = __reduce_add_sync(0xffffffffu, nfilm);
+  const unsigned wm = __reduce_add_sync(0xffffffffu, nmid);
+  const unsigned wa = __reduce_add_sync(0xffffffffu, narmed);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sh[0], (unsigned long long)wf);
+    atomicAdd(&sh[1], (unsigned long long)wm);
+    atomicAdd(&sh[2], (unsigned long long)wa);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
+}
+
+// bits 0 .. j of a word (j <= 31)
+__device__ __forceinline__ uint32_t low_bits(int j) {
+  return j >= 31 ? 0xffffffffu : (2u << j) - 1u;
+}
+
+// The walk along one line: cell p at base + p * stride, n cells, user axis
+// ua, taken cell by cell (step), or in groups of up to 32 cells (group): the
+// group's gas cells and old bits as bit masks (bit j: cell p0 + j), its gas
+// cells then one by one.
+template <int LAT, int ST>
+struct FilmWalk {
+  int64_t base, stride;
+  int n, ua, h;
+  int f0 = -1, lf = 0, a = -1, la = 0;  // first and last gas cell so far, their labels
+  uint64_t win = 0, first = 0;          // old bits: of cell p - j, of cell j
+  unsigned nfilm = 0, nmid = 0, narmed = 0;
+
+  // one cell: p, its label and state byte
+  __device__ __forceinline__ void step(const FilmArgs &A, int p, int32_t lab, uint32_t st) {
+    const uint64_t ob = (st >> ua) & 1u;
+    win = (win << 1) | ob;
+    if (p < 64) first |= ob << p;
+    if (ob) A.state[base + (int64_t)p * stride] = (uint8_t)(st & ~(1u << ua));
+    if (lab >= 0) {
+      if (a >= 0)
+        run(A, a, p, la, lab, win, false);
+      else
+        f0 = p, lf = lab;
+      a = p;
+      la = lab;
+    }
+  }
+  // cells p0 .. p0 + cnt - 1: gas mask gm, old-bit mask om; lab(j), st(j):
+  // label and state byte of cell p0 + j
+  template <class Lab, class St>
+  __device__ __forceinline__ void group(const FilmArgs &A, int p0, int cnt, uint32_t gm,
+                                        uint32_t om, Lab lab, St st) {
+    for (uint32_t m = om; m; m &= m - 1) {  // clear the old bits as the walk passes
+      const int j = __ffs(m) - 1;
+      A.state[base + (int64_t)(p0 + j) * stride] = (uint8_t)(st(j) & ~(1u << ua));
+    }
+    if (p0 < 64) first |= (uint64_t)om << p0;
+    const uint64_t w0 = win;
+    for (uint32_t m = gm; m; m &= m - 1) {
+      const int j = __ffs(m) - 1, b = p0 + j;
+      const int32_t lb = lab(j);
+      if (a >= 0) {
+        // old bits with cell b at bit 0
+        const uint64_t wb = (w0 << (j + 1)) | (uint64_t)(__brev(om & low_bits(j)) >> (31 - j));
+        run(A, a, b, la, lb, wb, false);
+      } else {
+        f0 = b;
+        lf = lb;
+      }
+      a = b;
+      la = lb;
+    }
+    win = (w0 << cnt) | (uint64_t)(__brev(om) >> (32 - cnt));
+  }
+  // the run from the last gas cell through the line's end to the first one
+  __device__ __forceinline__ void finish(const FilmArgs &A) {
+    if (f0 >= 0) run(A, a, f0 + n, la, lf, win, true);
+  }
+  // liquid cells a_ + 1 .. b - 1 between gas cells a_ and b (b may pass n);
+  // w: old bits with the walk's current cell at bit 0 (b, or n - 1 at the end)
+  __device__ __forceinline__ void run(const FilmArgs &A, int a_, int b, int32_t lm, int32_t lp,
+                                      uint64_t w, bool wrap) {
+    const int len = b - a_ - 1;
+    if (len < 1 || len > h || lm == lp) return;
+    nfilm += (unsigned)len;
+    const int c1 = (a_ + b) >> 1;
+    for (int c = c1; c <= c1 + ((a_ + b) & 1); ++c) {
+      const int pos = c >= n ? c - n : c;
+      uint64_t ob;
+      if (!wrap)
+        ob = (w >> (b - c)) & 1u;
+      else if (c >= n)
+        ob = (first >> pos) & 1u;
+      else
+        ob = (w >> (n - 1 - c)) & 1u;
+      ++nmid;
+      const int64_t k = base + (int64_t)pos * stride;
+      const unsigned long long slot = atomicAdd(&A.counts[5], 1ull);
+      if ((int64_t)slot < A.mid_cap)
+        A.mids[slot] = FilmMid{k, lm, lp, ua | ((int)ob << 2) | (len << 3)};
+      else
+        narmed += film_midpoint<LAT, ST>(A, k, ua, (int)ob, lm, lp, len);
+    }
+  }
+};
+
+// Lines along x: one thread per row (y, z), FILM_ROWS rows per block.  The
+// block stages FILM_COLS columns of its rows at a time: a warp reads one row's
+// columns with one coalesced load per lane, and its ballots give the row's
+// gas and old-bit masks; the labels go to shared memory (row padded against
+// bank conflicts) for the gas cells the walk then takes.
+constexpr int FILM_ROWS = 128, FILM_COLS = 32;
+template <int LAT, int ST>
+__global__ void __launch_bounds__(FILM_ROWS) k_film_rows(const __grid_constant__ FilmArgs A) {
+  __shared__ int32_t slab[FILM_ROWS][FILM_COLS + 1];
+  __shared__ uint32_t sgm[FILM_ROWS], som[FILM_ROWS];
+  __shared__ unsigned long long sh[3];
+  if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+  const int NX = (int)A.v.NX, rows = (int)(A.v.NY * A.v.NZ);
+  const int r0 = blockIdx.x * FILM_ROWS, t = (int)threadIdx.x, row = r0 + t;
+  const int lane = t & 31, wp = t >> 5;
+  FilmWalk<LAT, ST> w;
+  w.base = (int64_t)row * NX;
+  w.stride = 1;
+  w.n = NX;
+  w.ua = 0;
+  w.h = A.h_max;
+  constexpr int RPW = FILM_ROWS / (FILM_ROWS / 32);  // rows staged per warp
+  for (int c0 = 0; c0 < NX; c0 += FILM_COLS) {
+    const int wd = min(FILM_COLS, NX - c0);
+    __syncthreads();
+#pragma unroll 8
+    for (int u = 0; u < RPW; ++u) {
+      const int rr = wp * RPW + u;
+      int32_t lv = -1;
+      uint32_t sv = 0;
+      if (r0 + rr < rows && lane < wd) {
+        const int64_t k = (int64_t)(r0 + rr) * NX + c0 + lane;
+        lv = A.labels[k];
+        sv = A.state[k];
+      }
+      const uint32_t gm = __ballot_sync(0xffffffffu, lv >= 0);
+      const uint32_t om = __ballot_sync(0xffffffffu, sv & 1u);  // x is user axis 0
+      slab[rr][lane] = lv;
+      if (lane == 0) {
+        sgm[rr] = gm;
+        som[rr] = om;
+      }
+    }
+    __syncthreads();
+    if (row < rows) {
+      const int32_t *lr = slab[t];
+      const int64_t b0 = w.base + c0;
+      w.group(A, c0, wd, sgm[t], som[t], [&](int j) { return lr[j]; },
+              [&](int j) { return (uint32_t)A.state[b0 + j]; });
+    }
+  }
+  if (row < rows) w.finish(A);
+  film_counts_add(w.nfilm, w.nmid, w.narmed, A.counts, sh);
+}
+
+// Lines along view axis va (y, or z): one thread per line, x fastest across
+// the threads, so that each step's loads are coalesced; FILM_AHEAD cells
+// loaded ahead of their walk.
+constexpr int FILM_AHEAD = 16;
+template <int LAT, int ST>
+__global__ void __launch_bounds__(TPB) k_film_cols(const __grid_constant__ FilmArgs A, int ua,
+                                                   int va) {
+  __shared__ unsigned long long sh[3];
+  if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+  __syncthreads();
+  const int NX = (int)A.v.NX, NY = (int)A.v.NY, NZ = (int)A.v.NZ;
+  const int64_t nlines = (int64_t)NX * (va == 1 ? NZ : NY);
+  const int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  FilmWalk<LAT, ST> w;
+  if (line < nlines) {
+    const int o = (int)(line / NX);
+    const int x = (int)(line - (int64_t)o * NX), y = va == 1 ? 0 : o, z = va == 1 ? o : 0;
+    w.base = lin(x, y, z, A.v);
+    w.stride = va == 1 ? (int64_t)NX : (int64_t)NX * NY;
+    w.n = va == 1 ? NY : NZ;
+    w.ua = ua;
+    w.h = A.h_max;
+    const int n = w.n;
+    for (int p0 = 0; p0 < n; p0 += FILM_AHEAD) {
+      int32_t lab[FILM_AHEAD];
+      uint32_t st[FILM_AHEAD];
+#pragma unroll
+      for (int j = 0; j < FILM_AHEAD; ++j) {
+        lab[j] = -1;
+        st[j] = 0;
+        if (p0 + j < n) {
+          const int64_t k = w.base + (int64_t)(p0 + j) * w.stride;
+          lab[j] = A.labels[k];
+          st[j] = A.state[k];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < FILM_AHEAD; ++j)
+        if (p0 + j < n) w.step(A, p0 + j, lab[j], st[j]);
+    }
+    w.finish(A);
+  }
+  film_counts_add(w.nfilm, w.nmid, w.narmed, A.counts, sh);
+}
+
+// The queued midpoints, one per thread (grid-stride over the queue's length).
+template <int LAT, int ST>
+__global__ void __launch_bounds__(TPB) k_film_mids(const __grid_constant__ FilmArgs A) {
+  __shared__ unsigned long long sh[3];
+  if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t nq = (int64_t)min((unsigned long long)A.mid_cap, A.counts[5]);
+  unsigned narmed = 0;
+  GRID_LOOP(q, nq) {
+    const FilmMid m = A.mids[q];
+    narmed += film_midpoint<LAT, ST>(A, m.cell, m.meta & 3, (m.meta >> 2) & 1, m.label_minus,
+                                     m.label_plus, m.meta >> 3);
+  }
+  film_counts_add(0u, 0u, narmed, A.counts, sh);
+}
+
 
 // ---- film probe on FP64 density and pressure fields -------------------------
 struct FieldAcc {
@@ -975,13 +1278,34 @@ size_t film_record_bytes() { return sizeof(FilmRec); }
 cudaError_t diag_film_cells(const View &v, const int32_t *labels, const void *stored, double G,
                             double rho0, int h_max, double eps_arm, uint8_t *state,
                             unsigned long long *counts, int64_t cap, void *records,
-                            bool all_mid, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 5, s);
+                            bool all_mid, FilmMid *mids, int64_t mid_cap, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * FILM_COUNT_SLOTS, s);
   if (e != cudaSuccess) return e;
+  FilmRec *rec = static_cast<FilmRec *>(records);
+  const int am = all_mid ? 1 : 0;
   dispatch(v, [&](auto L, auto S) {
-    k_film_cells<decltype(L)::value, decltype(S)::value><<<nblocks(ncells(v)), TPB, 0, s>>>(
-        v, labels, stored, G, rho0, h_max, eps_arm, state, counts, cap,
-        static_cast<FilmRec *>(records), all_mid ? 1 : 0);
+    constexpr int LAT = decltype(L)::value, STV = decltype(S)::value;
+    if (h_max > FILM_LINE_HMAX || !mids) {
+      k_film_cells<LAT, STV><<<nblocks(ncells(v)), TPB, 0, s>>>(
+          v, labels, stored, G, rho0, h_max, eps_arm, state, counts, cap, rec, am);
+      return;
+    }
+    const FilmArgs A{v,     labels, stored, G,   rho0, eps_arm, h_max, am,
+                     state, counts, cap,    rec, mids, mid_cap};
+    // one walk per lattice line: rows along x, then the other axes in turn;
+    // then the queued midpoints
+    const int64_t rows = v.NY * v.NZ;
+    k_film_rows<LAT, STV><<<(int)((rows + FILM_ROWS - 1) / FILM_ROWS), FILM_ROWS, 0, s>>>(A);
+    const int naxes = LAT == D2Q9 ? 2 : 3;
+    for (int ua = 1; ua < naxes; ++ua) {
+      const int va = LAT == D2Q9 ? 2 : ua;  // D2Q9's second axis is the view's z
+      const int64_t nl = v.NX * (va == 1 ? v.NZ : v.NY);
+      k_film_cols<LAT, STV><<<(int)((nl + TPB - 1) / TPB), TPB, 0, s>>>(A, ua, va);
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_film_mids<LAT, STV><<<std::max(nsm, 1) * 4, TPB, 0, s>>>(A);
   });
   return cudaGetLastError();
 }

@@ -233,9 +233,22 @@ cudaError_t inject_spread(const View &v, int ngroups, const int4 *groups, const 
                           const double *rate, double *budget, const int32_t *count, double *dep,
                           const int32_t *labels, bool any_bubble, void *lattice, cudaStream_t s);
 size_t film_record_bytes();
+// A queued film midpoint: cell, the labels on its two sides, and
+// meta = user axis | old arming bit << 2 | run length << 3.
+struct FilmMid {
+  int64_t cell;
+  int32_t label_minus, label_plus;
+  int32_t meta, pad;
+};
+// counters of a film pass: film, midpoints, armed, fired, midpoint record
+// slots, queued midpoints
+constexpr int FILM_COUNT_SLOTS = 6;
+// The film test at every lattice point, arming state updated in place.
+// mids (capacity mid_cap) queues midpoints for the line walks (h_max <= 63);
+// NULL selects the per-cell kernel.
 cudaError_t diag_film_cells(const View &v, const int32_t *labels, const void *stored, double G,
                             double rho0, int h_max, double eps_arm, uint8_t *state,
                             unsigned long long *counts, int64_t cap, void *records,
-                            bool all_mid, cudaStream_t s);
+                            bool all_mid, FilmMid *mids, int64_t mid_cap, cudaStream_t s);
 
 }  // namespace sclbm
