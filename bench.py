@@ -55,8 +55,8 @@ FALLBACK_HBM_GBS = 6800.0
 # five times the L2 and the capture's traffic equals the algorithmic bytes.
 NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 25): 277.88e6,
                           ("d3q19_foam_128", "f64", 6): 626.2e6,
-                          ("d3q19_foam_512", "f32", 16): 8 * 2534.88e6,
-                          ("d3q19_foam_512", "f16", 24): 8 * 1268.09e6}
+                          ("d3q19_foam_512", "f32", 16): 8 * 2534.55e6,
+                          ("d3q19_foam_512", "f16", 24): 8 * 1264.90e6}
 # FP64 storage: the step kernel is bound by the FP64 pipe, not by HBM.  FP64
 # operations per lattice update of its D3Q19 kernel, DADD + DMUL + 2 DFMA as
 # ncu counts them on the 128^3 case (146 + 71 + 2 x 332).  The peak is
@@ -259,9 +259,9 @@ def diagnostics(L):
 
 # kernels of one diagnostic interval (FP32 storage): scan + final (totals and
 # gas flags), union + compress (labels), site gather, film test (one walk per
-# lattice line and axis, pressure of its midpoints computed in place), census
-# count + list
-DIAG_LAUNCHES = 10
+# lattice line and axis, then the queued midpoints with their pressure),
+# census count + list
+DIAG_LAUNCHES = 11
 
 
 # The oracle's FP64 populations of a 512^3 or 768^3 lattice (20 GB, 68 GB)
