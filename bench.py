@@ -53,8 +53,8 @@ FALLBACK_HBM_GBS = 6800.0
 # kernel report null.  The 512^3 entries are the 256^3 capture of the same
 # tile scaled by the cells per launch (x8): at 256^3 the lattice is already
 # five times the L2 and the capture's traffic equals the algorithmic bytes.
-NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 25): 277.88e6,
-                          ("d3q19_foam_128", "f64", 6): 626.2e6,
+NCU_TRAFFIC_PER_LAUNCH = {("d3q19_foam_128", "f32", 25): 277.73e6,
+                          ("d3q19_foam_128", "f64", 6): 626.48e6,
                           ("d3q19_foam_512", "f32", 16): 8 * 2534.55e6,
                           ("d3q19_foam_512", "f16", 24): 8 * 1264.90e6}
 # FP64 storage: the step kernel is bound by the FP64 pipe, not by HBM.  FP64
