@@ -34,6 +34,20 @@ def test_header_symbols_exported(lbm):
     assert set(names) == set(lbm.EXPORTS)
 
 
+def test_header_constants_match_binding(lbm):
+    """Every integer constant of include/lbm.h (enum members and #defines)
+    that the Python binding mirrors under the same name, without the LBM_
+    prefix, has the same value there."""
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = dict(re.findall(r"#define\s+LBM_([A-Z0-9_]+)\s+(-?\d+)\b", text))
+    consts.update(re.findall(r"\bLBM_([A-Z0-9_]+)\s*=\s*(-?\d+)", text))
+    mirrored = {k: int(v) for k, v in consts.items() if hasattr(lbm, k)}
+    assert len(mirrored) >= 25, sorted(mirrored)
+    for k, v in mirrored.items():
+        assert getattr(lbm, k) == v, k
+
+
 def test_version(lbm):
     assert "sm_103a" in lbm.version()
 
