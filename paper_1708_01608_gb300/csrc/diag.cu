@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(TPB)
   if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
 }
 
-// ---- the film test along lattice lines (h_max <= 63) --------------------------
+// ---- the film test along lattice lines (h_max <= 63; Sec. 4) ------------------
 // The classification of k_film_cells, taken one lattice line at a time: the
 // first gas cells on either side of a liquid cell are the two gas cells that
 // close the liquid run holding it (periodically: the run through the line's
