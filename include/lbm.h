@@ -109,7 +109,8 @@ typedef struct {
                            second staged plane, so that its bounded wait
                            (1 s) expires and lbm_sync reports LBM_ETIMEOUT;
                            exercises the timeout path without a fault.
-                           LBM_DEBUG_CONVERT_BEFORE_FMA: see below */
+                           LBM_DEBUG_CONVERT_BEFORE_FMA and
+                           LBM_DEBUG_SMALL_FILM_QUEUE: see below */
   double nucleus_radius; /* radius of the nuclei lbm_seed_bubbles samples
                             when given no bubble list (Sec. 3: random
                             nucleation sites); default 3 cells */
@@ -133,6 +134,10 @@ typedef struct {
    (they otherwise widen it inside the FMA); the results are the same bits,
    which a test checks by comparing the two forms */
 #define LBM_DEBUG_CONVERT_BEFORE_FMA 2
+/* The film test's midpoint queue holds 16 entries, so that the line walks
+   take most midpoints themselves (the path of a lattice with more than
+   2^20 midpoints); the results are the same */
+#define LBM_DEBUG_SMALL_FILM_QUEUE 4
 
 typedef struct {
   double x, y, z, r; /* centre (cell coordinates; z = 0 in 2-D) and radius */

@@ -1117,7 +1117,9 @@ static lbm_status film_prepare(lbm_ctx *c, int32_t h_max, double eps_arm) {
   CKS(dalloc(c, c->d_film_counts, FILM_COUNT_SLOTS * sizeof(unsigned long long)));
   // queue of the line walks' midpoints: up to 2^20 (one per cell and axis at
   // most); midpoints beyond it are taken inside the walks
-  c->film_mid_queue = std::min<int64_t>(int64_t(1) << 20, c->N * (c->lat == D2Q9 ? 2 : 3));
+  c->film_mid_queue = (c->cfg.debug_flags & 4)  // LBM_DEBUG_SMALL_FILM_QUEUE
+                           ? 16
+                           : std::min<int64_t>(int64_t(1) << 20, c->N * (c->lat == D2Q9 ? 2 : 3));
   CKS(dalloc(c, c->d_film_mids, sizeof(FilmMid) * (size_t)c->film_mid_queue));
   return LBM_OK;
 }

@@ -29,6 +29,7 @@ RHO, PSI, P, U, F, LAPP = range(6)
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_TWO_PASS = 0, 1, 2
 DEBUG_WITHHOLD_TMA = 1
 DEBUG_CONVERT_BEFORE_FMA = 2
+DEBUG_SMALL_FILM_QUEUE = 4
 # lbm_ensemble_set_launch modes
 ENS_AUTO, ENS_GRAPH, ENS_DEBUG_WITHHOLD_FLAG, ENS_PERSISTENT, ENS_TEMPORAL = 0, 1, 2, 3, 4
 

@@ -959,15 +959,17 @@ def test_film_cells_3d_match_oracle(lbm):
     L.close()
 
 
-@pytest.mark.parametrize("lat,ext,h_max", [("D3Q19", (40, 6, 30), 12), ("D3Q19", (40, 6, 30), 63),
-                                           ("D3Q19", (40, 6, 30), 64), ("D2Q9", (96, 70, 1), 5),
-                                           ("D2Q9", (96, 70, 1), 63)])
-def test_film_cells_many_bubbles_match_oracle(lbm, lat, ext, h_max):
+@pytest.mark.parametrize("lat,ext,h_max,flags", [
+    ("D3Q19", (40, 6, 30), 12, 0), ("D3Q19", (40, 6, 30), 63, 0), ("D3Q19", (40, 6, 30), 64, 0),
+    ("D2Q9", (96, 70, 1), 5, 0), ("D2Q9", (96, 70, 1), 63, 0), ("D3Q19", (40, 6, 30), 12, 4),
+    ("D2Q9", (96, 70, 1), 12, 4)])
+def test_film_cells_many_bubbles_match_oracle(lbm, lat, ext, h_max, flags):
     """Small bubbles at seeded random places (FP64), some across the
     periodic seams, and in 3D a y axis shorter than h_max: the film census,
     the arming state and the fired records agree with the oracle at three
     calls 10 steps apart.  h_max <= 63 takes the line walks, 64 the
-    per-cell kernel."""
+    per-cell kernel; with LBM_DEBUG_SMALL_FILM_QUEUE (flags 4) the walks
+    take all but 16 midpoints themselves."""
     nx, ny, nz = ext
     rng = np.random.default_rng(h_max)
     nb = 40 if lat == "D3Q19" else 30
@@ -975,11 +977,13 @@ def test_film_cells_many_bubbles_match_oracle(lbm, lat, ext, h_max):
                     rng.uniform(0, nz, nb) if nz > 1 else np.zeros(nb),
                     rng.uniform(1.5, 4.0, nb)], 1)
     f = oracle_init(lat, nx, ny, nz, bub, 2.0, 0.15, 1.5, 1e-3, 8)
-    L = lbm.Lattice(lat, nx, ny, nz, tau=1.0, G=-5.0, storage="f64")
+    L = lbm.Lattice(lat, nx, ny, nz, tau=1.0, G=-5.0, storage="f64", debug_flags=flags)
     L.write_f(f)
     state = np.zeros((nz, ny, nx), dtype=np.uint8)
     for call in range(3):
         got = L.film_cells(h_max, 1e-3)
+        if flags:
+            assert got[0]["midpoints"] > 16
         _same_film(got, _film_oracle(LAT[lat], f, -5.0, h_max, 1e-3, state))
         assert got[0]["film"] > 0 and got[0]["midpoints"] > 0
         L.step(10)
