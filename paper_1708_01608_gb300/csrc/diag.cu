@@ -595,10 +595,11 @@ __device__ __forceinline__ void uf_union(int32_t *L, int32_t a, int32_t b) {
 __global__ void k_ccl_init(int64_t N, const double *rho, double thr, int32_t *L) {
   GRID_LOOP(k, N) L[k] = rho[k] < thr ? (int32_t)k : -1;
 }
+// (gas or liquid is fixed before the pass: only gas entries change)
 __global__ void k_ccl_union(const View v, int32_t *L) {
   const int64_t N = v.NX * v.NY * v.NZ;
-  GRID_LOOP(k, N) {
-    if (L[k] < 0) continue;
+  quad_pass(N, L, [&](int64_t k, int32_t lk) {
+    if (lk < 0) return;
     const Idx c = idx_of(k, v);
     const int64_t nbr[3] = {lin(wr(c.x + 1, (int)v.NX), c.y, c.z, v),
                             lin(c.x, wr(c.y + 1, (int)v.NY), c.z, v),
@@ -607,16 +608,16 @@ __global__ void k_ccl_union(const View v, int32_t *L) {
       const int64_t m = nbr[q];
       if (m != k && L[m] >= 0) uf_union(L, (int32_t)k, (int32_t)m);
     }
-  }
+  });
 }
 __global__ void k_ccl_compress(int64_t N, int32_t *L, unsigned long long *ncomp) {
   unsigned int roots = 0;
-  GRID_LOOP(k, N) {
-    if (L[k] < 0) continue;
+  quad_pass(N, L, [&](int64_t k, int32_t lk) {
+    if (lk < 0) return;
     const int32_t r = uf_find(L, (int32_t)k);
     L[k] = r;
     roots += (r == (int32_t)k);
-  }
+  });
   if (roots) atomicAdd(ncomp, (unsigned long long)roots);
 }
 __global__ void k_gather_labels(const int32_t *L, const int32_t *cells, int32_t n, int32_t *out) {
@@ -1257,8 +1258,8 @@ cudaError_t diag_label_links(const View &v, int32_t *labels, unsigned long long 
   const int64_t N = ncells(v);
   cudaError_t e = cudaMemsetAsync(ncomp_dev, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_ccl_union<<<nblocks(N), TPB, 0, s>>>(v, labels);
-  k_ccl_compress<<<nblocks(N), TPB, 0, s>>>(N, labels, ncomp_dev);
+  k_ccl_union<<<nblocks((N + 3) / 4), TPB, 0, s>>>(v, labels);
+  k_ccl_compress<<<nblocks((N + 3) / 4), TPB, 0, s>>>(N, labels, ncomp_dev);
   return cudaGetLastError();
 }
 
@@ -1268,8 +1269,8 @@ cudaError_t diag_label(const View &v, const double *rho, double thr, int32_t *la
   cudaError_t e = cudaMemsetAsync(ncomp_dev, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_ccl_init<<<nblocks(N), TPB, 0, s>>>(N, rho, thr, labels);
-  k_ccl_union<<<nblocks(N), TPB, 0, s>>>(v, labels);
-  k_ccl_compress<<<nblocks(N), TPB, 0, s>>>(N, labels, ncomp_dev);
+  k_ccl_union<<<nblocks((N + 3) / 4), TPB, 0, s>>>(v, labels);
+  k_ccl_compress<<<nblocks((N + 3) / 4), TPB, 0, s>>>(N, labels, ncomp_dev);
   return cudaGetLastError();
 }
 

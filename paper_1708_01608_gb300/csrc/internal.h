@@ -165,6 +165,32 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f, uint32_t 
   const uint32_t t = __umulhi(f.m, n);
   return (t + ((n - t) >> f.s1)) >> f.s2;
 }
+// A grid-stride pass over the N cells of an int32 array A, four cells per
+// iteration from one 16-byte load: f(k, A[k]) for every cell, in increasing
+// k within a thread.  Four times the bytes in flight of a one-cell loop.  A
+// may be written during the pass only where f's decision does not depend on
+// the timing (the sign of a label).  An A not on a 16-byte boundary (a
+// caller's allocator) takes one cell per iteration.
+template <class F>
+__device__ __forceinline__ void quad_pass(int64_t N, const int32_t *A, F f) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (reinterpret_cast<uintptr_t>(A) & 15) {
+    for (int64_t k = t; k < N; k += stride) f(k, A[k]);
+    return;
+  }
+  const int64_t nq = N >> 2;
+  const int4 *A4 = reinterpret_cast<const int4 *>(A);
+  for (int64_t q = t; q < nq; q += stride) {
+    const int4 a = A4[q];
+    f(4 * q, a.x);
+    f(4 * q + 1, a.y);
+    f(4 * q + 2, a.z);
+    f(4 * q + 3, a.w);
+  }
+  const int64_t k = 4 * nq + t;  // the last N mod 4 cells
+  if (k < N) f(k, A[k]);
+}
 #endif
 // initial density field (doubles, N) from bubbles (view coordinates, x y z r)
 cudaError_t diag_init_rho(const View &v, const double *bub, int32_t nb, double rho_l,
